@@ -1,0 +1,253 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test names what fixes the expected value: the DFT definition summed by
+brute force, numpy's independent FFT, closed forms, textbook invariants, or
+hand-worked fixtures in tests/golden/.  The oracle is only trusted because
+these pass.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import abft
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+rng = np.random.default_rng(12345)
+
+
+def crandn(*shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def read_golden(name):
+    blocks, cur = [], {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, *vals = line.split()
+        if key == "N":
+            cur = {"N": int(vals[0])}
+            blocks.append(cur)
+        else:
+            v = np.array([float(t) for t in vals])
+            cur[key] = v[0::2] + 1j * v[1::2]
+    return blocks
+
+
+# ---------------------------------------------------------------- FFT pins
+@pytest.mark.parametrize("n", [1 << k for k in range(0, 9)])
+def test_fft_matches_bruteforce_definition(n):
+    """Section II definition summed directly in long double, N = 1..256."""
+    x = crandn(3, n)
+    assert rel(oracle.fft(x), oracle.dft_naive(x)) < 1e-15 * max(1, np.log2(n)) + 1e-16
+
+
+@pytest.mark.parametrize("n", [1 << k for k in range(1, 9)])
+def test_inverse_matches_bruteforce_definition(n):
+    y = crandn(2, n)
+    assert rel(oracle.ifft(y), oracle.dft_naive(y, sign=+1)) < 1e-15 * np.log2(n) + 1e-16
+
+
+@pytest.mark.parametrize("n", [1 << k for k in (4, 10, 13, 16)])
+def test_fft_matches_numpy_library(n):
+    """numpy's pocketfft is an independent FFT implementation."""
+    x = crandn(2, n)
+    assert rel(oracle.fft(x), np.fft.fft(x, axis=-1)) < 1e-15 * np.log2(n)
+
+
+def test_golden_hand_worked_dfts():
+    for blk in read_golden("dft_small.txt"):
+        y = oracle.fft(blk["x"])
+        assert np.allclose(y, blk["y"], rtol=0, atol=1e-14), blk["N"]
+
+
+@pytest.mark.parametrize("n", [2, 16, 1024, 1 << 15])
+def test_delta_maps_to_constant_and_shifted_delta_to_column(n):
+    x = np.zeros(n, complex); x[0] = 1.0
+    assert np.max(np.abs(oracle.fft(x) - 1.0)) < 1e-15
+    k = n // 2 + 1 if n > 2 else 1
+    x = np.zeros(n, complex); x[k] = 1.0
+    col = np.exp(-2j * np.pi * ((np.arange(n) * k) % n) / n)     # column k of W
+    assert np.max(np.abs(oracle.fft(x) - col)) < 1e-14
+
+
+@pytest.mark.parametrize("n,k0", [(64, 5), (4096, 1234), (1 << 16, 40000)])
+def test_pure_tone_maps_to_one_bin(n, k0):
+    t = np.arange(n)
+    x = np.exp(2j * np.pi * ((k0 * t) % n) / n)
+    y = oracle.fft(x)
+    expect = np.zeros(n, complex); expect[k0] = n
+    assert np.max(np.abs(y - expect)) < 1e-11 * n
+
+
+@pytest.mark.parametrize("n", [8, 4096, 1 << 18])
+def test_parseval_and_roundtrip(n):
+    x = crandn(2, n)
+    y = oracle.fft(x)
+    assert abs(np.sum(np.abs(y) ** 2) / (n * np.sum(np.abs(x) ** 2)) - 1) < 1e-13
+    assert rel(oracle.ifft(y), x) < 1e-15 * np.log2(n)
+
+
+def test_linearity():
+    n = 2048
+    a, b = crandn(n), crandn(n)
+    alpha, beta = 0.3 - 1.7j, -2.5 + 0.25j
+    lhs = oracle.fft(alpha * a + beta * b)
+    rhs = alpha * oracle.fft(a) + beta * oracle.fft(b)
+    assert rel(lhs, rhs) < 1e-14
+
+
+def test_sizes_one_and_two_closed_form():
+    a, b = 0.25 - 3j, 1.5 + 2j
+    assert np.allclose(oracle.fft(np.array([a])), [a], atol=0)
+    assert np.allclose(oracle.fft(np.array([a, b])), [a + b, a - b], atol=1e-15)
+
+
+def test_rejects_non_power_of_two():
+    with pytest.raises(ValueError):
+        oracle.fft(np.ones(12, complex))
+
+
+# ---------------------------------------------------------- checksum pins
+@pytest.mark.parametrize("n", [4, 256, 1024, 1 << 14])
+def test_checksum_vector_two_independent_ways(n):
+    """Closed-form geometric sum vs the DFT of r (absolute error of the FFT
+    route is ~u sqrt(N) log2 N; the closed form is accurate to a few u)."""
+    a = abft.checksum_vector_closed_form(n)
+    b = abft.checksum_vector_by_fft(n)
+    eps = np.finfo(np.float64).eps
+    assert np.all(np.abs(a - b) <= 4 * eps * (np.abs(b) + np.sqrt(n) * np.log2(n)))
+    assert np.min(np.abs(a)) > 0.86        # never zero for N = 2^m
+
+
+def test_checksum_vector_golden_n4():
+    blk = read_golden("checksum_small.txt")[0]
+    assert np.allclose(abft.checksum_vector_closed_form(4), blk["w"], atol=1e-14)
+    assert np.allclose(abft.checksum_vector_by_fft(4), blk["w"], atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [16, 1024, 1 << 16])
+def test_left_checksum_identity(n):
+    """(r^T W) x = r^T (W x) for any x (Eq. ABFT / C)."""
+    x = crandn(n)
+    w = abft.checksum_vector_closed_form(n)
+    lhs = w @ x
+    rhs = abft.left_vector(n) @ oracle.fft(x)
+    assert abs(lhs - rhs) / (np.sqrt(n) * np.linalg.norm(x)) < 1e-14
+
+
+def test_all_ones_left_vector_sums_to_n_x0():
+    """Textbook special case: sum_k y_k = N x_0 (why e = ones is weak)."""
+    n = 512
+    x = crandn(n)
+    assert abs(np.sum(oracle.fft(x)) - n * x[0]) < 1e-11 * n
+
+
+# ------------------------------------------------------------ ABFT pins
+def _clean_group(n, g, seed):
+    r = np.random.default_rng(seed)
+    x = r.uniform(-1, 1, (g, n)) + 1j * r.uniform(-1, 1, (g, n))
+    return x, oracle.fft(x)
+
+
+def test_clean_group_is_not_detected():
+    for seed in range(20):
+        x, y = _clean_group(256, 8, seed)
+        cs = abft.group_checksums(x, y)
+        v = abft.verify_group(cs, 256, 8, u=2.0 ** -53, kappa=4.0)
+        assert not v.detected
+
+
+@pytest.mark.parametrize("n,g", [(8, 1), (16, 4), (64, 8)])
+def test_every_site_detected_located_corrected(n, g):
+    """Brute force over every (signal, element) output site: an exact fault
+    gives the quotient b*+1, and the correction recovers W x."""
+    x, y = _clean_group(n, g, 7)
+    for b in range(g):
+        for j in range(n):
+            yf = y.copy()
+            yf[b, j] += 0.3 - 0.2j
+            cs = abft.group_checksums(x, yf)
+            v = abft.verify_group(cs, n, g, u=2.0 ** -53, kappa=4.0)
+            assert v.detected and v.located == b, (b, j, v)
+            assert abs(v.quotient - (b + 1)) < 1e-9
+            yc = abft.correct_group(x, yf, b)
+            assert rel(yc, y) < 1e-14
+
+
+def test_weight_zero_would_hide_signal_zero():
+    """Plant the e_3 indexing mistake (weights 0..G-1) in a copy: the quotient
+    for a fault in signal 0 becomes 0 and cannot name it -- the reason the
+    weights are 1..G."""
+    n, g = 32, 4
+    x, y = _clean_group(n, g, 3)
+    yf = y.copy(); yf[0, 5] += 1.0
+    d1 = abft.left_vector(n) @ (np.ones(g) @ (yf - y))
+    d2 = abft.left_vector(n) @ (np.arange(g) @ (yf - y))
+    assert abs(d2 / d1) < 1e-12
+    cs = abft.group_checksums(x, yf)
+    assert abft.verify_group(cs, n, g, 2.0 ** -53, 4.0).located == 0
+
+
+def test_planted_sign_error_in_w_is_caught():
+    """Plant a conjugated e_Wang (w3^{+j}) in the left vector: the identity
+    pin fails, so a wrong sign cannot slip through."""
+    n = 64
+    x = crandn(n)
+    bad_r = np.conj(abft.left_vector(n))
+    lhs = abft.checksum_vector_closed_form(n) @ x
+    assert abs(lhs - bad_r @ oracle.fft(x)) > 1e-3
+
+
+@pytest.mark.parametrize("stage", [-1, 0, 3, 5])
+@pytest.mark.parametrize("bit", [20, 45, 62])
+def test_emulated_bitflip_fp64_detected_and_corrected(stage, bit):
+    """Section II-A fault model run on the CPU: one bit flipped in an
+    intermediate FP64 value of signal 2; large flips are caught and fixed."""
+    n, g, bs = 64, 4, 2
+    x, y = _clean_group(n, g, 11)
+    yf = y.copy()
+    yf[bs] = oracle.fft_faulty(x[bs], 64, stage=stage, elem=13, comp=1, bit=bit)
+    err = np.linalg.norm(yf[bs] - y[bs]) / np.linalg.norm(y[bs])
+    with np.errstate(all='ignore'):
+        res = abft.run(x, yf, group=g, u=2.0 ** -53, kappa=4.0)
+    if not np.isfinite(err) or err > 1e-12:
+        assert res.detected_groups == [0]
+        assert res.located == {0: bs}
+        assert rel(res.y, y) < 1e-12
+    else:
+        assert rel(res.y, y) < 1e-12     # benign: output already within tolerance
+
+
+def test_fp32_emulation_clean_matches_within_fp32_rounding():
+    n = 1024
+    x, y = _clean_group(n, 1, 5)
+    y32 = oracle.fft_faulty(x[0].astype(np.complex64), 32)
+    assert 1e-9 < rel(y32, y[0]) < 2e-6 * np.log2(n)
+
+
+def test_nonfinite_fault_located_by_scan():
+    n, g = 32, 4
+    x, y = _clean_group(n, g, 9)
+    yf = y.copy(); yf[3, 7] = np.inf
+    res = abft.run(x, yf, group=g, u=2.0 ** -53, kappa=4.0)
+    assert res.detected_groups == [0] and res.located == {0: 3}
+    assert rel(res.y, y) < 1e-13
+
+
+def test_ragged_last_group():
+    n, B, g = 16, 11, 4
+    r = np.random.default_rng(1)
+    x = r.standard_normal((B, n)) + 1j * r.standard_normal((B, n))
+    y = oracle.fft(x)
+    yf = y.copy(); yf[10, 2] *= 1.01
+    res = abft.run(x, yf, group=g, u=2.0 ** -53, kappa=4.0)
+    assert res.detected_groups == [2] and res.located == {2: 10}
+    assert rel(res.y, y) < 1e-13
