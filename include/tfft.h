@@ -1,0 +1,251 @@
+/*
+ * tfft.h -- C ABI of the GB300 (sm_103a) fault-tolerant batched FFT.
+ *
+ * The library computes the batched one-dimensional complex-to-complex forward
+ * DFT of TurboFFT (Wu et al., arXiv 2405.02520), Section II:
+ *
+ *     y_j = sum_{n=0}^{N-1} x_n exp(-2 pi i j n / N),   j = 0..N-1,
+ *
+ * unnormalised, for every signal of a batch, fused with the paper's two-sided
+ * algorithm-based fault tolerance (ABFT), Section III (Eqs. two_side_X and
+ * two_side_Y, Section III-B "Delayed Batched Correction"): the batch is
+ * encoded on the input side with the checksum vector w = W^T r and on the
+ * output side with r, where r_j = exp(-2 pi i j / 3) (Wang's e_Wang vector,
+ * Section II), and across each group of G consecutive signals with the all-ones
+ * vector and the index weights (1, 2, ..., G).  A silent data corruption in a
+ * group is detected from the unweighted checksums, the faulty signal is named
+ * by the quotient of the weighted and unweighted residuals, and it is
+ * corrected by subtracting the batch-checksum divergence
+ * (sum_b y'_b - W sum_b x_b) -- no recomputation of that signal.
+ *
+ * Data layout (all entry points): `batch` signals of `n` complex values,
+ * signal-major [batch][n], each value interleaved (re, im); complex64 is two
+ * floats (8 bytes), complex128 two doubles (16 bytes).  Device pointers must be
+ * 16-byte aligned.  Output is in natural order.
+ *
+ * Return codes: 0 (TFFT_SUCCESS) or a negative TFFT_ERR_* value.  Faults that
+ * the ABFT detects are NOT errors: tfft_exec is asynchronous and never reports
+ * them through its return value; read them with tfft_report / tfft_report_ex.
+ *
+ * Threading: a plan may be used from one host thread at a time; two execs of
+ * one plan must not overlap on the GPU (they share the plan's workspace).
+ * Different plans are independent.
+ */
+#ifndef TFFT_H
+#define TFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; 0 (NULL) is the legacy default stream. */
+struct CUstream_st;
+typedef struct CUstream_st *tfft_stream_t;
+
+/* Opaque plan, owned by the library: tfft_plan* creates it, tfft_destroy
+ * frees it and every device allocation it made. */
+typedef struct tfft_plan_s *tfft_plan_t;
+
+enum tfft_dtype { TFFT_C64 = 0, TFFT_C128 = 1 };
+
+enum tfft_abft_mode {
+    TFFT_ABFT_OFF = 0,        /* plain FFT                                   */
+    TFFT_ABFT_TWO_SIDED = 2   /* Section III two-sided checksums; 1 is kept
+                                 free for a one-sided mode                    */
+};
+
+enum tfft_status {
+    TFFT_SUCCESS = 0,
+    TFFT_ERR_INVALID_ARG = -1,  /* n not a power of two in [2^0, 2^26], batch
+                                   < 1, null or misaligned pointer, bad option */
+    TFFT_ERR_UNSUPPORTED = -2,  /* dtype or abft_mode not implemented         */
+    TFFT_ERR_CUDA = -3,         /* a CUDA runtime call failed; see
+                                   tfft_last_cuda_error()                     */
+    TFFT_ERR_INPLACE = -4,      /* in == out with ABFT on: the correction and
+                                   the group recompute re-read the input      */
+    TFFT_ERR_ALLOC = -5,        /* device or host allocation failed           */
+    TFFT_ERR_NO_DEVICE = -6     /* no CUDA device, or not compute capability
+                                   10.3 (the kernels are built for sm_103a)   */
+};
+
+/*
+ * tfft_plan -- plan a batched forward FFT of `batch` signals of length `n`
+ * (a power of two, 1 <= n <= 2^26), element type `dtype` (TFFT_C64 or
+ * TFFT_C128), fault tolerance `abft_mode` (TFFT_ABFT_OFF or
+ * TFFT_ABFT_TWO_SIDED).  Chooses the pass decomposition (one pass when a
+ * signal fits one thread block's tile, otherwise the kernel-level tiling of
+ * Section IV-A into two or three launches), builds the FP64-accurate twiddle
+ * and checksum tables on the host, uploads them, and allocates the workspace
+ * (the inter-pass buffer, checksum records, fault lists, counters) on the
+ * current CUDA device.  Launches no kernel.  *out receives the plan.
+ */
+int tfft_plan(tfft_plan_t *out, int64_t n, int64_t batch, int dtype, int abft_mode);
+
+/* Extended options.  Zero-initialise and set what you need; zero means the
+ * default for every field except n, batch, dtype, abft_mode. */
+typedef struct tfft_plan_opts {
+    int64_t n;
+    int64_t batch;
+    int dtype;
+    int abft_mode;
+    int group;          /* G: signals per checksum group (default 16)          */
+    double kappa;       /* detection threshold constant (default 4); the
+                           threshold is kappa*u*log2(n)*sqrt(n)*sqrt(E_g), E_g
+                           the group's input energy sum_b ||x_b||^2, u the
+                           unit roundoff of dtype                               */
+    int detect_only;    /* 1: detect and locate but leave outputs uncorrected  */
+    int max_faults;     /* groups corrected per exec (default: as many as fit
+                           a 1 GiB budget, at most 8); more are counted
+                           uncorrectable                                       */
+    int force_passes;   /* 0: planner's choice; 1, 2 or 3 forces the count
+                           (TFFT_ERR_INVALID_ARG when it cannot tile n)         */
+    int checksum_vector;       /* signal-side encoding vector r:
+                                  TFFT_R_RANDOM (default) r_k = +-1 with the
+                                  sign of bit 63 of output k of the SplitMix64
+                                  stream seeded with checksum_seed;
+                                  TFFT_R_WANG r_k = e^{-2 pi i k/3} (e_Wang)  */
+    uint64_t checksum_seed;    /* seed of the random vector (0: a fixed default) */
+} tfft_plan_opts;
+
+enum tfft_checksum_vector { TFFT_R_RANDOM = 0, TFFT_R_WANG = 1 };
+
+int tfft_plan_ex(tfft_plan_t *out, const tfft_plan_opts *opts);
+
+/*
+ * tfft_exec -- transform `batch` signals from device buffer `in` to device
+ * buffer `out` (layout above, each plan->batch*n elements), asynchronously on
+ * `stream`.  `in` is never written.  With ABFT on, `in` and `out` must not
+ * overlap (TFFT_ERR_INPLACE).  No host synchronisation, no allocation.
+ * Returns TFFT_ERR_CUDA if a launch fails.
+ */
+int tfft_exec(tfft_plan_t p, const void *in, void *out, tfft_stream_t stream);
+
+/*
+ * tfft_exec_host -- the same transform on HOST buffers (pinned or pageable):
+ * copies `host_in` to a plan-owned device buffer, runs tfft_exec, copies the
+ * result to `host_out`, all on `stream`, and synchronises `stream` before
+ * returning.  The plan allocates its two device staging buffers on the first
+ * call and keeps them until tfft_destroy.
+ */
+int tfft_exec_host(tfft_plan_t p, const void *host_in, void *host_out, tfft_stream_t stream);
+
+/*
+ * tfft_report -- synchronise the stream of the plan's last exec and return
+ * the cumulative number of groups in which a fault was detected, and of
+ * those that were corrected (by the checksum correction or, when the faulty
+ * signal could not be named with confidence, by recomputing the group from
+ * its input).  detected - corrected groups were left uncorrected.  Either
+ * pointer may be NULL.
+ */
+int tfft_report(tfft_plan_t p, int64_t *detected, int64_t *corrected);
+
+typedef struct tfft_stats {
+    int64_t detected;       /* groups flagged by the residual test             */
+    int64_t corrected;      /* fixed by the checksum correction                */
+    int64_t recomputed;     /* fixed by recomputing the whole group            */
+    int64_t uncorrectable;  /* detected, not fixed (lists full / detect_only)  */
+    int64_t execs;          /* tfft_exec calls since plan / reset              */
+    int64_t launches;       /* kernels launched since plan / reset             */
+    double max_clean_ratio; /* largest |T1 - S1| / threshold over the groups
+                               that were NOT flagged (calibration of kappa)     */
+} tfft_stats;
+
+int tfft_report_ex(tfft_plan_t p, tfft_stats *stats);
+int tfft_reset_counters(tfft_plan_t p);
+
+/* One detection, as logged on the device (ring of 1024 entries). */
+typedef struct tfft_fault_event {
+    int64_t exec_index;     /* 0-based exec count of the plan                   */
+    int64_t group;          /* checksum group                                   */
+    int64_t signal;         /* located signal (batch index), -1 if not located  */
+    int32_t action;         /* 1 corrected, 2 group recomputed, 3 uncorrected   */
+    int32_t nonfinite;      /* the residual or a partial sum was not finite     */
+    double residual;        /* |T1 - S1|                                        */
+    double tau;             /* threshold                                        */
+    double q_re, q_im;      /* quotient (T2 - S2) / (T1 - S1)                   */
+} tfft_fault_event;
+
+/* Copy up to `capacity` most recent events (oldest first) and the total
+ * number logged since plan / reset into *total.  Synchronises. */
+int tfft_fault_log(tfft_plan_t p, tfft_fault_event *events, int capacity, int64_t *total);
+
+/*
+ * Fault injection (the Section II-A fault model: one soft error in a compute
+ * unit).  Arms one fault for the NEXT tfft_exec only.  The kernel that owns
+ * the value applies it in registers, after the value is computed and before
+ * it is checksummed or stored, so it is a computation error, not a memory
+ * error.  Sites: pass p (0-based), stage s (-1 = the value just loaded, 0..
+ * stages-1 = the value produced by that radix stage, the last stage's value
+ * being the pass output), signal, line (line index within the signal for
+ * that pass, see tfft_plan_info) and index (element index within the line in
+ * that stage's output order).
+ */
+enum tfft_fault_mode {
+    TFFT_FAULT_NONE = 0,
+    TFFT_FAULT_BITFLIP = 1,   /* flip bit `bit` of the value: bits 0..w-1 of
+                                 the real part, w..2w-1 of the imaginary part
+                                 (w = 32 for C64, 64 for C128)                 */
+    TFFT_FAULT_SCALE = 2,     /* multiply the value by (factor + 0 i)          */
+    TFFT_FAULT_ADD = 3,       /* add (factor + 0 i) to the value               */
+    TFFT_FAULT_ADD_PAIR = 4   /* add (factor + 0 i) to the same value of
+                                 signals `signal` and `signal`+1: two faults,
+                                 outside the single-event model, to exercise
+                                 the recompute fallback                        */
+};
+
+typedef struct tfft_fault {
+    int mode;
+    int pass;
+    int stage;
+    int bit;
+    int64_t signal;
+    int64_t line;
+    int64_t index;
+    double factor;
+} tfft_fault;
+
+int tfft_set_fault(tfft_plan_t p, const tfft_fault *fault);
+
+typedef struct tfft_info {
+    int64_t n, batch;
+    int dtype, abft_mode;
+    int passes;
+    int nsub[3];             /* sub-transform length per pass                 */
+    int stages[3];           /* radix stages per pass                          */
+    int lines_per_tile[3];
+    int64_t lines_per_signal[3];
+    int group;
+    int max_faults;
+    double kappa;
+    int64_t workspace_bytes;
+    int launches_per_exec;   /* kernels one tfft_exec launches                 */
+    int checksum_vector;
+    uint64_t checksum_seed;
+} tfft_info;
+
+int tfft_plan_info(tfft_plan_t p, tfft_info *info);
+
+/*
+ * Per-kernel timing for measurement.  When enabled, tfft_exec records a CUDA
+ * event pair around every kernel it launches (on the exec stream).
+ * tfft_timing synchronises, adds the elapsed times up per kernel kind and
+ * clears the record.  kinds: 0 first pass, 1 middle pass, 2 last pass, 3 the
+ * single pass, 4 verify, 5 correction path.  Arrays have `nkinds` entries.
+ */
+int tfft_set_timing(tfft_plan_t p, int enable);
+int tfft_timing(tfft_plan_t p, double *ms_per_kind, int64_t *launches_per_kind, int nkinds);
+
+int tfft_destroy(tfft_plan_t p);
+
+/* Static string for a status code. */
+const char *tfft_error_string(int status);
+/* The last cudaError_t value seen by the library in this process. */
+int tfft_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TFFT_H */

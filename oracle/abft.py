@@ -8,8 +8,10 @@ Signals are split into checksum groups of G consecutive signals; inside a
 group b = 0..G-1.
 
 * Signal-side (left) encoding vector r: Wang's e_Wang, r_j = w3^j with
-  w3 = e^{-2 pi i/3} (Section II, "ABFT scheme").  Its image through the DFT
-  is the checksum vector w = W^T r = W r (W is symmetric).
+  w3 = e^{-2 pi i/3} (Section II, "ABFT scheme"), or a seeded random +-1
+  vector (the sign of bit 63 of output j of a SplitMix64 stream, Steele, Lea
+  and Flood, OOPSLA 2014).  Its image through the DFT is the checksum vector
+  w = W^T r = W r (W is symmetric).
 * Batch-side (right) encoding vectors: e_1 = ones and the index weights
   e_3 = (1, 2, ..., G) (Section III, "another encoding vector e_3").
 * Input checksums   S1 = w^T (X e_1),  S2 = w^T (X e_3).
@@ -44,6 +46,41 @@ def left_vector(n: int) -> np.ndarray:
     j = np.arange(n) % 3
     table = np.array([1.0 + 0j, W3, W3.conjugate()])   # w3^0, w3^1, w3^2
     return table[j]
+
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_MIX1 = np.uint64(0xBF58476D1CE4E5B9)
+_MIX2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
+    """Outputs start..start+count-1 of the SplitMix64 generator whose state
+    starts at `seed`: output k = mix(seed + (k+1) gamma) with the published
+    constants (gamma = 0x9E3779B97F4A7C15, multipliers 0xBF58476D1CE4E5B9 and
+    0x94D049BB133111EB, shifts 30, 27, 31), all arithmetic modulo 2^64."""
+    k = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + k * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _MIX1
+        z = (z ^ (z >> np.uint64(27))) * _MIX2
+    return z ^ (z >> np.uint64(31))
+
+
+def random_left_vector(n: int, seed: int) -> np.ndarray:
+    """r_k = +1 when bit 63 of SplitMix64 output k is 0, else -1."""
+    bits = splitmix64(seed, n) >> np.uint64(63)
+    return np.where(bits == 0, 1.0, -1.0).astype(np.complex128)
+
+
+def vectors(n: int, kind: str = "wang", seed: int = 0):
+    """(r, w) for kind 'wang' (e_Wang, w in closed form) or 'random'
+    (w = W r with the oracle FFT)."""
+    if kind == "wang":
+        return left_vector(n), checksum_vector_closed_form(n)
+    if kind == "random":
+        r = random_left_vector(n, seed)
+        return r, _fft(r)
+    raise ValueError(kind)
 
 
 def checksum_vector_closed_form(n: int) -> np.ndarray:
@@ -149,7 +186,7 @@ def verify_group(cs: GroupChecksums, n: int, g: int, u: float, kappa: float) -> 
                         tau=float(tau), quotient=q)
 
 
-def locate_nonfinite(xg: np.ndarray, yg: np.ndarray) -> int:
+def locate_nonfinite(xg: np.ndarray, yg: np.ndarray, r=None, w=None) -> int:
     """When the group residual is not finite (a value or a checksum sum
     overflowed) the quotient is undefined.  The faulty column is then the
     unique signal holding a non-finite value or, if every value is finite,
@@ -165,8 +202,8 @@ def locate_nonfinite(xg: np.ndarray, yg: np.ndarray) -> int:
         return -1
     n = yg.shape[1]
     scale = max(1.0, float(np.max(np.abs(yg))), float(np.max(np.abs(xg))))
-    r = left_vector(n)
-    w = checksum_vector_closed_form(n)
+    if r is None:
+        r, w = left_vector(n), checksum_vector_closed_form(n)
     res = [abs(r @ (yg[b] / scale) - w @ (xg[b] / scale)) for b in range(yg.shape[0])]
     return int(np.argmax(res))
 
@@ -191,16 +228,19 @@ class BatchResult:
     uncorrectable_groups: list
 
 
-def run(x: np.ndarray, y_faulty: np.ndarray, group: int, u: float, kappa: float) -> BatchResult:
+def run(x: np.ndarray, y_faulty: np.ndarray, group: int, u: float, kappa: float,
+        kind: str = "wang", seed: int = 0) -> BatchResult:
     """Apply the whole scheme to a batch: groups of ``group`` consecutive
-    signals (the last one may be shorter), detect, locate, correct."""
+    signals (the last one may be shorter), detect, locate, correct, with the
+    signal-side vector of ``kind`` (see :func:`vectors`)."""
     x = np.asarray(x, dtype=np.complex128)
     y = np.array(y_faulty, dtype=np.complex128, copy=True)
     bsz, n = x.shape
+    r, w = vectors(n, kind, seed)
     det, loc, unc = [], {}, []
     for g0 in range(0, bsz, group):
         g1 = min(bsz, g0 + group)
-        cs = group_checksums(x[g0:g1], y[g0:g1])
+        cs = group_checksums(x[g0:g1], y[g0:g1], w=w, r=r)
         v = verify_group(cs, n, g1 - g0, u, kappa)
         if not v.detected:
             continue
@@ -208,7 +248,7 @@ def run(x: np.ndarray, y_faulty: np.ndarray, group: int, u: float, kappa: float)
         det.append(gi)
         b = v.located
         if b < 0 and not (np.isfinite(cs.T1) and np.isfinite(cs.T2)):
-            b = locate_nonfinite(x[g0:g1], y[g0:g1])
+            b = locate_nonfinite(x[g0:g1], y[g0:g1], r, w)
         if b < 0:
             unc.append(gi)
             continue

@@ -1,0 +1,274 @@
+"""Python binding of the GB300 fault-tolerant batched FFT (``libtfft.so``).
+
+Argument marshalling only: every step of the transform, the checksum encode,
+verification and correction runs in the library's CUDA kernels.  The names
+mirror the C ABI of ``include/tfft.h``; tensors are accepted wherever the C
+function takes a device pointer (their ``data_ptr()`` is passed) and torch
+streams wherever it takes a ``cudaStream_t``.
+
+There is no CPU fallback: if ``libtfft.so`` cannot be loaded (and cannot be
+built because nvcc is absent) importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+from . import build as _build
+
+TFFT_C64, TFFT_C128 = 0, 1
+TFFT_ABFT_OFF, TFFT_ABFT_TWO_SIDED = 0, 2
+TFFT_R_RANDOM, TFFT_R_WANG = 0, 1
+TFFT_FAULT_NONE, TFFT_FAULT_BITFLIP, TFFT_FAULT_SCALE, TFFT_FAULT_ADD, TFFT_FAULT_ADD_PAIR = 0, 1, 2, 3, 4
+TIMING_KINDS = ("first_pass", "middle_pass", "last_pass", "single_pass", "verify", "correction")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TfftError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = lib().tfft_error_string(code).decode() if _lib is not None else str(code)
+        extra = ""
+        if code == -3 and _lib is not None:
+            extra = f" (cudaError {_lib.tfft_last_cuda_error()})"
+        super().__init__(f"{where}: {msg} [{code}]{extra}")
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("batch", ctypes.c_int64), ("dtype", ctypes.c_int),
+                ("abft_mode", ctypes.c_int), ("group", ctypes.c_int), ("kappa", ctypes.c_double),
+                ("detect_only", ctypes.c_int), ("max_faults", ctypes.c_int),
+                ("force_passes", ctypes.c_int), ("checksum_vector", ctypes.c_int),
+                ("checksum_seed", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("detected", ctypes.c_int64), ("corrected", ctypes.c_int64),
+                ("recomputed", ctypes.c_int64), ("uncorrectable", ctypes.c_int64),
+                ("execs", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("max_clean_ratio", ctypes.c_double)]
+
+
+class FaultEvent(ctypes.Structure):
+    _fields_ = [("exec_index", ctypes.c_int64), ("group", ctypes.c_int64), ("signal", ctypes.c_int64),
+                ("action", ctypes.c_int32), ("nonfinite", ctypes.c_int32), ("residual", ctypes.c_double),
+                ("tau", ctypes.c_double), ("q_re", ctypes.c_double), ("q_im", ctypes.c_double)]
+
+
+class Fault(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("pass_", ctypes.c_int), ("stage", ctypes.c_int),
+                ("bit", ctypes.c_int), ("signal", ctypes.c_int64), ("line", ctypes.c_int64),
+                ("index", ctypes.c_int64), ("factor", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("batch", ctypes.c_int64), ("dtype", ctypes.c_int),
+                ("abft_mode", ctypes.c_int), ("passes", ctypes.c_int), ("nsub", ctypes.c_int * 3),
+                ("stages", ctypes.c_int * 3), ("lines_per_tile", ctypes.c_int * 3),
+                ("lines_per_signal", ctypes.c_int64 * 3), ("group", ctypes.c_int),
+                ("max_faults", ctypes.c_int), ("kappa", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_int64), ("launches_per_exec", ctypes.c_int),
+                ("checksum_vector", ctypes.c_int), ("checksum_seed", ctypes.c_uint64)]
+
+
+def lib() -> ctypes.CDLL:
+    """Load (building first if needed) the CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not _build.up_to_date():
+                path = _build.build()
+            L = ctypes.CDLL(path)
+            P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            PP = ctypes.POINTER(ctypes.c_void_p)
+            sig = {
+                "tfft_plan": [PP, I64, I64, I, I],
+                "tfft_plan_ex": [PP, ctypes.POINTER(PlanOpts)],
+                "tfft_exec": [P, P, P, P],
+                "tfft_exec_host": [P, P, P, P],
+                "tfft_report": [P, ctypes.POINTER(I64), ctypes.POINTER(I64)],
+                "tfft_report_ex": [P, ctypes.POINTER(Stats)],
+                "tfft_reset_counters": [P],
+                "tfft_fault_log": [P, ctypes.POINTER(FaultEvent), I, ctypes.POINTER(I64)],
+                "tfft_set_fault": [P, ctypes.POINTER(Fault)],
+                "tfft_plan_info": [P, ctypes.POINTER(Info)],
+                "tfft_set_timing": [P, I],
+                "tfft_timing": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I],
+                "tfft_destroy": [P],
+                "tfft_error_string": [I],
+                "tfft_last_cuda_error": [],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = ctypes.c_char_p if name == "tfft_error_string" else ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    raise TypeError(f"not a stream: {type(s)}")
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != 0:
+        raise TfftError(rc, where)
+
+
+# ------------------------------------------------------------ C-ABI names
+def tfft_plan(n: int, batch: int, dtype: int = TFFT_C64, abft_mode: int = TFFT_ABFT_TWO_SIDED) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().tfft_plan(ctypes.byref(h), n, batch, dtype, abft_mode), "tfft_plan")
+    return h.value
+
+
+def tfft_plan_ex(n: int, batch: int, dtype: int = TFFT_C64, abft_mode: int = TFFT_ABFT_TWO_SIDED,
+                 group: int = 0, kappa: float = 0.0, detect_only: bool = False, max_faults: int = 0,
+                 force_passes: int = 0, checksum_vector: int = TFFT_R_RANDOM, checksum_seed: int = 0) -> int:
+    o = PlanOpts(n, batch, dtype, abft_mode, group, kappa, int(detect_only), max_faults, force_passes,
+                 checksum_vector, checksum_seed)
+    h = ctypes.c_void_p()
+    _check(lib().tfft_plan_ex(ctypes.byref(h), ctypes.byref(o)), "tfft_plan_ex")
+    return h.value
+
+
+def tfft_exec(plan: int, x, y, stream=None) -> None:
+    _check(lib().tfft_exec(plan, _ptr(x), _ptr(y), _stream(stream)), "tfft_exec")
+
+
+def tfft_exec_host(plan: int, host_in, host_out, stream=None) -> None:
+    _check(lib().tfft_exec_host(plan, _ptr(host_in), _ptr(host_out), _stream(stream)), "tfft_exec_host")
+
+
+def tfft_report(plan: int) -> tuple[int, int]:
+    d, c = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().tfft_report(plan, ctypes.byref(d), ctypes.byref(c)), "tfft_report")
+    return d.value, c.value
+
+
+def tfft_report_ex(plan: int) -> dict:
+    s = Stats()
+    _check(lib().tfft_report_ex(plan, ctypes.byref(s)), "tfft_report_ex")
+    return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+def tfft_reset_counters(plan: int) -> None:
+    _check(lib().tfft_reset_counters(plan), "tfft_reset_counters")
+
+
+def tfft_fault_log(plan: int, capacity: int = 1024) -> tuple[list, int]:
+    arr = (FaultEvent * max(1, capacity))()
+    tot = ctypes.c_int64()
+    _check(lib().tfft_fault_log(plan, arr, capacity, ctypes.byref(tot)), "tfft_fault_log")
+    n = min(capacity, tot.value)
+    return [{f: getattr(arr[k], f) for f, _ in FaultEvent._fields_} for k in range(n)], tot.value
+
+
+def tfft_set_fault(plan: int, mode: int, pass_: int = 0, stage: int = -1, signal: int = 0,
+                   line: int = 0, index: int = 0, bit: int = 0, factor: float = 0.0) -> None:
+    f = Fault(mode, pass_, stage, bit, signal, line, index, factor)
+    _check(lib().tfft_set_fault(plan, ctypes.byref(f)), "tfft_set_fault")
+
+
+def tfft_plan_info(plan: int) -> dict:
+    i = Info()
+    _check(lib().tfft_plan_info(plan, ctypes.byref(i)), "tfft_plan_info")
+    out = {}
+    for f, _ in Info._fields_:
+        v = getattr(i, f)
+        out[f] = list(v) if not isinstance(v, (int, float)) else v
+    return out
+
+
+def tfft_set_timing(plan: int, enable: bool) -> None:
+    _check(lib().tfft_set_timing(plan, int(enable)), "tfft_set_timing")
+
+
+def tfft_timing(plan: int) -> dict:
+    k = len(TIMING_KINDS)
+    ms = (ctypes.c_double * k)()
+    cnt = (ctypes.c_int64 * k)()
+    _check(lib().tfft_timing(plan, ms, cnt, k), "tfft_timing")
+    return {name: (ms[i], cnt[i]) for i, name in enumerate(TIMING_KINDS)}
+
+
+def tfft_destroy(plan: int) -> None:
+    _check(lib().tfft_destroy(plan), "tfft_destroy")
+
+
+def tfft_error_string(code: int) -> str:
+    return lib().tfft_error_string(code).decode()
+
+
+@dataclass
+class Plan:
+    """RAII holder of a plan handle (``with Plan(...) as p: p.exec(x, y)``)."""
+    n: int
+    batch: int
+    dtype: int = TFFT_C64
+    abft_mode: int = TFFT_ABFT_TWO_SIDED
+    group: int = 0
+    kappa: float = 0.0
+    detect_only: bool = False
+    max_faults: int = 0
+    force_passes: int = 0
+    checksum_vector: int = TFFT_R_RANDOM
+    checksum_seed: int = 0
+
+    def __post_init__(self):
+        self.handle = tfft_plan_ex(self.n, self.batch, self.dtype, self.abft_mode, self.group,
+                                   self.kappa, self.detect_only, self.max_faults, self.force_passes,
+                                   self.checksum_vector, self.checksum_seed)
+
+    def exec(self, x, y, stream=None):
+        tfft_exec(self.handle, x, y, stream)
+
+    def report(self):
+        return tfft_report_ex(self.handle)
+
+    def info(self):
+        return tfft_plan_info(self.handle)
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            tfft_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

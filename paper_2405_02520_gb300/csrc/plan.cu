@@ -1,0 +1,781 @@
+// plan.cu -- host side of the library: planner, FP64 twiddle and checksum
+// tables, workspace, the exec launch sequence and the C ABI of include/tfft.h.
+//
+// Plan (TurboFFT Section IV-A, "Tiled FFT" and "Kernel Parameters"): a signal
+// that fits one thread block's tile is transformed in one launch; a longer one
+// is viewed as an N1 x N2 (x N3) array and transformed by two (three)
+// launches, one per axis, the first ones writing in place and the last one
+// transposing into natural order (the four-step factorisation
+//   y[k1 + N1 k2] = sum_{n2} wN2^{n2 k2} wN^{n2 k1} sum_{n1} x[N2 n1 + n2] wN1^{n1 k1}).
+// Exec (Section III): pass kernels with the checksum encode fused into the
+// first and last pass, then verify, then the correction path, all on the
+// caller's stream with no host synchronisation.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tfft.h"
+#include "tfft_internal.h"
+
+using namespace tfft;
+
+namespace {
+
+std::atomic<int> g_last_cuda_error{0};
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda_error.store((int)e);
+  return TFFT_ERR_CUDA;
+}
+
+#define TFFT_CUDA(call)                       \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+// e^{-2 pi i m / n} in FP64: the integer m is reduced modulo n and split into
+// a quarter turn q and a remainder before any rounding, and the remaining
+// angle is taken from whichever of r, n - r keeps it below pi/4.
+void unit_root(int64_t m, int64_t n, double* re, double* im) {
+  m %= n;
+  if (m < 0) m += n;
+  const int64_t q = (4 * m) / n, r = 4 * m - q * n;       // theta = (pi/2)(q + r/n)
+  const double half_pi = 1.57079632679489661923132169163975144;
+  double c, s;
+  if (2 * r <= n) {
+    const double a = half_pi * (double)r / (double)n;
+    c = std::cos(a); s = std::sin(a);
+  } else {
+    const double a = half_pi * (double)(n - r) / (double)n;
+    c = std::sin(a); s = std::cos(a);
+  }
+  double x, y;   // e^{+i theta}
+  switch (q & 3) {
+    case 0: x = c; y = s; break;
+    case 1: x = -s; y = c; break;
+    case 2: x = -c; y = -s; break;
+    default: x = s; y = -c; break;
+  }
+  *re = x;
+  *im = -y;
+}
+
+int ilog2(int64_t v) { int k = 0; while ((int64_t(1) << k) < v) k++; return k; }
+bool is_pow2(int64_t v) { return v >= 1 && (v & (v - 1)) == 0; }
+
+struct PassPlan {
+  int nsub = 1, E = 1, C = 1, nthreads = 32, nstages = 1, pitch = 1;
+  int in_map = MAP_ROW, mid_map = MAP_ROW, out_map = MAP_ROW;
+  int lines_are_signals = 0, twiddle = 0, parts = 1;
+  int64_t LO = 1, HI = 1, line_blocks = 1;
+  int64_t in_es = 1, in_lo = 0, in_hi = 0, out_es = 1, out_lo = 0, out_hi = 0;
+  int64_t tw_scale = 1;
+  size_t smem = 0;
+  int bps = 1;       // resident blocks per SM
+};
+
+struct TimedLaunch {
+  cudaEvent_t a, b;
+  int kind;
+};
+
+}  // namespace
+
+struct tfft_plan_s {
+  int64_t n = 0, batch = 0;
+  int dtype = 0, abft = 0;
+  int G = 16;
+  double kappa = 4.0;
+  int rvec = RVEC_RANDOM;
+  unsigned long long rseed = 20240502ull;
+  void* wtab = nullptr;
+  int detect_only = 0;
+  int cap_fix = 1, cap_rec = 1;
+  int passes = 1;
+  PassPlan pp[3];
+  int64_t ngroups = 0;
+  int device = 0, sms = 1;
+  size_t esize = 8;
+
+  void* tw_sub = nullptr; int tw_sub_n = 1;
+  void* twN_lo = nullptr; void* twN_hi = nullptr; int twN_lbits = 0;
+  void* wt_lo = nullptr; void* wt_hi = nullptr; int wt_lbits = 0;
+  void* tmp = nullptr;
+  RecIn* rec_in = nullptr; RecOut* rec_out = nullptr;
+  int64_t slots_in = 1, slots_out = 1;
+  long long* lists_mem = nullptr;
+  Lists lists{};
+  Counters* counters = nullptr;
+  LogEvent* log = nullptr;
+  void* ws_c1 = nullptr; void* ws_acc = nullptr;
+  void* stage_in = nullptr; void* stage_out = nullptr;
+
+  FaultSite pending{};
+  int64_t execs = 0, launches = 0;
+  cudaStream_t last_stream = nullptr;
+  bool used = false;
+  int timing = 0;
+  std::vector<TimedLaunch> timed;
+  std::vector<cudaEvent_t> event_pool;
+  int64_t workspace_bytes = 0;
+  std::mutex mu;
+};
+
+namespace {
+
+template <typename real>
+struct HostC { real x, y; };
+
+template <typename real>
+int upload_table(void** dst, const std::vector<double>& re, const std::vector<double>& im, int64_t* bytes) {
+  std::vector<HostC<real>> h(re.size());
+  for (size_t i = 0; i < re.size(); i++) h[i] = HostC<real>{(real)re[i], (real)im[i]};
+  const size_t b = h.size() * sizeof(HostC<real>);
+  TFFT_CUDA(cudaMalloc(dst, std::max<size_t>(b, 16)));
+  TFFT_CUDA(cudaMemcpy(*dst, h.data(), b, cudaMemcpyHostToDevice));
+  *bytes += (int64_t)b;
+  return 0;
+}
+
+int upload(tfft_plan_s* p, void** dst, const std::vector<double>& re, const std::vector<double>& im) {
+  return p->dtype == TFFT_C64 ? upload_table<float>(dst, re, im, &p->workspace_bytes)
+                              : upload_table<double>(dst, re, im, &p->workspace_bytes);
+}
+
+void free_plan(tfft_plan_s* p) {
+  void* bufs[] = {p->tw_sub, p->twN_lo, p->twN_hi, p->wt_lo, p->wt_hi, p->wtab, p->tmp, p->rec_in, p->rec_out,
+                  p->lists_mem, p->counters, p->log, p->ws_c1, p->ws_acc, p->stage_in, p->stage_out};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (auto& t : p->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+  for (auto e : p->event_pool) cudaEventDestroy(e);
+  delete p;
+}
+
+int pass_attrs(const tfft_plan_s* p, PassPlan& q) {
+  cudaError_t e = p->dtype == TFFT_C64 ? pass_func_attrs_f32(q.E, q.smem, q.nthreads, &q.bps)
+                                       : pass_func_attrs_f64(q.E, q.smem, q.nthreads, &q.bps);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (q.bps < 1) return TFFT_ERR_UNSUPPORTED;
+  return 0;
+}
+
+// Elements per thread for a sub-transform of length nsub: the full radix E0
+// unless the line is so short that fewer than four threads would share it.
+int pick_E(int nsub, int E0) {
+  int E = std::min(E0, nsub);
+  while (E > 2 && nsub / E < 4) E /= 2;
+  return std::max(E, 1);
+}
+
+int row_pad(int nsub, int E, int S) {
+  const int lanes = std::max(1, nsub / E);
+  return lanes < S ? lanes : 0;
+}
+
+int col_pad(int C, int S) { return C < S ? S / C : 1; }
+
+int nstages_of(int nsub, int E) {
+  if (nsub <= 1) return 1;
+  int s = 0;
+  int64_t v = 1;
+  while (v < nsub) { v *= E; s++; }
+  return std::max(s, 1);
+}
+
+int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
+  const int64_t n = o->n;
+  const bool c64 = o->dtype == TFFT_C64;
+  p->esize = c64 ? 8 : 16;
+  const int E0 = c64 ? 16 : 8;
+  const int TILE = c64 ? 4096 : 2048;        // elements of one thread block's tile
+  const int S = c64 ? 16 : 8;                // elements per 128-byte shared-memory row
+  const int CMIN = c64 ? 8 : 4;              // lines per tile for 64-byte column runs
+  const int NSUBMAX = TILE / CMIN;
+
+  int passes;
+  if (o->force_passes) passes = o->force_passes;
+  else if (n <= TILE) passes = 1;
+  else if (n <= (int64_t)NSUBMAX * NSUBMAX) passes = 2;
+  else passes = 3;
+  const int m = ilog2(n);
+  int mf[3] = {m, 0, 0};
+  if (passes == 2) { mf[0] = (m + 1) / 2; mf[1] = m - mf[0]; }
+  if (passes == 3) { mf[0] = (m + 2) / 3; mf[1] = (m - mf[0] + 1) / 2; mf[2] = m - mf[0] - mf[1]; }
+  if (passes == 1 && n > TILE) return TFFT_ERR_INVALID_ARG;
+  for (int i = 1; i < passes; i++)
+    if (mf[i] < 1) return TFFT_ERR_INVALID_ARG;
+  if (passes > 1)
+    for (int i = 0; i < passes; i++)
+      if ((int64_t(1) << mf[i]) > NSUBMAX) return TFFT_ERR_INVALID_ARG;
+  p->passes = passes;
+
+  int G = o->group > 0 ? o->group : 16;
+
+  if (passes == 1) {
+    PassPlan& q = p->pp[0];
+    q.nsub = (int)n;
+    q.E = pick_E(q.nsub, E0);
+    q.lines_are_signals = 1;
+    int C = std::max(1, TILE / q.nsub);
+    while (C > 1 && (G % C != 0 || C > G)) C >>= 1;   // tiles never straddle groups
+    while ((int64_t)C * q.nsub / q.E < 32) C <<= 1;  // at least one full warp
+    if (C > G) G = C;                                 // tiny n: group grows to the tile
+    q.C = C;
+    q.in_map = q.mid_map = q.out_map = MAP_ROW;
+    q.in_es = q.out_es = 1;
+    q.pitch = q.nsub + row_pad(q.nsub, q.E, S);
+  } else {
+    const int64_t N1 = int64_t(1) << mf[0];
+    const int64_t M = n / N1;
+    // first pass: columns n_rest of length N1, stride M, twiddle wN^{n_rest k1}
+    PassPlan& a = p->pp[0];
+    a.nsub = (int)N1; a.E = pick_E(a.nsub, E0);
+    a.LO = M; a.HI = 1;
+    a.C = (int)std::min<int64_t>(std::min<int64_t>(TILE / N1, M), 64);
+    a.in_es = M; a.in_lo = 1; a.out_es = M; a.out_lo = 1;
+    a.in_map = a.mid_map = a.out_map = MAP_COL;
+    a.twiddle = 1; a.tw_scale = 1;
+    a.pitch = a.nsub + col_pad(a.C, S);
+    if (passes == 2) {
+      PassPlan& b = p->pp[1];
+      const int64_t N2 = M;
+      b.nsub = (int)N2; b.E = pick_E(b.nsub, E0);
+      b.LO = N1; b.HI = 1;
+      b.C = (int)std::min<int64_t>(std::min<int64_t>(TILE / N2, N1), 64);
+      b.in_es = 1; b.in_lo = N2; b.out_es = N1; b.out_lo = 1;
+      b.in_map = MAP_ROW; b.out_map = MAP_COL; b.mid_map = b.C >= S / 2 ? MAP_COL : MAP_ROW;
+      b.pitch = b.nsub + (b.mid_map == MAP_COL ? col_pad(b.C, S) : row_pad(b.nsub, b.E, S));
+    } else {
+      const int64_t N2 = int64_t(1) << mf[1], N3 = int64_t(1) << mf[2];
+      PassPlan& b = p->pp[1];           // lines (k1, n3) over n2, stride N3
+      b.nsub = (int)N2; b.E = pick_E(b.nsub, E0);
+      b.LO = N3; b.HI = N1;
+      b.C = (int)std::min<int64_t>(std::min<int64_t>(TILE / N2, N3), 64);
+      b.in_es = N3; b.in_lo = 1; b.in_hi = M;
+      b.out_es = N3; b.out_lo = 1; b.out_hi = M;
+      b.in_map = b.mid_map = b.out_map = MAP_COL;
+      b.twiddle = 1; b.tw_scale = N1;    // wM^{n3 k2} = wN^{N1 n3 k2}
+      b.pitch = b.nsub + col_pad(b.C, S);
+      PassPlan& c = p->pp[2];           // lines (k1, k2) over n3, contiguous; store transposed
+      c.nsub = (int)N3; c.E = pick_E(c.nsub, E0);
+      c.LO = N1; c.HI = N2;
+      c.C = (int)std::min<int64_t>(std::min<int64_t>(TILE / N3, N1), 64);
+      c.in_es = 1; c.in_lo = M; c.in_hi = N3;
+      c.out_es = N1 * N2; c.out_lo = 1; c.out_hi = N1;
+      c.in_map = MAP_ROW; c.out_map = MAP_COL; c.mid_map = c.C >= S / 2 ? MAP_COL : MAP_ROW;
+      c.pitch = c.nsub + (c.mid_map == MAP_COL ? col_pad(c.C, S) : row_pad(c.nsub, c.E, S));
+    }
+  }
+  p->G = G;
+  p->ngroups = (p->batch + G - 1) / G;
+
+  for (int i = 0; i < passes; i++) {
+    PassPlan& q = p->pp[i];
+    q.nthreads = (int)((int64_t)q.C * q.nsub / q.E);
+    if (q.nthreads < 32 || q.nthreads > 512 || q.nthreads % 32 != 0) return TFFT_ERR_UNSUPPORTED;
+    q.nstages = nstages_of(q.nsub, q.E);
+    q.smem = (size_t)q.C * q.pitch * p->esize;
+    q.line_blocks = q.lines_are_signals ? 1 : q.LO * q.HI / q.C;
+    int rc = pass_attrs(p, q);
+    if (rc) return rc;
+  }
+  // chunks per group: enough thread blocks to fill the GPU when groups are few
+  for (int i = 0; i < passes; i++) {
+    PassPlan& q = p->pp[i];
+    const int64_t target = (int64_t)2 * p->sms * q.bps;
+    const int64_t base = p->ngroups * q.line_blocks;
+    const int64_t tiles_per_group = q.lines_are_signals ? std::max<int64_t>(1, G / q.C) : G;
+    q.parts = 1;
+    if (base < target) q.parts = (int)std::min<int64_t>(tiles_per_group, (target + base - 1) / base);
+  }
+  p->slots_in = (int64_t)p->pp[0].parts * p->pp[0].line_blocks;
+  p->slots_out = (int64_t)p->pp[passes - 1].parts * p->pp[passes - 1].line_blocks;
+  return 0;
+}
+
+int plan_tables(tfft_plan_s* p) {
+  const int64_t n = p->n;
+  int rc;
+  // stage twiddles: omega_T^m, T = the longest sub-transform
+  int T = 1;
+  for (int i = 0; i < p->passes; i++) T = std::max(T, p->pp[i].nsub);
+  p->tw_sub_n = T;
+  {
+    std::vector<double> re(T), im(T);
+    for (int m = 0; m < T; m++) unit_root(m, T, &re[m], &im[m]);
+    if ((rc = upload(p, &p->tw_sub, re, im))) return rc;
+  }
+  // omega_N^m two-level table (inter-pass twiddles)
+  {
+    const int lb = (ilog2(n) + 1) / 2;
+    p->twN_lbits = lb;
+    const int64_t L = int64_t(1) << lb, H = std::max<int64_t>(1, (n + L - 1) / L);
+    std::vector<double> re(L), im(L), hre(H), him(H);
+    for (int64_t m = 0; m < L; m++) unit_root(m, n, &re[m], &im[m]);
+    for (int64_t h = 0; h < H; h++) unit_root(h * L, n, &hre[h], &him[h]);
+    if ((rc = upload(p, &p->twN_lo, re, im))) return rc;
+    if ((rc = upload(p, &p->twN_hi, hre, him))) return rc;
+  }
+  // e^{i pi m / (3N)}, 0 <= m <= 3N/2 (checksum weights), two-level
+  {
+    const int64_t mmax = 3 * n / 2 + 1;
+    const int lb = (ilog2(mmax) + 1) / 2;
+    p->wt_lbits = lb;
+    const int64_t L = int64_t(1) << lb, H = (mmax + L - 1) / L + 1;
+    const double pi = 3.14159265358979323846264338327950288;
+    std::vector<double> re(L), im(L), hre(H), him(H);
+    for (int64_t m = 0; m < L; m++) {
+      const double a = pi * (double)m / (3.0 * (double)n);
+      re[m] = std::cos(a); im[m] = std::sin(a);
+    }
+    for (int64_t h = 0; h < H; h++) {
+      const double a = pi * (double)(h * L) / (3.0 * (double)n);
+      hre[h] = std::cos(a); him[h] = std::sin(a);
+    }
+    if ((rc = upload(p, &p->wt_lo, re, im))) return rc;
+    if ((rc = upload(p, &p->wt_hi, hre, him))) return rc;
+  }
+  return 0;
+}
+
+// w = W r for the random signal-side vector, computed on the device by an
+// internal complex128 plan of the same length (FP64 accurate), then rounded
+// to the plan's element type.
+int plan_wtable(tfft_plan_s* p) {
+  if (!p->abft || p->rvec != RVEC_RANDOM) return 0;
+  const int64_t n = p->n;
+  void* r = nullptr; void* w = nullptr;
+  TFFT_CUDA(cudaMalloc(&r, n * 16));
+  TFFT_CUDA(cudaMalloc(&w, n * 16));
+  cudaError_t e = launch_gen_signs(r, n, p->rseed, nullptr);
+  if (e != cudaSuccess) { cudaFree(r); cudaFree(w); return cuda_fail(e); }
+  tfft_plan_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.n = n; o.batch = 1; o.dtype = TFFT_C128; o.abft_mode = TFFT_ABFT_OFF;
+  tfft_plan_t q = nullptr;
+  int rc = tfft_plan_ex(&q, &o);
+  if (!rc) rc = tfft_exec(q, r, w, nullptr);
+  if (!rc) {
+    e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+  }
+  if (q) tfft_destroy(q);
+  cudaFree(r);
+  if (rc) { cudaFree(w); return rc; }
+  if (p->dtype == TFFT_C64) {
+    void* w32 = nullptr;
+    e = cudaMalloc(&w32, n * 8);
+    if (e == cudaSuccess) e = launch_c128_to_c64(w, w32, n, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    cudaFree(w);
+    if (e != cudaSuccess) { if (w32) cudaFree(w32); return cuda_fail(e); }
+    p->wtab = w32;
+    p->workspace_bytes += n * 8;
+  } else {
+    p->wtab = w;
+    p->workspace_bytes += n * 16;
+  }
+  return 0;
+}
+
+int plan_workspace(tfft_plan_s* p) {
+  const size_t sig = (size_t)p->n * p->esize;
+  // correction slots: at most 8, within a 1 GiB budget for c1 and the partial sum
+  if (p->cap_fix <= 0) {
+    int64_t cap = (int64_t(1) << 30) / (int64_t)(2 * sig);
+    p->cap_fix = (int)std::max<int64_t>(1, std::min<int64_t>(8, cap));
+  }
+  p->cap_fix = (int)std::min<int64_t>(p->cap_fix, std::max<int64_t>(1, p->ngroups));
+  p->cap_rec = (int)std::min<int64_t>(8, std::max<int64_t>(1, p->ngroups));
+  if (p->passes > 1) {
+    const int64_t rows = std::max<int64_t>(p->batch, p->abft ? p->cap_fix : 0);
+    TFFT_CUDA(cudaMalloc(&p->tmp, rows * sig));
+    p->workspace_bytes += rows * (int64_t)sig;
+  }
+  const size_t nl = (size_t)(2 + p->cap_fix + p->cap_fix + p->cap_rec);
+  TFFT_CUDA(cudaMalloc(&p->lists_mem, nl * sizeof(long long)));
+  TFFT_CUDA(cudaMemset(p->lists_mem, 0, nl * sizeof(long long)));
+  p->lists.fix = p->lists_mem;
+  p->lists.fix_signal = p->lists_mem + 1 + p->cap_fix;
+  p->lists.rec = p->lists_mem + 1 + 2 * p->cap_fix;
+  p->lists.cap_fix = p->cap_fix;
+  p->lists.cap_rec = p->cap_rec;
+  TFFT_CUDA(cudaMalloc(&p->counters, sizeof(Counters)));
+  TFFT_CUDA(cudaMemset(p->counters, 0, sizeof(Counters)));
+  TFFT_CUDA(cudaMalloc(&p->log, sizeof(LogEvent) * kLogRing));
+  TFFT_CUDA(cudaMemset(p->log, 0, sizeof(LogEvent) * kLogRing));
+  p->workspace_bytes += nl * sizeof(long long) + sizeof(Counters) + sizeof(LogEvent) * kLogRing;
+  if (p->abft) {
+    TFFT_CUDA(cudaMalloc(&p->rec_in, sizeof(RecIn) * p->ngroups * p->slots_in));
+    TFFT_CUDA(cudaMalloc(&p->rec_out, sizeof(RecOut) * p->ngroups * p->slots_out));
+    TFFT_CUDA(cudaMalloc(&p->ws_c1, p->cap_fix * sig));
+    TFFT_CUDA(cudaMalloc(&p->ws_acc, p->cap_fix * sig));
+    p->workspace_bytes += sizeof(RecIn) * p->ngroups * p->slots_in +
+                          sizeof(RecOut) * p->ngroups * p->slots_out + 2 * p->cap_fix * (int64_t)sig;
+  }
+  return 0;
+}
+
+// ------------------------------------------------------------------ exec
+PassParams base_params(const tfft_plan_s* p, int i) {
+  const PassPlan& q = p->pp[i];
+  PassParams a;
+  std::memset(&a, 0, sizeof(a));
+  a.nsub = q.nsub; a.log2nsub = ilog2(q.nsub); a.C = q.C; a.nthreads = q.nthreads;
+  a.nstages = q.nstages; a.pitch = q.pitch; a.lines_are_signals = q.lines_are_signals;
+  a.in_map = q.in_map; a.mid_map = q.mid_map; a.out_map = q.out_map; a.pass_index = i;
+  a.n = p->n; a.batch = p->batch; a.LO = q.LO; a.HI = q.HI;
+  a.in_es = q.in_es; a.in_lo = q.in_lo; a.in_hi = q.in_hi;
+  a.out_es = q.out_es; a.out_lo = q.out_lo; a.out_hi = q.out_hi;
+  a.tw_sub = p->tw_sub; a.tw_sub_stride = p->tw_sub_n / q.nsub;
+  a.twiddle = q.twiddle; a.tw_scale = q.tw_scale;
+  a.twN_lo = p->twN_lo; a.twN_hi = p->twN_hi; a.twN_lbits = p->twN_lbits;
+  a.group = p->G; a.parts = q.parts; a.ngroups = p->ngroups; a.line_blocks = q.line_blocks;
+  a.wt_lo = p->wt_lo; a.wt_hi = p->wt_hi; a.wt_lbits = p->wt_lbits;
+  const int nmod3 = (int)(p->n % 3);          // K = 1 - w3^N, w3 = e^{-2 pi i/3}
+  a.wk_re = 1.5;
+  a.wk_im = nmod3 == 1 ? 0.86602540378443864676 : (nmod3 == 2 ? -0.86602540378443864676 : 0.0);
+  if (nmod3 == 0) a.wk_re = 0.0;
+  a.rvec = p->rvec; a.rseed = p->rseed; a.wtab = p->wtab;
+  a.nchunks = p->ngroups * q.parts * q.line_blocks;
+  return a;
+}
+
+int launch_pass(tfft_plan_s* p, const PassParams& a, int i, int kind, cudaStream_t s) {
+  const PassPlan& q = p->pp[i];
+  const int64_t maxgrid = (int64_t)p->sms * q.bps;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.nchunks, maxgrid));
+  TimedLaunch tl{};
+  if (p->timing) {
+    tl.kind = kind;
+    TFFT_CUDA(cudaEventCreate(&tl.a)); TFFT_CUDA(cudaEventCreate(&tl.b));
+    TFFT_CUDA(cudaEventRecord(tl.a, s));
+  }
+  cudaError_t e = p->dtype == TFFT_C64 ? launch_pass_f32(a, q.E, grid, q.smem, s)
+                                       : launch_pass_f64(a, q.E, grid, q.smem, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  p->launches++;
+  if (p->timing) {
+    TFFT_CUDA(cudaEventRecord(tl.b, s));
+    p->timed.push_back(tl);
+  }
+  return 0;
+}
+
+template <typename F>
+int timed_launch(tfft_plan_s* p, int kind, cudaStream_t s, F&& f) {
+  TimedLaunch tl{};
+  if (p->timing) {
+    tl.kind = kind;
+    TFFT_CUDA(cudaEventCreate(&tl.a)); TFFT_CUDA(cudaEventCreate(&tl.b));
+    TFFT_CUDA(cudaEventRecord(tl.a, s));
+  }
+  cudaError_t e = f();
+  if (e != cudaSuccess) return cuda_fail(e);
+  p->launches++;
+  if (p->timing) {
+    TFFT_CUDA(cudaEventRecord(tl.b, s));
+    p->timed.push_back(tl);
+  }
+  return 0;
+}
+
+int kind_of(const tfft_plan_s* p, int i) {
+  if (p->passes == 1) return 3;
+  if (i == 0) return 0;
+  return i == p->passes - 1 ? 2 : 1;
+}
+
+// Run the passes from `in` to `out` (through tmp when there are several).
+int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool main_exec,
+               const long long* list, int list_identity, int list_cap, int64_t list_block,
+               int64_t batch, int kind_override) {
+  for (int i = 0; i < p->passes; i++) {
+    PassParams a = base_params(p, i);
+    a.batch = batch;
+    a.in = (i == 0) ? in : p->tmp;
+    a.out = (i == p->passes - 1) ? out : p->tmp;
+    if (main_exec) {
+      a.abft_in = p->abft && i == 0;
+      a.abft_out = p->abft && i == p->passes - 1;
+      a.slots = (i == 0) ? p->slots_in : p->slots_out;
+      if (p->passes == 1) a.slots = p->slots_in;
+      a.rec_in = p->rec_in; a.rec_out = p->rec_out;
+      a.fault = p->pending;
+      if (i == 0 && p->abft) { a.zero_on_entry[0] = p->lists.fix; a.zero_on_entry[1] = p->lists.rec; }
+    } else {
+      a.list = list; a.list_identity = list_identity; a.list_cap = list_cap;
+      a.list_block = list_block;
+      a.ngroups = list_cap;
+      a.parts = 1;
+      a.nchunks = (int64_t)list_cap * p->pp[i].line_blocks;
+    }
+    int rc = launch_pass(p, a, i, kind_override >= 0 ? kind_override : kind_of(p, i), s);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
+  int rc = run_passes(p, in, out, s, true, nullptr, 0, 0, 0, p->batch, -1);
+  if (rc) return rc;
+  if (p->abft) {
+    VerifyParams v{};
+    v.n = p->n; v.batch = p->batch; v.group = p->G; v.ngroups = p->ngroups;
+    v.slots_in = p->slots_in; v.slots_out = p->slots_out;
+    v.rec_in = p->rec_in; v.rec_out = p->rec_out;
+    const double u = p->dtype == TFFT_C64 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    const int lg = std::max(1, ilog2(p->n));
+    v.kappa_u_log2n_sqrtn = p->kappa * u * lg * std::sqrt((double)p->n);
+    v.detect_only = p->detect_only;
+    v.lists = p->lists; v.counters = p->counters; v.log = p->log; v.exec_index = p->execs;
+    if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
+    FixParams f{};
+    f.n = p->n; f.batch = p->batch; f.group = p->G; f.dtype = p->dtype;
+    f.in = in; f.out = out; f.ws_c1 = p->ws_c1; f.ws_acc = p->ws_acc; f.lists = p->lists;
+    if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_gather(f, s); }))) return rc;
+    // W X e_1 of every queued group, in place in ws_c1
+    if ((rc = run_passes(p, p->ws_c1, p->ws_c1, s, false, p->lists.fix, 1, p->cap_fix, 1,
+                         p->cap_fix, 5)))
+      return rc;
+    if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_apply(f, s); }))) return rc;
+    // groups that could not be located: recompute from the input
+    if ((rc = run_passes(p, in, out, s, false, p->lists.rec, 0, p->cap_rec, p->G, p->batch, 5)))
+      return rc;
+  }
+  return 0;
+}
+
+bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
+  if (!out || !o) return TFFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!is_pow2(o->n) || o->n > (int64_t(1) << 26) || o->batch < 1) return TFFT_ERR_INVALID_ARG;
+  if (o->dtype != TFFT_C64 && o->dtype != TFFT_C128) return TFFT_ERR_UNSUPPORTED;
+  if (o->abft_mode != TFFT_ABFT_OFF && o->abft_mode != TFFT_ABFT_TWO_SIDED) return TFFT_ERR_UNSUPPORTED;
+  if (o->group < 0 || o->kappa < 0 || o->max_faults < 0 || o->force_passes < 0 || o->force_passes > 3)
+    return TFFT_ERR_INVALID_ARG;
+  if (o->checksum_vector != TFFT_R_RANDOM && o->checksum_vector != TFFT_R_WANG) return TFFT_ERR_INVALID_ARG;
+  int dev = 0, count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) return TFFT_ERR_NO_DEVICE;
+  TFFT_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  TFFT_CUDA(cudaGetDeviceProperties(&prop, dev));
+  if (!(prop.major == 10 && prop.minor == 3)) return TFFT_ERR_NO_DEVICE;
+
+  tfft_plan_s* p = new (std::nothrow) tfft_plan_s();
+  if (!p) return TFFT_ERR_ALLOC;
+  p->n = o->n; p->batch = o->batch; p->dtype = o->dtype; p->abft = o->abft_mode == TFFT_ABFT_TWO_SIDED;
+  p->kappa = o->kappa > 0 ? o->kappa : 4.0;
+  p->detect_only = o->detect_only ? 1 : 0;
+  p->cap_fix = o->max_faults;
+  p->rvec = o->checksum_vector == TFFT_R_WANG ? RVEC_WANG : RVEC_RANDOM;
+  if (o->checksum_seed) p->rseed = (unsigned long long)o->checksum_seed;
+  p->device = dev;
+  p->sms = prop.multiProcessorCount;
+  int rc = plan_build(p, o);
+  if (!rc) rc = plan_tables(p);
+  if (!rc) rc = plan_workspace(p);
+  if (!rc) rc = plan_wtable(p);
+  if (rc) { free_plan(p); return rc; }
+  *out = p;
+  return TFFT_SUCCESS;
+}
+
+int tfft_plan(tfft_plan_t* out, int64_t n, int64_t batch, int dtype, int abft_mode) {
+  tfft_plan_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.n = n; o.batch = batch; o.dtype = dtype; o.abft_mode = abft_mode;
+  return tfft_plan_ex(out, &o);
+}
+
+int tfft_exec(tfft_plan_t p, const void* in, void* out, tfft_stream_t stream) {
+  if (!p || !in || !out || !aligned16(in) || !aligned16(out)) return TFFT_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)p->batch * p->n * p->esize;
+  const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
+  if (p->abft && a < b + bytes && b < a + bytes) return TFFT_ERR_INPLACE;
+  std::lock_guard<std::mutex> lk(p->mu);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = exec_device(p, in, out, s);
+  p->pending = FaultSite{};     // an armed fault lasts one exec
+  p->execs++;
+  p->last_stream = s;
+  p->used = true;
+  return rc;
+}
+
+int tfft_exec_host(tfft_plan_t p, const void* host_in, void* host_out, tfft_stream_t stream) {
+  if (!p || !host_in || !host_out) return TFFT_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)p->batch * p->n * p->esize;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!p->stage_in) {
+    TFFT_CUDA(cudaMalloc(&p->stage_in, bytes));
+    TFFT_CUDA(cudaMalloc(&p->stage_out, bytes));
+  }
+  TFFT_CUDA(cudaMemcpyAsync(p->stage_in, host_in, bytes, cudaMemcpyHostToDevice, s));
+  int rc = tfft_exec(p, p->stage_in, p->stage_out, stream);
+  if (rc) return rc;
+  TFFT_CUDA(cudaMemcpyAsync(host_out, p->stage_out, bytes, cudaMemcpyDeviceToHost, s));
+  TFFT_CUDA(cudaStreamSynchronize(s));
+  return TFFT_SUCCESS;
+}
+
+int tfft_report_ex(tfft_plan_t p, tfft_stats* st) {
+  if (!p || !st) return TFFT_ERR_INVALID_ARG;
+  if (p->used) TFFT_CUDA(cudaStreamSynchronize(p->last_stream));
+  Counters c;
+  TFFT_CUDA(cudaMemcpy(&c, p->counters, sizeof(c), cudaMemcpyDeviceToHost));
+  st->detected = (int64_t)c.detected;
+  st->corrected = (int64_t)c.corrected;
+  st->recomputed = (int64_t)c.recomputed;
+  st->uncorrectable = (int64_t)c.uncorrectable;
+  st->execs = p->execs;
+  st->launches = p->launches;
+  double ratio;
+  std::memcpy(&ratio, &c.max_clean_ratio_bits, sizeof(ratio));
+  st->max_clean_ratio = ratio;
+  return TFFT_SUCCESS;
+}
+
+int tfft_report(tfft_plan_t p, int64_t* detected, int64_t* corrected) {
+  tfft_stats st;
+  int rc = tfft_report_ex(p, &st);
+  if (rc) return rc;
+  if (detected) *detected = st.detected;
+  if (corrected) *corrected = st.corrected + st.recomputed;
+  return TFFT_SUCCESS;
+}
+
+int tfft_reset_counters(tfft_plan_t p) {
+  if (!p) return TFFT_ERR_INVALID_ARG;
+  if (p->used) TFFT_CUDA(cudaStreamSynchronize(p->last_stream));
+  TFFT_CUDA(cudaMemset(p->counters, 0, sizeof(Counters)));
+  p->execs = 0;
+  p->launches = 0;
+  return TFFT_SUCCESS;
+}
+
+int tfft_fault_log(tfft_plan_t p, tfft_fault_event* ev, int capacity, int64_t* total) {
+  if (!p || capacity < 0 || (capacity > 0 && !ev)) return TFFT_ERR_INVALID_ARG;
+  if (p->used) TFFT_CUDA(cudaStreamSynchronize(p->last_stream));
+  Counters c;
+  TFFT_CUDA(cudaMemcpy(&c, p->counters, sizeof(c), cudaMemcpyDeviceToHost));
+  std::vector<LogEvent> ring(kLogRing);
+  TFFT_CUDA(cudaMemcpy(ring.data(), p->log, sizeof(LogEvent) * kLogRing, cudaMemcpyDeviceToHost));
+  const int64_t tot = (int64_t)c.log_total;
+  if (total) *total = tot;
+  const int64_t avail = std::min<int64_t>(tot, kLogRing);
+  const int64_t take = std::min<int64_t>(avail, capacity);
+  for (int64_t k = 0; k < take; k++) {
+    const LogEvent& e = ring[(tot - take + k) % kLogRing];
+    ev[k].exec_index = e.exec_index; ev[k].group = e.group; ev[k].signal = e.signal;
+    ev[k].action = e.action; ev[k].nonfinite = e.nonfinite;
+    ev[k].residual = e.residual; ev[k].tau = e.tau; ev[k].q_re = e.q_re; ev[k].q_im = e.q_im;
+  }
+  return TFFT_SUCCESS;
+}
+
+int tfft_set_fault(tfft_plan_t p, const tfft_fault* f) {
+  if (!p || !f) return TFFT_ERR_INVALID_ARG;
+  if (f->mode < 0 || f->mode > 4) return TFFT_ERR_INVALID_ARG;
+  if (f->mode != 0) {
+    if (f->pass < 0 || f->pass >= p->passes) return TFFT_ERR_INVALID_ARG;
+    if (f->stage < -1 || f->stage >= p->pp[f->pass].nstages) return TFFT_ERR_INVALID_ARG;
+    if (f->signal < 0 || f->signal >= p->batch || (f->mode == 4 && f->signal + 1 >= p->batch))
+      return TFFT_ERR_INVALID_ARG;
+    if (f->index < 0 || f->index >= p->pp[f->pass].nsub) return TFFT_ERR_INVALID_ARG;
+    const int64_t lps = p->pp[f->pass].lines_are_signals ? 1 : p->pp[f->pass].LO * p->pp[f->pass].HI;
+    if (f->line < 0 || f->line >= lps) return TFFT_ERR_INVALID_ARG;
+    const int w = p->dtype == TFFT_C64 ? 32 : 64;
+    if (f->mode == 1 && (f->bit < 0 || f->bit >= 2 * w)) return TFFT_ERR_INVALID_ARG;
+  }
+  FaultSite s{};
+  s.mode = f->mode; s.pass = f->pass; s.stage = f->stage; s.bit = f->bit;
+  s.signal = f->signal; s.line = f->line; s.index = f->index; s.factor = f->factor;
+  std::lock_guard<std::mutex> lk(p->mu);
+  p->pending = s;
+  return TFFT_SUCCESS;
+}
+
+int tfft_plan_info(tfft_plan_t p, tfft_info* info) {
+  if (!p || !info) return TFFT_ERR_INVALID_ARG;
+  std::memset(info, 0, sizeof(*info));
+  info->n = p->n; info->batch = p->batch; info->dtype = p->dtype;
+  info->abft_mode = p->abft ? TFFT_ABFT_TWO_SIDED : TFFT_ABFT_OFF;
+  info->passes = p->passes;
+  for (int i = 0; i < p->passes; i++) {
+    info->nsub[i] = p->pp[i].nsub;
+    info->stages[i] = p->pp[i].nstages;
+    info->lines_per_tile[i] = p->pp[i].C;
+    info->lines_per_signal[i] = p->pp[i].lines_are_signals ? 1 : p->pp[i].LO * p->pp[i].HI;
+  }
+  info->group = p->G;
+  info->max_faults = p->cap_fix;
+  info->kappa = p->kappa;
+  info->workspace_bytes = p->workspace_bytes;
+  info->launches_per_exec = p->passes + (p->abft ? 3 + 2 * p->passes : 0);
+  info->checksum_vector = p->rvec == RVEC_WANG ? TFFT_R_WANG : TFFT_R_RANDOM;
+  info->checksum_seed = p->rseed;
+  return TFFT_SUCCESS;
+}
+
+int tfft_set_timing(tfft_plan_t p, int enable) {
+  if (!p) return TFFT_ERR_INVALID_ARG;
+  p->timing = enable ? 1 : 0;
+  return TFFT_SUCCESS;
+}
+
+int tfft_timing(tfft_plan_t p, double* ms, int64_t* cnt, int nkinds) {
+  if (!p || nkinds < 0 || (nkinds > 0 && (!ms || !cnt))) return TFFT_ERR_INVALID_ARG;
+  for (int k = 0; k < nkinds; k++) { ms[k] = 0.0; cnt[k] = 0; }
+  for (auto& t : p->timed) {
+    TFFT_CUDA(cudaEventSynchronize(t.b));
+    float el = 0.f;
+    TFFT_CUDA(cudaEventElapsedTime(&el, t.a, t.b));
+    if (t.kind >= 0 && t.kind < nkinds) { ms[t.kind] += el; cnt[t.kind]++; }
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  p->timed.clear();
+  return TFFT_SUCCESS;
+}
+
+int tfft_destroy(tfft_plan_t p) {
+  if (!p) return TFFT_ERR_INVALID_ARG;
+  if (p->used) cudaStreamSynchronize(p->last_stream);
+  free_plan(p);
+  return TFFT_SUCCESS;
+}
+
+const char* tfft_error_string(int status) {
+  switch (status) {
+    case TFFT_SUCCESS: return "success";
+    case TFFT_ERR_INVALID_ARG: return "invalid argument";
+    case TFFT_ERR_UNSUPPORTED: return "unsupported dtype, mode or size";
+    case TFFT_ERR_CUDA: return "CUDA runtime error";
+    case TFFT_ERR_INPLACE: return "in-place transform with ABFT on";
+    case TFFT_ERR_ALLOC: return "allocation failed";
+    case TFFT_ERR_NO_DEVICE: return "no compute-capability 10.3 CUDA device";
+    default: return "unknown status";
+  }
+}
+
+int tfft_last_cuda_error(void) { return g_last_cuda_error.load(); }
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// tfft_internal.h -- device-side parameter blocks shared by the library's
+// translation units.  Not part of the public ABI (that is include/tfft.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tfft {
+
+// How the butterflies of one radix stage are dealt to the threads of a tile.
+// ROW: consecutive threads take consecutive butterflies of one line (the
+//      line's elements are contiguous in memory).
+// COL: consecutive threads take the same butterfly of consecutive lines (the
+//      lines are adjacent columns, so their elements are contiguous).
+enum MapMode : int { MAP_ROW = 0, MAP_COL = 1 };
+
+constexpr int kMaxThreads = 1024;
+constexpr int kLogRing = 1024;     // fault-event log entries
+
+// Fault injection site (Section II-A single-event upset), see tfft_fault.
+struct FaultSite {
+  int mode;      // 0 none, 1 bit flip, 2 scale, 3 add
+  int pass;
+  int stage;     // -1 loaded value, 0..nstages-1 stage output
+  int bit;
+  int64_t signal;
+  int64_t line;
+  int64_t index;
+  double factor;
+};
+
+// Partial checksums of one chunk (one thread block's share of one group).
+// Input side (first pass): S1 = w^T sum_b x_b, S2 = w^T sum_b (b+1) x_b, and
+// the energy sum_b ||x_b||^2.  Output side (last pass): T1 = r^T sum_b y_b,
+// T2 = r^T sum_b (b+1) y_b and the range of signals whose partial output sum
+// was not finite.
+struct RecIn {
+  double s1r, s1i, s2r, s2i, energy, pad0, pad1, pad2;
+};
+struct RecOut {
+  double t1r, t1i, t2r, t2i;
+  long long nf_min, nf_max;   // signal indices (INT64_MAX / -1 when none)
+  double pad0, pad1;
+};
+
+struct Counters {
+  unsigned long long detected, corrected, recomputed, uncorrectable;
+  unsigned long long log_total, execs;
+  unsigned long long max_clean_ratio_bits;   // max |T1-S1|/tau of undetected groups (double bits)
+  unsigned long long pad1;
+};
+
+// Signal-side encoding vector r of the checksum scheme.
+//   RVEC_RANDOM: r_k = +-1, the sign taken from bit 63 of output k of the
+//                SplitMix64 stream seeded with rseed; w = W r is tabulated.
+//   RVEC_WANG  : r_k = w3^k (e_Wang), w in closed form.
+enum RVec : int { RVEC_RANDOM = 0, RVEC_WANG = 1 };
+
+// Output k (0-based) of the SplitMix64 generator of Steele, Lea and Flood
+// (OOPSLA 2014) started from state `seed`: mix(seed + (k + 1) * gamma).
+__host__ __device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed,
+                                                                   unsigned long long k) {
+  unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct LogEvent {   // mirrors tfft_fault_event
+  long long exec_index, group, signal;
+  int action, nonfinite;
+  double residual, tau, q_re, q_im;
+};
+
+// Lists filled by the verify kernel, consumed by the correction path.
+//   fix list   : groups whose faulty signal was named; entry e -> (group, b*)
+//   recompute  : groups recomputed from their input
+// list[0] = count, list[1 + e] = group index; fix_signal[e] = b*.
+struct Lists {
+  long long* fix;         // 1 + cap_fix
+  long long* fix_signal;  // cap_fix
+  long long* rec;         // 1 + cap_rec
+  int cap_fix, cap_rec;
+};
+
+struct PassParams {
+  // ---- geometry of the batched sub-transform of this pass ----
+  int nsub, log2nsub;     // line length
+  int C;                  // lines per tile (power of two)
+  int nthreads;           // C * nsub / E
+  int nstages;            // radix stages: E, E, ..., then nsub / E^(nstages-1)
+  int pitch;              // shared-memory line pitch in elements (>= nsub)
+  int lines_are_signals;  // 1: single pass, a line is a whole signal
+  int in_map, mid_map, out_map;
+  int pass_index;
+  int64_t n;              // signal length N (signal stride in elements)
+  int64_t batch;          // signals in the addressed buffers
+  int64_t LO, HI;         // lines per signal = LO * HI; C divides LO
+  int64_t in_es, in_lo, in_hi;     // element / lo-line / hi-line strides
+  int64_t out_es, out_lo, out_hi;
+  const void* in;
+  void* out;
+
+  // ---- twiddles ----
+  const void* tw_sub;     // omega_{tw_sub_n}^m, m < tw_sub_n (stage twiddles)
+  int tw_sub_stride;      // tw_sub_n / nsub
+  int twiddle;            // multiply output i of line lo by omega_{tw_n}^{lo*i}
+  int64_t tw_scale;       // N / tw_n
+  const void* twN_lo;     // omega_N^m = twN_hi[m >> twN_lbits] * twN_lo[m & mask]
+  const void* twN_hi;
+  int twN_lbits;
+
+  // ---- two-sided ABFT ----
+  int abft_in, abft_out;
+  int group;              // G
+  int parts;              // chunks per (group, line block)
+  int64_t ngroups;
+  int64_t line_blocks;    // LO * HI / C (1 when lines are signals)
+  int64_t slots;          // records per group written by this pass
+  RecIn* rec_in;
+  RecOut* rec_out;
+  const void* wt_lo;      // e^{i pi m / (3N)} = wt_hi[m >> wt_lbits] * wt_lo[m & mask]
+  const void* wt_hi;
+  int wt_lbits;
+  double wk_re, wk_im;    // K = 1 - w3^N
+  int rvec;               // RVec
+  unsigned long long rseed;
+  const void* wtab;       // w = W r, N entries (RVEC_RANDOM)
+  long long* zero_on_entry[2];   // list counts zeroed by block 0 (first pass of an exec)
+
+  // ---- work list (correction path); list == nullptr for a normal exec ----
+  const long long* list;  // list[0] = count, list[1 + e] = block (ignored if list_identity)
+  int list_identity;      // block index = entry index
+  int list_cap;
+  int64_t list_block;     // signals per listed block
+
+  int64_t nchunks;
+  FaultSite fault;
+};
+
+// Launchers (one per element type), defined in fft_pass_f32.cu / _f64.cu.
+cudaError_t launch_pass_f32(const PassParams& p, int E, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_pass_f64(const PassParams& p, int E, int grid, size_t smem, cudaStream_t s);
+cudaError_t pass_func_attrs_f32(int E, size_t smem, int block, int* blocks_per_sm);
+cudaError_t pass_func_attrs_f64(int E, size_t smem, int block, int* blocks_per_sm);
+
+// Verify / correction kernels (abft_fix.cu).
+struct VerifyParams {
+  int64_t n, batch;
+  int group;
+  int64_t ngroups;
+  int64_t slots_in, slots_out;
+  const RecIn* rec_in;
+  const RecOut* rec_out;
+  double kappa_u_log2n_sqrtn;   // kappa * u * log2(N) * sqrt(N)
+  int detect_only;
+  Lists lists;
+  Counters* counters;
+  LogEvent* log;
+  long long exec_index;
+};
+cudaError_t launch_verify(const VerifyParams& v, cudaStream_t s);
+
+struct FixParams {
+  int64_t n, batch;
+  int group;
+  int dtype;           // 0 c64, 1 c128
+  const void* in;      // user input (read)
+  void* out;           // user output (patched)
+  void* ws_c1;         // cap_fix x n : gathered sum_b x_b, transformed in place
+  void* ws_acc;        // cap_fix x n : sum_{b != b*} y'_b
+  Lists lists;
+};
+cudaError_t launch_fix_gather(const FixParams& f, cudaStream_t s);
+// r_k = +-1 (SplitMix64 signs) as complex128, and a complex128 -> complex64 copy.
+cudaError_t launch_gen_signs(void* r, int64_t n, unsigned long long seed, cudaStream_t s);
+cudaError_t launch_c128_to_c64(const void* src, void* dst, int64_t n, cudaStream_t s);
+cudaError_t launch_fix_apply(const FixParams& f, cudaStream_t s);
+
+}  // namespace tfft

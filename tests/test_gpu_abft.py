@@ -1,0 +1,141 @@
+"""Two-sided ABFT on the GPU: detection, location and correction of injected
+faults (Section II-A fault model, Section III scheme), and no false alarms."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import abft as oabft
+import paper_2405_02520_gb300 as t
+from paper_2405_02520_gb300.inputs import normal_batch, uniform_batch
+from tests.gpu_util import oracle_fft, rel_err_rows, run_gpu, tol
+
+pytestmark = pytest.mark.gpu
+
+
+def test_config1_scaled_output_element_detected_located_corrected():
+    """N = 1024, batch 256, U[-1,1) from seed 0; one output element of one
+    signal multiplied by 1 + 1e-2, site drawn from seed 1."""
+    n, batch = 1024, 256
+    x = uniform_batch(n, batch, seed=0)
+    rng = np.random.default_rng(1)
+    sig, idx = int(rng.integers(batch)), int(rng.integers(n))
+    plan = t.tfft_plan(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED)
+    info = t.tfft_plan_info(plan)
+    fault = dict(mode=t.TFFT_FAULT_SCALE, pass_=0, stage=info["stages"][0] - 1, signal=sig,
+                 line=0, index=idx, factor=1.0 + 1e-2)
+    y, _ = run_gpu(x, t.TFFT_C64, plan=plan, fault=fault)
+    ref = oracle_fft(x)
+    assert rel_err_rows(y, ref).max() <= tol(n, t.TFFT_C64)
+    assert t.tfft_report(plan) == (1, 1)
+    ev, total = t.tfft_fault_log(plan)
+    assert total == 1 and ev[0]["signal"] == sig and ev[0]["action"] == 1
+    assert abs(ev[0]["q_re"] - (sig % info["group"] + 1)) < 0.05
+    t.tfft_destroy(plan)
+
+    # the same fault left uncorrected is harmful, and the oracle's own
+    # checksum test names the same group and signal
+    plan = t.tfft_plan_ex(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED, detect_only=True)
+    yf, _ = run_gpu(x, t.TFFT_C64, plan=plan, fault=fault)
+    assert rel_err_rows(yf[sig:sig + 1], ref[sig:sig + 1])[0] > tol(n, t.TFFT_C64)
+    res = oabft.run(x, yf, group=info["group"], u=2.0 ** -24, kappa=info["kappa"])
+    assert res.located == {sig // info["group"]: sig}
+    assert t.tfft_report(plan)[0] == 1
+    t.tfft_destroy(plan)
+
+
+def _site(info, rng, passes=None):
+    p = int(rng.integers(info["passes"])) if passes is None else passes
+    stage = int(rng.integers(-1, info["stages"][p]))
+    line = int(rng.integers(info["lines_per_signal"][p]))
+    index = int(rng.integers(info["nsub"][p]))
+    return p, stage, line, index
+
+
+@pytest.mark.parametrize("log2n,batch", [(10, 64), (16, 8), (20, 4)])
+def test_large_bitflips_every_pass_corrected(log2n, batch):
+    """High exponent/mantissa bit flips (bits 26..30 of the real part) at
+    random (pass, stage, signal, element): detected, named, corrected."""
+    n = 1 << log2n
+    x = uniform_batch(n, batch, seed=40 + log2n)
+    ref = oracle_fft(x)
+    rng = np.random.default_rng(log2n)
+    plan = t.tfft_plan(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED)
+    info = t.tfft_plan_info(plan)
+    expect = 0
+    for trial in range(12):
+        p, stage, line, index = _site(info, rng)
+        sig = int(rng.integers(batch))
+        bit = int(rng.integers(26, 31))
+        fault = dict(mode=t.TFFT_FAULT_BITFLIP, pass_=p, stage=stage, signal=sig, line=line,
+                     index=index, bit=bit)
+        y, _ = run_gpu(x, t.TFFT_C64, plan=plan, fault=fault)
+        err = rel_err_rows(y, ref)
+        assert err.max() <= tol(n, t.TFFT_C64), (trial, fault, err.max())
+        d, c = t.tfft_report(plan)
+        expect += 1
+        assert d == expect and c == expect, (trial, fault, d, c)
+    t.tfft_destroy(plan)
+
+
+def test_nonfinite_fault_located_and_corrected():
+    n, batch = 4096, 32
+    x = uniform_batch(n, batch, seed=9)
+    plan = t.tfft_plan(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED)
+    fault = dict(mode=t.TFFT_FAULT_SCALE, pass_=0, stage=1, signal=21, line=0, index=77,
+                 factor=float("inf"))
+    y, _ = run_gpu(x, t.TFFT_C64, plan=plan, fault=fault)
+    assert np.all(np.isfinite(y))
+    assert rel_err_rows(y, oracle_fft(x)).max() <= tol(n, t.TFFT_C64)
+    ev, _ = t.tfft_fault_log(plan)
+    assert ev[-1]["signal"] == 21 and ev[-1]["nonfinite"] == 1
+    t.tfft_destroy(plan)
+
+
+@pytest.mark.parametrize("log2n", [10, 16])
+def test_two_faults_in_a_group_fall_back_to_recompute(log2n):
+    n = 1 << log2n
+    batch = 40
+    x = uniform_batch(n, batch, seed=11)
+    plan = t.tfft_plan(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED)
+    info = t.tfft_plan_info(plan)
+    fault = dict(mode=t.TFFT_FAULT_ADD_PAIR, pass_=info["passes"] - 1,
+                 stage=info["stages"][info["passes"] - 1] - 1, signal=18, line=0, index=5,
+                 factor=3.0)
+    y, _ = run_gpu(x, t.TFFT_C64, plan=plan, fault=fault)
+    assert rel_err_rows(y, oracle_fft(x)).max() <= tol(n, t.TFFT_C64)
+    st = t.tfft_report_ex(plan)
+    assert st["detected"] == 1 and st["recomputed"] == 1, st
+    t.tfft_destroy(plan)
+
+
+def test_c128_one_fault_per_launch():
+    """complex128, N = 2^12 x 2^14 reduced to 256 signals: one fault per
+    launch, corrected to 1e-14 log2 N."""
+    n, batch = 1 << 12, 256
+    x = normal_batch(n, batch, seed=3)
+    ref = oracle_fft(x)
+    plan = t.tfft_plan(n, batch, t.TFFT_C128, t.TFFT_ABFT_TWO_SIDED)
+    info = t.tfft_plan_info(plan)
+    rng = np.random.default_rng(33)
+    for k in range(6):
+        p, stage, line, index = _site(info, rng)
+        fault = dict(mode=t.TFFT_FAULT_BITFLIP, pass_=p, stage=stage, signal=int(rng.integers(batch)),
+                     line=line, index=index, bit=int(rng.integers(56, 63)))
+        y, _ = run_gpu(x, t.TFFT_C128, plan=plan, fault=fault)
+        assert rel_err_rows(y, ref).max() <= tol(n, t.TFFT_C128), (k, fault)
+    st = t.tfft_report_ex(plan)
+    assert st["detected"] == 6 and st["corrected"] + st["recomputed"] == 6
+    t.tfft_destroy(plan)
+
+
+@pytest.mark.parametrize("log2n,batch,launches", [(10, 256, 300), (16, 64, 50), (20, 16, 20)])
+def test_no_false_positives_on_clean_launches(log2n, batch, launches):
+    import torch
+    n = 1 << log2n
+    plan = t.tfft_plan(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED)
+    y = torch.empty(batch, n, dtype=torch.complex64, device="cuda")
+    for s in range(launches):
+        x = torch.from_numpy(uniform_batch(n, batch, seed=10000 + s)).cuda()
+        t.tfft_exec(plan, x, y, torch.cuda.current_stream())
+    assert t.tfft_report(plan) == (0, 0)
+    t.tfft_destroy(plan)

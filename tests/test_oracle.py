@@ -251,3 +251,62 @@ def test_ragged_last_group():
     res = abft.run(x, yf, group=g, u=2.0 ** -53, kappa=4.0)
     assert res.detected_groups == [2] and res.located == {2: 10}
     assert rel(res.y, y) < 1e-13
+
+
+# ------------------------------------------------ random signal-side vector
+def test_splitmix64_golden_outputs():
+    lines = [l.split() for l in open(os.path.join(GOLDEN, "splitmix64.txt"))
+             if l.strip() and not l.startswith("#")]
+    seed = int(lines[0][1])
+    expect = [int(v, 16) for v in lines[1][1:]]
+    got = [int(v) for v in abft.splitmix64(seed, 3)]
+    assert got == expect
+
+
+def test_splitmix64_counter_matches_sequential_stream():
+    """output k started at `start` equals output start+k of the stream."""
+    a = abft.splitmix64(12345, 10)
+    b = abft.splitmix64(12345, 4, start=6)
+    assert list(a[6:]) == list(b)
+
+
+def test_random_vector_is_balanced_and_flat():
+    """+-1 signs, about half each; W r has no systematically small entry
+    (|w_k|^2 averages N by Parseval)."""
+    n = 1 << 14
+    r, w = abft.vectors(n, "random", seed=20240502)
+    assert set(np.unique(r.real)) == {-1.0, 1.0} and np.all(r.imag == 0)
+    assert abs(np.mean(r.real)) < 4 / np.sqrt(n)
+    assert abs(np.mean(np.abs(w) ** 2) / n - 1) < 1e-12
+    assert np.mean(np.abs(w) < 0.05 * np.sqrt(n)) < 0.01
+
+
+@pytest.mark.parametrize("kind", ["wang", "random"])
+def test_identity_holds_for_both_vectors(kind):
+    n = 4096
+    r, w = abft.vectors(n, kind, seed=7)
+    x = crandn(n)
+    assert abs(w @ x - r @ oracle.fft(x)) / (np.sqrt(n) * np.linalg.norm(x)) < 1e-14
+
+
+def test_random_vector_detects_early_stage_fault_wang_misses():
+    """A small input-stage fault at a position where |w_Wang| is minimal:
+    e_Wang's residual stays below the threshold, the random vector's does not
+    (the blind band of e_Wang)."""
+    n, g = 1 << 12, 4
+    x, y = _clean_group(n, g, 21)
+    rw, ww = abft.vectors(n, "wang")
+    k = int(np.argmin(np.abs(ww)))                      # |w_k| ~ 0.87
+    eps = 2e-3
+    xf = x.copy(); xf[1, k] += eps
+    yf = y.copy(); yf[1] = oracle.fft(xf[1])             # fault before the FFT
+    err = np.linalg.norm(yf[1] - y[1]) / np.linalg.norm(y[1])
+    assert err > 2e-6 * 12                               # harmful at FP32 tolerance
+    u = 2.0 ** -24                                      # judged at FP32 noise
+    cw = abft.group_checksums(x, yf, w=ww, r=rw)
+    assert not abft.verify_group(cw, n, g, u, 1.0).detected
+    rr, wr = abft.vectors(n, "random", seed=20240502)
+    if abs(wr[k]) > 0.3 * np.sqrt(n):
+        cr = abft.group_checksums(x, yf, w=wr, r=rr)
+        v = abft.verify_group(cr, n, g, u, 1.0)
+        assert v.detected and v.located == 1
