@@ -1,0 +1,477 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fault-tolerant batched FFT (one JSON line).
+
+Workload: the batched 1-D complex-to-complex FFT, complex64, swept over
+N = 2^8 .. 2^24 (powers of two) with batch = 2^28 / N, i.e. 2^28 elements
+(2 GiB in, 2 GiB out) per transform, inputs i.i.d. uniform [-1, 1) in real and
+imaginary parts, two-sided ABFT on.  One step = one transform of every N of
+the sweep.  GFLOP/s counts 5 N log2 N flops per signal.
+
+Reported: whole-job GFLOP/s from CUDA events over K steps (max over ranks);
+the HBM roofline fraction of the dominant kernel from the library's
+per-launch events over the same timed region; the ABFT overhead against the
+same sweep with ABFT off; an end-to-end number through tfft_exec_host (host
+buffers, copies inside the timed region); the FP64 CPU oracle timed on a
+bounded sample; SM clocks sampled during the timed region.
+
+Multi-GPU (torchrun, one process per GPU): signals are independent, so each
+rank runs the whole sweep on its own GPU (weak scaling) with no collective on
+the data path; only the timing is reduced (max over ranks).
+
+--impl reference times the FP64 CPU oracle (radix-2 FFT plus the checksum
+encode and verification) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SWEEP = list(range(8, 25))
+TOTAL_LOG2 = 28
+METRIC = "GFLOP/s (5N·log2N) and % HBM roofline with ABFT on; ABFT overhead %; vs plain FP32"
+KERNEL_KINDS = ("first_pass", "middle_pass", "last_pass", "single_pass", "verify", "correction")
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ----------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(backend: str):
+    import torch.distributed as dist
+    ws, rank, _ = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return ws, rank
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def reduce_scalar(value: float, op: str, device=None) -> float:
+    """max / sum of a scalar over ranks (identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard_signals(batch: int, world: int, rank: int, group: int):
+    """Contiguous whole-group slice of the batch for one rank (used when a
+    single batch is split instead of replicated)."""
+    groups = (batch + group - 1) // group
+    g0 = (groups * rank) // world
+    g1 = (groups * (rank + 1)) // world
+    return min(batch, g0 * group), min(batch, g1 * group)
+
+
+# ------------------------------------------------------------------ utils
+def flops(n: int, batch: int) -> float:
+    return 5.0 * n * np.log2(n) * batch if n > 1 else 0.0
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2405_02520_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kind: str):
+    """DRAM bytes per launch of `kind` from the committed ncu summary, only if
+    it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_source_hash") != kernel_source_hash():
+            return None
+        return d.get("bytes_per_launch", {}).get(kind)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", self.gpu_id],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        power = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons,
+                "samples": len(self.rows),
+                "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(elems_per_n: int, seed: int = 0, sweep=SWEEP):
+    """Time the FP64 oracle (radix-2 FFT + two-sided checksum encode and
+    verification per group of 16) on max(1, elems_per_n / N) signals of
+    each N.  Returns (flops, seconds, description)."""
+    import oracle
+    from oracle import abft
+    from paper_2405_02520_gb300.inputs import uniform_batch
+    tot_flops, tot_s, desc = 0.0, 0.0, []
+    for lg in sweep:
+        n = 1 << lg
+        b = max(1, elems_per_n // n)
+        x = uniform_batch(n, b, seed=seed + lg).astype(np.complex128)
+        r, w = abft.vectors(n, "signed_wang", seed=20240502)
+        t0 = time.perf_counter()
+        y = oracle.fft(x)
+        for g0 in range(0, b, 16):
+            cs = abft.group_checksums(x[g0:g0 + 16], y[g0:g0 + 16], w=w, r=r)
+            abft.verify_group(cs, n, min(16, b - g0), 2.0 ** -24, 4.0)
+        tot_s += time.perf_counter() - t0
+        tot_flops += flops(n, b)
+        desc.append(f"2^{lg}x{b}")
+    return tot_flops, tot_s, "per N of the sweep: " + ", ".join(desc)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return 0
+    elems = 1 << 18
+    for _ in range(args.warmup):
+        oracle_sample(elems)
+    tf, ts = 0.0, 0.0
+    for _ in range(args.steps):
+        f, s, desc = oracle_sample(elems)
+        tf += f
+        ts += s
+    value = tf / ts / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ts / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batched 1-D C2C FFT sweep N=2^8..2^24, batch*N=2^28, ABFT on "
+                               "(bounded sample per step)", "sample": desc},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import paper_2405_02520_gb300 as t
+    from paper_2405_02520_gb300.inputs import uniform_batch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sweep = args.sweep
+
+    total = 1 << args.total_log2
+    x_host = uniform_batch(total, 1, seed=rank).reshape(-1)
+    x = torch.from_numpy(x_host).to(dev)
+    y = torch.empty_like(x)
+    del x_host
+
+    plans = {}
+    for lg in sweep:
+        n = 1 << lg
+        plans[lg] = t.tfft_plan(n, total // n, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED)
+
+    def step(pl, timing_events=None):
+        for lg in sweep:
+            if timing_events is not None:
+                timing_events[lg][0].record(stream)
+            t.tfft_exec(pl[lg], x, y, stream)
+            if timing_events is not None:
+                timing_events[lg][1].record(stream)
+
+    for _ in range(args.warmup):
+        step(plans)
+    torch.cuda.synchronize()
+    for lg in sweep:
+        t.tfft_reset_counters(plans[lg])
+        t.tfft_set_timing(plans[lg], True)
+        t.tfft_timing(plans[lg])          # drop warm-up records
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(local)
+    uuid = getattr(props, "uuid", None)
+    if uuid is not None:
+        s = str(uuid)
+        gpu_id = s if s.startswith("GPU-") else "GPU-" + s
+    sampler = ClockSampler(gpu_id)
+
+    def new_events():
+        return {lg: [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+                     for _ in range(args.steps)] for lg in sweep}
+
+    def timed_steps(pl, evs):
+        for k in range(args.steps):
+            step(pl, {lg: evs[lg][k] for lg in sweep})
+
+    def per_n_total(evs):
+        return {lg: sum(a.elapsed_time(b) for a, b in evs[lg]) / args.steps for lg in sweep}
+
+    per_n = new_events()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.start()
+    time.sleep(0.2)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    timed_steps(plans, per_n)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    sampler.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    max_ms = reduce_scalar(elapsed_ms, "max", dev)
+
+    kinds = {k: [0.0, 0] for k in KERNEL_KINDS}
+    launches = 0
+    stats = {}
+    for lg in sweep:
+        tm = t.tfft_timing(plans[lg])
+        for k, (ms, cnt) in tm.items():
+            kinds[k][0] += ms
+            kinds[k][1] += cnt
+        st = t.tfft_report_ex(plans[lg])
+        stats[lg] = st
+        launches += st["launches"]
+        t.tfft_set_timing(plans[lg], False)
+    torch.cuda.synchronize()
+    per_n_ms = per_n_total(per_n)
+
+    flops_step = sum(flops(1 << lg, total >> lg) for lg in sweep)
+    value = ws * args.steps * flops_step / (max_ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel: 16 B (8 read + 8 write) per element per pass
+    bytes_per_launch = total * 16
+    dom = max((k for k in KERNEL_KINDS if kinds[k][1] > 0), key=lambda k: kinds[k][0])
+    dom_ms, dom_n = kinds[dom]
+    peak, peak_src = measured_peaks()
+    achieved = bytes_per_launch / (dom_ms / dom_n / 1e3) / 1e9
+    passes = {lg: t.tfft_plan_info(plans[lg])["passes"] for lg in sweep}
+    step_bytes = sum(passes[lg] * bytes_per_launch for lg in sweep)
+    step_gbs = step_bytes * args.steps / (elapsed_ms / 1e3) / 1e9
+
+    # ABFT off: same sweep, for the overhead
+    for lg in sweep:
+        t.tfft_destroy(plans[lg])
+    off = {lg: t.tfft_plan(1 << lg, total >> lg, t.TFFT_C64, t.TFFT_ABFT_OFF) for lg in sweep}
+    per_off = new_events()
+    for _ in range(args.warmup):
+        step(off)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    timed_steps(off, per_off)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    off_ms = reduce_scalar(e0.elapsed_time(e1), "max", dev)
+    off_per_n = per_n_total(per_off)
+    for lg in sweep:
+        t.tfft_destroy(off[lg])
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        plans = {lg: t.tfft_plan(1 << lg, total >> lg, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED)
+                 for lg in sweep}
+        hin = torch.empty(total, dtype=torch.complex64, pin_memory=True)
+        hin.copy_(x.cpu())
+        hout = torch.empty(total, dtype=torch.complex64, pin_memory=True)
+        del x, y
+        torch.cuda.empty_cache()
+        e2e_steps = max(1, min(args.steps, 3))
+        e2e_ms = 0.0
+        for rep in range(1 + e2e_steps):
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for lg in sweep:
+                t.tfft_exec_host(plans[lg], hin, hout, stream)
+            dt = (time.perf_counter() - t0) * 1e3
+            if rep > 0:
+                e2e_ms += dt
+        e2e_ms = reduce_scalar(e2e_ms, "max", dev)
+        e2e = {"value": round(ws * e2e_steps * flops_step / (e2e_ms / 1e3) / 1e9, 2), "unit": "GFLOP/s",
+               "h2d_bytes_per_step": len(sweep) * total * 8, "d2h_bytes_per_step": len(sweep) * total * 8,
+               "steps": e2e_steps, "ms_per_step": round(e2e_ms / e2e_steps, 3)}
+        for lg in sweep:
+            t.tfft_destroy(plans[lg])
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        f, s, desc = oracle_sample(1 << 24)
+        cpu = {"value": round(f / s / 1e9, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": desc, "seconds": round(s, 2)}
+
+    if rank != 0:
+        return 0
+    clocks = sampler.summary()
+    tr = recorded_traffic(dom)
+    per_n_out = {}
+    for lg in sweep:
+        n = 1 << lg
+        ms_on, ms_off = per_n_ms[lg], off_per_n[lg]
+        per_n_out[str(lg)] = {
+            "passes": passes[lg],
+            "ms": round(ms_on, 4), "ms_abft_off": round(ms_off, 4),
+            "gflops": round(flops(n, total // n) / (ms_on / 1e3) / 1e9, 1),
+            "hbm_frac": round(passes[lg] * bytes_per_launch / (ms_on / 1e3) / 1e9 / peak, 4),
+            "abft_overhead_pct": round((ms_on - ms_off) / ms_off * 100, 2),
+        }
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GFLOP/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(max_ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": f"batched 1-D C2C FFT complex64, N=2^{sweep[0]}..2^{sweep[-1]} (one transform "
+                        f"per N per step), batch*N=2^{args.total_log2} ({total * 8 / 2**30:g} GiB), "
+                        "U[-1,1) re/im, two-sided ABFT on (G=16)",
+            "sweep_log2n": sweep,
+            "elements_per_transform": total,
+            "parallelism": f"replicas x{ws} (weak scaling, no data-path collective)",
+            "l2": f"inputs ({total * 8 / 2**30:g} GiB per transform) larger than L2",
+        },
+        "hbm_roofline_pct_step": round(100 * step_gbs / peak, 2),
+        "abft_overhead_pct": round((max_ms - off_ms) / off_ms * 100, 2),
+        "roofline": {
+            "bound": "hbm",
+            "kernel": dom,
+            "achieved": round(achieved, 1),
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": tr,
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+            "algorithmic_bytes_per_launch": bytes_per_launch,
+            "launches": dom_n,
+        },
+        "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in kinds.items() if v[1]},
+        "per_n": per_n_out,
+        "faults": {"detected": int(sum(s["detected"] for s in stats.values())),
+                   "max_clean_ratio": max(s["max_clean_ratio"] for s in stats.values())},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--sweep", type=lambda s: [int(v) for v in s.split(",")], default=SWEEP,
+                    help="comma-separated log2 N values (default 8..24)")
+    ap.add_argument("--total-log2", type=int, default=TOTAL_LOG2,
+                    help="log2 of the elements per transform (default 28; smaller for profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)      # at least three untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -10,8 +10,9 @@
  * algorithm-based fault tolerance (ABFT), Section III (Eqs. two_side_X and
  * two_side_Y, Section III-B "Delayed Batched Correction"): the batch is
  * encoded on the input side with the checksum vector w = W^T r and on the
- * output side with r, where r_j = exp(-2 pi i j / 3) (Wang's e_Wang vector,
- * Section II), and across each group of G consecutive signals with the all-ones
+ * output side with r, where r_j = s_j exp(-2 pi i j / 3) (Wang's e_Wang
+ * vector of Section II with seeded random signs s_j = +-1; plain e_Wang is an
+ * option), and across each group of G consecutive signals with the all-ones
  * vector and the index weights (1, 2, ..., G).  A silent data corruption in a
  * group is detected from the unweighted checksums, the faulty signal is named
  * by the quotient of the weighted and unweighted residuals, and it is
@@ -92,8 +93,8 @@ typedef struct tfft_plan_opts {
     int dtype;
     int abft_mode;
     int group;          /* G: signals per checksum group (default 16)          */
-    double kappa;       /* detection threshold constant (default 4); the
-                           threshold is kappa*u*log2(n)*sqrt(n)*sqrt(E_g), E_g
+    double kappa;       /* detection threshold constant (default 2); the
+                           threshold is kappa*u*(log2(n)+4)*sqrt(n)*sqrt(E_g), E_g
                            the group's input energy sum_b ||x_b||^2, u the
                            unit roundoff of dtype                               */
     int detect_only;    /* 1: detect and locate but leave outputs uncorrected  */
@@ -103,14 +104,17 @@ typedef struct tfft_plan_opts {
     int force_passes;   /* 0: planner's choice; 1, 2 or 3 forces the count
                            (TFFT_ERR_INVALID_ARG when it cannot tile n)         */
     int checksum_vector;       /* signal-side encoding vector r:
-                                  TFFT_R_RANDOM (default) r_k = +-1 with the
-                                  sign of bit 63 of output k of the SplitMix64
-                                  stream seeded with checksum_seed;
-                                  TFFT_R_WANG r_k = e^{-2 pi i k/3} (e_Wang)  */
-    uint64_t checksum_seed;    /* seed of the random vector (0: a fixed default) */
+                                  TFFT_R_SIGNED_WANG (default)
+                                    r_k = s_k e^{-2 pi i k/3}, s_k = -1 when
+                                    bit 63 of output k of the SplitMix64
+                                    stream seeded with checksum_seed is set,
+                                    else +1 (w = W r tabulated at plan time);
+                                  TFFT_R_WANG r_k = e^{-2 pi i k/3} (e_Wang,
+                                    Section II; w in closed form)             */
+    uint64_t checksum_seed;    /* seed of the signs (0: the default 20240502)  */
 } tfft_plan_opts;
 
-enum tfft_checksum_vector { TFFT_R_RANDOM = 0, TFFT_R_WANG = 1 };
+enum tfft_checksum_vector { TFFT_R_SIGNED_WANG = 0, TFFT_R_WANG = 1 };
 
 int tfft_plan_ex(tfft_plan_t *out, const tfft_plan_opts *opts);
 

@@ -10,7 +10,7 @@ group b = 0..G-1.
 * Signal-side (left) encoding vector r: Wang's e_Wang, r_j = w3^j with
   w3 = e^{-2 pi i/3} (Section II, "ABFT scheme"), or a seeded random +-1
   vector (the sign of bit 63 of output j of a SplitMix64 stream, Steele, Lea
-  and Flood, OOPSLA 2014).  Its image through the DFT is the checksum vector
+  and Flood, OOPSLA 2014), or their product s_j w3^j ("signed e_Wang").  Its image through the DFT is the checksum vector
   w = W^T r = W r (W is symmetric).
 * Batch-side (right) encoding vectors: e_1 = ones and the index weights
   e_3 = (1, 2, ..., G) (Section III, "another encoding vector e_3").
@@ -24,8 +24,9 @@ group b = 0..G-1.
   batch checksum, delta = Y' e_1 - W (X e_1), is subtracted from column b*.
 
 Readings of points the paper leaves open (listed in the design doc as well):
-  - tau = kappa * u * log2(N) * sqrt(N) * sqrt(sum_b ||x_b||^2): an absolute,
-    Parseval-scaled threshold; the paper prints no value for delta.
+  - tau = kappa * u * (log2(N) + 4) * sqrt(N) * sqrt(sum_b ||x_b||^2): an
+    absolute, Parseval-scaled threshold (the +4 covers the rounding of the
+    checksum arithmetic itself); the paper prints no value for delta.
   - The correction is evaluated as y_{b*} = W(X e_1) - sum_{b != b*} y'_b,
     which equals y'_{b*} - delta exactly in real arithmetic and stays exact
     when the fault is huge or non-finite.
@@ -73,12 +74,16 @@ def random_left_vector(n: int, seed: int) -> np.ndarray:
 
 
 def vectors(n: int, kind: str = "wang", seed: int = 0):
-    """(r, w) for kind 'wang' (e_Wang, w in closed form) or 'random'
-    (w = W r with the oracle FFT)."""
+    """(r, w) for kind 'wang' (e_Wang, w in closed form), 'random' (+-1
+    signs) or 'signed_wang' (r_k = s_k w3^k, the random signs times e_Wang);
+    for the random kinds w = W r with the oracle FFT."""
     if kind == "wang":
         return left_vector(n), checksum_vector_closed_form(n)
     if kind == "random":
         r = random_left_vector(n, seed)
+        return r, _fft(r)
+    if kind == "signed_wang":
+        r = random_left_vector(n, seed) * left_vector(n)
         return r, _fft(r)
     raise ValueError(kind)
 
@@ -153,9 +158,9 @@ def _group_checksums(xg, yg, w, r, e1, e3):
 
 
 def threshold(n: int, energy: float, u: float, kappa: float) -> float:
-    """tau = kappa * u * log2(N) * sqrt(N) * sqrt(energy)."""
-    log2n = max(1, int(round(np.log2(n))))
-    return kappa * u * log2n * np.sqrt(n) * np.sqrt(energy)
+    """tau = kappa * u * (log2(N) + 4) * sqrt(N) * sqrt(energy)."""
+    log2n = int(round(np.log2(n)))
+    return kappa * u * (log2n + 4) * np.sqrt(n) * np.sqrt(energy)
 
 
 @dataclass

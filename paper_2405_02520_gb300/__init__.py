@@ -20,7 +20,7 @@ from . import build as _build
 
 TFFT_C64, TFFT_C128 = 0, 1
 TFFT_ABFT_OFF, TFFT_ABFT_TWO_SIDED = 0, 2
-TFFT_R_RANDOM, TFFT_R_WANG = 0, 1
+TFFT_R_SIGNED_WANG, TFFT_R_WANG = 0, 1
 TFFT_FAULT_NONE, TFFT_FAULT_BITFLIP, TFFT_FAULT_SCALE, TFFT_FAULT_ADD, TFFT_FAULT_ADD_PAIR = 0, 1, 2, 3, 4
 TIMING_KINDS = ("first_pass", "middle_pass", "last_pass", "single_pass", "verify", "correction")
 
@@ -151,7 +151,7 @@ def tfft_plan(n: int, batch: int, dtype: int = TFFT_C64, abft_mode: int = TFFT_A
 
 def tfft_plan_ex(n: int, batch: int, dtype: int = TFFT_C64, abft_mode: int = TFFT_ABFT_TWO_SIDED,
                  group: int = 0, kappa: float = 0.0, detect_only: bool = False, max_faults: int = 0,
-                 force_passes: int = 0, checksum_vector: int = TFFT_R_RANDOM, checksum_seed: int = 0) -> int:
+                 force_passes: int = 0, checksum_vector: int = TFFT_R_SIGNED_WANG, checksum_seed: int = 0) -> int:
     o = PlanOpts(n, batch, dtype, abft_mode, group, kappa, int(detect_only), max_faults, force_passes,
                  checksum_vector, checksum_seed)
     h = ctypes.c_void_p()
@@ -239,7 +239,7 @@ class Plan:
     detect_only: bool = False
     max_faults: int = 0
     force_passes: int = 0
-    checksum_vector: int = TFFT_R_RANDOM
+    checksum_vector: int = TFFT_R_SIGNED_WANG
     checksum_seed: int = 0
 
     def __post_init__(self):

@@ -188,10 +188,13 @@ cudaError_t launch_fix_apply(const FixParams& f, cudaStream_t s) {
 
 // ------------------------------------------------ random checksum vector
 __global__ void gen_signs_kernel(double2* r, int64_t n, unsigned long long seed) {
+  const double h = 0.86602540378443864676;   // sqrt(3)/2: w3 = -1/2 - i h
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const bool neg = (splitmix64_at(seed, (unsigned long long)k) >> 63) != 0;
-    r[k] = double2{neg ? -1.0 : 1.0, 0.0};
+    const double s = (splitmix64_at(seed, (unsigned long long)k) >> 63) ? -1.0 : 1.0;
+    const int m = (int)(k % 3);
+    const double re = m == 0 ? 1.0 : -0.5, im = m == 0 ? 0.0 : (m == 1 ? -h : h);
+    r[k] = double2{s * re, s * im};
   }
 }
 

@@ -320,7 +320,38 @@ fft_pass_kernel(const __grid_constant__ PassParams p) {
   const int R_last = nsub >> (__ffs(E) - 1) * (p.nstages - 1);   // nsub / E^(nstages-1)
 
   cT wv[E];             // checksum weights of this thread's input positions
+  unsigned smask = 0;   // signs s_k of r at this thread's outputs, bit u*RL+q
   Partials<real> acc;
+  bool setup_done = false;
+  auto setup_positions = [&](int64_t hi, int64_t lo0) {
+      if (p.abft_in) {
+      const cT* wtab = reinterpret_cast<const cT*>(p.wtab);
+#pragma unroll
+      for (int r = 0; r < E; r++) {
+        const int i = j0 + r * (nsub / E);
+        const int64_t npos = p.lines_are_signals ? (int64_t)i * p.in_es
+                                                 : hi * p.in_hi + (lo0 + c0) * p.in_lo + (int64_t)i * p.in_es;
+        wv[r] = (p.rvec == RVEC_WANG) ? checksum_weight<cT>(p, npos) : ldg_c(wtab + npos);
+      }
+    }
+    // signs s_k of r at this thread's output positions, bit u*RL+q
+    smask = 0;
+    if (p.abft_out && p.rvec == RVEC_SIGNED_WANG) {
+      const int RL = p.nstages > 1 ? R_last : E;
+      const int nb = nsub / RL;
+      for (int ub = 0; ub < E / RL; ub++) {
+        int c, j;
+        if (p.nstages > 1) map_bfly(t + ub * p.nthreads, p.out_map, C, nb, c, j);
+        else { c = c0; j = j0; }
+        const int64_t lo = p.lines_are_signals ? 0 : lo0 + c;
+        const int64_t kb = hi * p.out_hi + lo * p.out_lo;
+        for (int q = 0; q < RL; q++) {
+          const int64_t kpos = kb + (int64_t)(j + q * nb) * p.out_es;
+          smask |= (unsigned)(splitmix64_at(p.rseed, (unsigned long long)kpos) >> 63) << (ub * RL + q);
+        }
+      }
+    }
+  };
 
   for (int64_t chunk = blockIdx.x; chunk < p.nchunks; chunk += gridDim.x) {
     // ---- decode chunk -> (group, part, line block) and its signal range ----
@@ -355,32 +386,12 @@ fft_pass_kernel(const __grid_constant__ PassParams p) {
     const int64_t hi = p.lines_are_signals ? 0 : L0 / p.LO;
     const int64_t lo0 = p.lines_are_signals ? 0 : L0 % p.LO;
 
-    if (p.abft_in) {
-      const cT* wtab = reinterpret_cast<const cT*>(p.wtab);
-#pragma unroll
-      for (int r = 0; r < E; r++) {
-        const int i = j0 + r * (nsub / E);
-        const int64_t npos = p.lines_are_signals ? (int64_t)i * p.in_es
-                                                 : hi * p.in_hi + (lo0 + c0) * p.in_lo + (int64_t)i * p.in_es;
-        wv[r] = (p.rvec == RVEC_WANG) ? checksum_weight<cT>(p, npos) : ldg_c(wtab + npos);
-      }
-    }
-    // signs of r at this thread's output positions (random vector), bit u*RL+q
-    unsigned smask = 0;
-    if (p.abft_out && p.rvec == RVEC_RANDOM) {
-      const int RL = p.nstages > 1 ? R_last : E;
-      const int nb = nsub / RL;
-      for (int ub = 0; ub < E / RL; ub++) {
-        int c, j;
-        if (p.nstages > 1) map_bfly(t + ub * p.nthreads, p.out_map, C, nb, c, j);
-        else { c = c0; j = j0; }
-        const int64_t lo = p.lines_are_signals ? 0 : lo0 + c;
-        const int64_t kb = hi * p.out_hi + lo * p.out_lo;
-        for (int q = 0; q < RL; q++) {
-          const int64_t kpos = kb + (int64_t)(j + q * nb) * p.out_es;
-          smask |= (unsigned)(splitmix64_at(p.rseed, (unsigned long long)kpos) >> 63) << (ub * RL + q);
-        }
-      }
+    // checksum weights of this thread's input positions and signs of r at
+    // its output positions: fixed for the whole kernel when lines are
+    // signals, else per chunk (line block)
+    if (!p.lines_are_signals || !setup_done) {
+      setup_positions(hi, lo0);
+      setup_done = true;
     }
     if (abft) acc.zero();
 
@@ -512,30 +523,18 @@ fft_pass_kernel(const __grid_constant__ PassParams p) {
 #pragma unroll
             for (int q = 0; q < RL; q++) gout[obase + (int64_t)(j + q * nb) * p.out_es] = w[q];
           }
-          if (p.abft_out && valid && p.rvec == RVEC_RANDOM) {
-            // r_k = +-1: sum of the outputs with their signs
-            real tr = 0, ti = 0;
-#pragma unroll
-            for (int q = 0; q < RL; q++) {
-              const bool neg = (smask >> (ub * RL + q)) & 1u;
-              tr += neg ? -w[q].x : w[q].x;
-              ti += neg ? -w[q].y : w[q].y;
-            }
-            const real wgt = (real)(b - gb + 1);
-            acc.t1r += tr; acc.t1i += ti;
-            acc.t2r = fma(wgt, tr, acc.t2r); acc.t2i = fma(wgt, ti, acc.t2i);
-            if (!(isfinite(tr) && isfinite(ti))) {
-              acc.nf_min = min(acc.nf_min, (long long)b);
-              acc.nf_max = max(acc.nf_max, (long long)b);
-            }
-          } else if (p.abft_out && valid) {
-            // r_k = w3^(k mod 3), k = hi*out_hi + lo*out_lo + (j + q nb) out_es
+          if (p.abft_out && valid) {
+            // r_k = s_k w3^(k mod 3), k = hi*out_hi + lo*out_lo + (j + q nb) out_es,
+            // s_k = -1 where the sign mask has a bit (s = 1 for plain e_Wang):
+            // signed sums per residue class of q mod 3, then the w3 powers
             real a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
 #pragma unroll
             for (int q = 0; q < RL; q++) {
-              if (q % 3 == 0) { a0r += w[q].x; a0i += w[q].y; }
-              else if (q % 3 == 1) { a1r += w[q].x; a1i += w[q].y; }
-              else { a2r += w[q].x; a2i += w[q].y; }
+              const bool neg = (smask >> (ub * RL + q)) & 1u;
+              const real yr = neg ? -w[q].x : w[q].x, yi = neg ? -w[q].y : w[q].y;
+              if (q % 3 == 0) { a0r += yr; a0i += yi; }
+              else if (q % 3 == 1) { a1r += yr; a1i += yi; }
+              else { a2r += yr; a2i += yi; }
             }
             const int64_t kpos = hi * p.out_hi + lo * p.out_lo + (int64_t)j * p.out_es;
             const int k0 = (int)(kpos % 3);

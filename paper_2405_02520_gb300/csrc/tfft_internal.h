@@ -51,10 +51,14 @@ struct Counters {
 };
 
 // Signal-side encoding vector r of the checksum scheme.
-//   RVEC_RANDOM: r_k = +-1, the sign taken from bit 63 of output k of the
-//                SplitMix64 stream seeded with rseed; w = W r is tabulated.
-//   RVEC_WANG  : r_k = w3^k (e_Wang), w in closed form.
-enum RVec : int { RVEC_RANDOM = 0, RVEC_WANG = 1 };
+//   RVEC_SIGNED_WANG: r_k = s_k w3^k, s_k = +-1 from bit 63 of output k of
+//                     the SplitMix64 stream seeded with rseed; w = W r is
+//                     tabulated.  The random signs spread the spectrum of r
+//                     (no small w_n, so early-stage faults stay visible); the
+//                     w3 phases keep the few outputs that a late-stage fault
+//                     touches from cancelling in r^T e.
+//   RVEC_WANG       : r_k = w3^k (e_Wang), w in closed form.
+enum RVec : int { RVEC_SIGNED_WANG = 0, RVEC_WANG = 1 };
 
 // Output k (0-based) of the SplitMix64 generator of Steele, Lea and Flood
 // (OOPSLA 2014) started from state `seed`: mix(seed + (k + 1) * gamma).
@@ -125,7 +129,7 @@ struct PassParams {
   double wk_re, wk_im;    // K = 1 - w3^N
   int rvec;               // RVec
   unsigned long long rseed;
-  const void* wtab;       // w = W r, N entries (RVEC_RANDOM)
+  const void* wtab;       // w = W r, N entries (RVEC_SIGNED_WANG)
   long long* zero_on_entry[2];   // list counts zeroed by block 0 (first pass of an exec)
 
   // ---- work list (correction path); list == nullptr for a normal exec ----
@@ -152,7 +156,7 @@ struct VerifyParams {
   int64_t slots_in, slots_out;
   const RecIn* rec_in;
   const RecOut* rec_out;
-  double kappa_u_log2n_sqrtn;   // kappa * u * log2(N) * sqrt(N)
+  double kappa_u_log2n_sqrtn;   // kappa * u * (log2(N) + 4) * sqrt(N)
   int detect_only;
   Lists lists;
   Counters* counters;
@@ -172,7 +176,7 @@ struct FixParams {
   Lists lists;
 };
 cudaError_t launch_fix_gather(const FixParams& f, cudaStream_t s);
-// r_k = +-1 (SplitMix64 signs) as complex128, and a complex128 -> complex64 copy.
+// r_k = s_k w3^k (SplitMix64 signs) as complex128, and a complex128 -> complex64 copy.
 cudaError_t launch_gen_signs(void* r, int64_t n, unsigned long long seed, cudaStream_t s);
 cudaError_t launch_c128_to_c64(const void* src, void* dst, int64_t n, cudaStream_t s);
 cudaError_t launch_fix_apply(const FixParams& f, cudaStream_t s);

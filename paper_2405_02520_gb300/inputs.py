@@ -59,3 +59,16 @@ def tones_batch(n: int, batch: int, seed: int, ntones: int = 8, noise_std: float
 def ragged_lengths(count: int, lo_log2: int, hi_log2: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return (1 << rng.integers(lo_log2, hi_log2 + 1, size=count)).astype(np.int64)
+
+
+def uniform_batch_device(n: int, batch: int, seed: int, device="cuda", dtype=None):
+    """Same distribution as ``uniform_batch`` drawn on the device with torch's
+    seeded generator (for campaigns that only count detections and never
+    compare against the oracle)."""
+    import torch
+    dtype = dtype or torch.complex64
+    real = torch.float32 if dtype == torch.complex64 else torch.float64
+    g = torch.Generator(device=device).manual_seed(seed)
+    re = torch.rand(batch, n, generator=g, device=device, dtype=real) * 2 - 1
+    im = torch.rand(batch, n, generator=g, device=device, dtype=real) * 2 - 1
+    return torch.complex(re, im)

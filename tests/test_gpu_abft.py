@@ -37,7 +37,9 @@ def test_config1_scaled_output_element_detected_located_corrected():
     plan = t.tfft_plan_ex(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED, detect_only=True)
     yf, _ = run_gpu(x, t.TFFT_C64, plan=plan, fault=fault)
     assert rel_err_rows(yf[sig:sig + 1], ref[sig:sig + 1])[0] > tol(n, t.TFFT_C64)
-    res = oabft.run(x, yf, group=info["group"], u=2.0 ** -24, kappa=info["kappa"])
+    kind = "signed_wang" if info["checksum_vector"] == t.TFFT_R_SIGNED_WANG else "wang"
+    res = oabft.run(x, yf, group=info["group"], u=2.0 ** -24, kappa=info["kappa"], kind=kind,
+                    seed=info["checksum_seed"])
     assert res.located == {sig // info["group"]: sig}
     assert t.tfft_report(plan)[0] == 1
     t.tfft_destroy(plan)

@@ -1,0 +1,28 @@
+"""Fault-coverage and false-alarm campaigns on the GPU."""
+import pytest
+
+import paper_2405_02520_gb300 as t
+from tests.campaign import clean_campaign, run_campaign
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("log2n,batch,dtype", [(10, 64, t.TFFT_C64), (13, 32, t.TFFT_C64),
+                                               (16, 8, t.TFFT_C64), (20, 4, t.TFFT_C64),
+                                               (12, 32, t.TFFT_C128)])
+def test_every_harmful_bitflip_detected_and_corrected(log2n, batch, dtype):
+    r = run_campaign(1 << log2n, batch, dtype, faults=60, seed=log2n)
+    assert r["harmful"] > 0
+    assert r["harmful_detected"] == r["harmful"], r
+    assert r["harmful_corrected"] == r["harmful"], r
+    assert r["benign_output_ok"] == r["benign"], r
+
+
+def test_config1_ten_thousand_clean_launches_no_false_positive():
+    r = clean_campaign(1024, 256, 10000)
+    assert r["detected"] == 0, r
+
+
+def test_large_n_clean_launches_no_false_positive():
+    r = clean_campaign(1 << 16, 64, 1000)
+    assert r["detected"] == 0, r
