@@ -244,6 +244,28 @@ int tfft_timing(tfft_plan_t p, double *ms_per_kind, int64_t *launches_per_kind, 
 
 int tfft_destroy(tfft_plan_t p);
 
+/*
+ * tfft_exec_noalloc -- the plain forward transform (no ABFT) of `batch`
+ * complex64 signals of length `n` from device buffer `in` to device buffer
+ * `out` (layout above; in == out is allowed), asynchronously on `stream`,
+ * without any allocation.  The paper has no counterpart: this is for callers
+ * that may not allocate device memory -- code inside a CUDA-graph capture
+ * that must not record allocation nodes, code under a memory manager or
+ * sandbox that owns every device allocation, real-time loops that may not
+ * block on the allocator -- and therefore cannot create a plan.
+ *
+ * Limits: n a power of two with 8192 <= n <= 2^18 (the two-pass range) and
+ * batch * n <= 2^23 (the 64 MiB scratch); anything else returns
+ * TFFT_ERR_INVALID_ARG before any work.  The inter-pass buffer and the
+ * twiddle tables are file-scope __device__ arrays that every GPU loading the
+ * library holds until the process exits; no cudaMalloc, cudaFree or other
+ * allocating call is made.  The first call on a device looks up the arrays'
+ * device addresses (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the arrays and leave the last call's
+ * contents in them; calls that overlap on the GPU race and give wrong results.
+ */
+int tfft_exec_noalloc(int64_t n, int64_t batch, const void *in, void *out, tfft_stream_t stream);
+
 /* Static string for a status code. */
 const char *tfft_error_string(int status);
 /* The last cudaError_t value seen by the library in this process. */

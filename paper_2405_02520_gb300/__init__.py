@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
                 "tfft_set_timing": [P, I],
                 "tfft_timing": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I],
                 "tfft_destroy": [P],
+                "tfft_exec_noalloc": [I64, I64, P, P, P],
                 "tfft_error_string": [I],
                 "tfft_last_cuda_error": [],
             }
@@ -221,6 +222,11 @@ def tfft_timing(plan: int) -> dict:
 
 def tfft_destroy(plan: int) -> None:
     _check(lib().tfft_destroy(plan), "tfft_destroy")
+
+
+def tfft_exec_noalloc(n: int, batch: int, x, y, stream=None) -> None:
+    """Allocation-free two-pass complex64 transform (see include/tfft.h)."""
+    _check(lib().tfft_exec_noalloc(n, batch, _ptr(x), _ptr(y), _stream(stream)), "tfft_exec_noalloc")
 
 
 def tfft_error_string(code: int) -> str:
