@@ -404,6 +404,7 @@ def run_ours(args):
             "gflops": round(flops(n, total // n) / (ms_on / 1e3) / 1e9, 1),
             "hbm_frac": round(passes[lg] * bytes_per_launch / (ms_on / 1e3) / 1e9 / peak, 4),
             "abft_overhead_pct": round((ms_on - ms_off) / ms_off * 100, 2),
+            "max_clean_ratio": round(stats[lg]["max_clean_ratio"], 4),
         }
     line = {
         "metric": METRIC,

@@ -68,8 +68,11 @@ enum tfft_status {
     TFFT_ERR_INPLACE = -4,      /* in == out with ABFT on: the correction and
                                    the group recompute re-read the input      */
     TFFT_ERR_ALLOC = -5,        /* device or host allocation failed           */
-    TFFT_ERR_NO_DEVICE = -6     /* no CUDA device, or not compute capability
+    TFFT_ERR_NO_DEVICE = -6,    /* no CUDA device, or not compute capability
                                    10.3 (the kernels are built for sm_103a)   */
+    TFFT_ERR_TIMEOUT = -7       /* a kernel gave up waiting for a tile copy
+                                   (bounded wait); the results of the execs
+                                   since the last report are not valid        */
 };
 
 /*

@@ -72,8 +72,22 @@ void unit_root(int64_t m, int64_t n, double* re, double* im) {
 int ilog2(int64_t v) { int k = 0; while ((int64_t(1) << k) < v) k++; return k; }
 bool is_pow2(int64_t v) { return v >= 1 && (v & (v - 1)) == 0; }
 
+// Geometry of one tensor map (in 8-byte units along the innermost dimension).
+struct MapGeom {
+  int rank = 0;
+  uint64_t dims[3] = {0, 0, 0};
+  uint64_t strides[2] = {0, 0};   // bytes, dimensions 1 and 2
+  uint32_t box[3] = {1, 1, 1};
+};
+
 struct PassPlan {
   int nsub = 1, E = 1, C = 1, nthreads = 32, nstages = 1, pitch = 1;
+  // TMA tile pipeline (fft_tile_kernel) for the main exec
+  int tma = 0, nbuf = 0, tbps = 1;
+  unsigned buf_bytes = 0;
+  size_t tsmem = 0;
+  TileMap map_in{}, map_out{};
+  MapGeom gin{}, gout{};
   int in_map = MAP_ROW, mid_map = MAP_ROW, out_map = MAP_ROW;
   int lines_are_signals = 0, twiddle = 0, parts = 1;
   int64_t LO = 1, HI = 1, line_blocks = 1;
@@ -118,6 +132,9 @@ struct tfft_plan_s {
   LogEvent* log = nullptr;
   void* ws_c1 = nullptr; void* ws_acc = nullptr;
   void* stage_in = nullptr; void* stage_out = nullptr;
+  int* err_flag = nullptr;
+  const void* enc_ptr[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+  CUtensorMap enc_map[3][2];
 
   FaultSite pending{};
   int64_t execs = 0, launches = 0;
@@ -153,7 +170,8 @@ int upload(tfft_plan_s* p, void** dst, const std::vector<double>& re, const std:
 
 void free_plan(tfft_plan_s* p) {
   void* bufs[] = {p->tw_sub, p->twN_lo, p->twN_hi, p->wt_lo, p->wt_hi, p->wtab, p->tmp, p->rec_in, p->rec_out,
-                  p->lists_mem, p->counters, p->log, p->ws_c1, p->ws_acc, p->stage_in, p->stage_out};
+                  p->lists_mem, p->counters, p->log, p->ws_c1, p->ws_acc, p->stage_in, p->stage_out,
+                  p->err_flag};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& t : p->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -303,6 +321,132 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
   return 0;
 }
 
+// cuTensorMapEncodeTiled, fetched from the driver through the runtime (no
+// link-time dependency on libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  });
+  return fn;
+}
+
+bool encode_map(CUtensorMap* m, const MapGeom& g, const void* base) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t gd[3], gs[2];
+  cuuint32_t bd[3], es[3] = {1, 1, 1};
+  for (int i = 0; i < g.rank; i++) { gd[i] = g.dims[i]; bd[i] = g.box[i]; }
+  for (int i = 0; i + 1 < g.rank; i++) gs[i] = g.strides[i];
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)g.rank, const_cast<void*>(base), gd, gs, bd, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool geom_ok(const MapGeom& g) {
+  for (int i = 0; i < g.rank; i++)
+    if (g.box[i] < 1 || g.box[i] > 256 || g.dims[i] < g.box[i] || g.dims[i] >= (uint64_t(1) << 32)) return false;
+  if ((g.box[0] * 8) % 16) return false;
+  for (int i = 0; i + 1 < g.rank; i++)
+    if (g.strides[i] % 16 || g.strides[i] >= (uint64_t(1) << 40)) return false;
+  return true;
+}
+
+// Tile maps of the TMA pipeline for every pass (Section IV-A kernel-level
+// tiling expressed as tensor-map boxes).  A pass whose boxes do not fit the
+// TMA limits keeps the direct-load kernel.
+int plan_tma(tfft_plan_s* p) {
+  if (!encode_fn()) return 0;
+  const int64_t u = (int64_t)p->esize / 8;     // 8-byte units per element
+  const int64_t B = p->batch, es = (int64_t)p->esize;
+  for (int i = 0; i < p->passes; i++) {
+    PassPlan& q = p->pp[i];
+    TileMap mi{}, mo{};
+    MapGeom gi{}, go{};
+    const int64_t nsub = q.nsub, C = q.C;
+    if (q.lines_are_signals) {
+      if (nsub < 16) continue;
+      mi.kind = mo.kind = 1;
+      mi.layout = mo.layout = 0;
+    } else {
+      const bool first = i == 0, last = i == p->passes - 1;
+      const int64_t N1 = p->pp[0].nsub, M = p->n / N1;
+      const int64_t rows = std::min<int64_t>(nsub, 256);
+      auto em_box = [&](TileMap& m) {          // element-major [nsub][C] in boxes of <= 256 rows
+        m.kind = 0; m.layout = 1;
+        m.nbox = (int)((nsub + rows - 1) / rows);
+        m.box_rows = (int)rows;
+        m.box_elems = (int)(rows * C);
+      };
+      if (first) {
+        em_box(mi); em_box(mo);
+        mi.kind = mo.kind = 2;
+        mi.ax = mo.ax = u; mi.by = mo.by = N1;
+        gi.rank = 2; gi.dims[0] = M * u; gi.dims[1] = B * N1; gi.strides[0] = M * es;
+        gi.box[0] = (uint32_t)(C * u); gi.box[1] = (uint32_t)rows;
+        go = gi;
+      } else if (!last) {                      // middle pass of three
+        const int64_t N2 = nsub, N3 = q.LO;
+        em_box(mi); em_box(mo);
+        mi.kind = mo.kind = 3;
+        mi.ax = mo.ax = u; mi.az = mo.az = 1; mi.bz = mo.bz = N1;
+        gi.rank = 3; gi.dims[0] = N3 * u; gi.dims[1] = N2; gi.dims[2] = B * N1;
+        gi.strides[0] = N3 * es; gi.strides[1] = M * es;
+        gi.box[0] = (uint32_t)(C * u); gi.box[1] = (uint32_t)rows; gi.box[2] = 1;
+        go = gi;
+      } else if (p->passes == 2) {
+        const int64_t N2 = nsub;
+        const int64_t S = std::min<int64_t>(N2, 256 / u);   // row split for the box limit
+        mi.kind = 3; mi.layout = 0; mi.nbox = 1; mi.bz = N1; mi.cz = 1;
+        gi.rank = 3; gi.dims[0] = S * u; gi.dims[1] = N2 / S; gi.dims[2] = B * N1;
+        gi.strides[0] = S * es; gi.strides[1] = N2 * es;
+        gi.box[0] = (uint32_t)(S * u); gi.box[1] = (uint32_t)(N2 / S); gi.box[2] = (uint32_t)C;
+        em_box(mo);
+        mo.kind = 2; mo.ax = u; mo.by = N2;
+        go.rank = 2; go.dims[0] = N1 * u; go.dims[1] = B * N2; go.strides[0] = N1 * es;
+        go.box[0] = (uint32_t)(C * u); go.box[1] = (uint32_t)rows;
+      } else {                                 // last pass of three
+        const int64_t N3 = nsub, N2 = q.HI;
+        mi.kind = 3; mi.layout = 0; mi.nbox = 1; mi.ay = 1; mi.bz = N1; mi.cz = 1;
+        gi.rank = 3; gi.dims[0] = N3 * u; gi.dims[1] = N2; gi.dims[2] = B * N1;
+        gi.strides[0] = N3 * es; gi.strides[1] = M * es;
+        gi.box[0] = (uint32_t)(N3 * u); gi.box[1] = 1; gi.box[2] = (uint32_t)C;
+        mo.kind = 3; mo.layout = 1; mo.nbox = 1; mo.box_rows = (int)N3; mo.box_elems = (int)(N3 * C);
+        mo.ax = u; mo.ay = 1; mo.bz = N3;
+        go.rank = 3; go.dims[0] = N1 * u; go.dims[1] = N2; go.dims[2] = B * N3;
+        go.strides[0] = N1 * es; go.strides[1] = N1 * N2 * es;
+        go.box[0] = (uint32_t)(C * u); go.box[1] = 1; go.box[2] = (uint32_t)N3;
+      }
+      if (!geom_ok(gi) || !geom_ok(go)) continue;
+    }
+    mi.bytes = mo.bytes = (unsigned)(C * nsub * es);
+    q.map_in = mi; q.map_out = mo; q.gin = gi; q.gout = go;
+    q.buf_bytes = (unsigned)((C * nsub * es + 1023) / 1024 * 1024);
+    const size_t budget = 218 * 1024 - 1024;
+    q.nbuf = (int)std::min<size_t>(6, budget / (q.buf_bytes + 8));
+    if (q.nbuf < 2) continue;
+    q.tsmem = (size_t)q.nbuf * q.buf_bytes + (size_t)q.nbuf * 8 + 1024;
+    cudaError_t e = p->dtype == TFFT_C64 ? tile_func_attrs_f32(q.E, q.tsmem, q.nthreads, &q.tbps)
+                                         : tile_func_attrs_f64(q.E, q.tsmem, q.nthreads, &q.tbps);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (q.tbps < 1) continue;
+    q.tma = 1;
+  }
+  return 0;
+}
+
 int plan_tables(tfft_plan_s* p) {
   const int64_t n = p->n;
   int rc;
@@ -410,6 +554,8 @@ int plan_workspace(tfft_plan_s* p) {
   p->lists.rec = p->lists_mem + 1 + 2 * p->cap_fix;
   p->lists.cap_fix = p->cap_fix;
   p->lists.cap_rec = p->cap_rec;
+  TFFT_CUDA(cudaMalloc(&p->err_flag, sizeof(int)));
+  TFFT_CUDA(cudaMemset(p->err_flag, 0, sizeof(int)));
   TFFT_CUDA(cudaMalloc(&p->counters, sizeof(Counters)));
   TFFT_CUDA(cudaMemset(p->counters, 0, sizeof(Counters)));
   TFFT_CUDA(cudaMalloc(&p->log, sizeof(LogEvent) * kLogRing));
@@ -451,9 +597,25 @@ PassParams base_params(const tfft_plan_s* p, int i) {
   return a;
 }
 
-int launch_pass(tfft_plan_s* p, const PassParams& a, int i, int kind, cudaStream_t s) {
+int launch_pass(tfft_plan_s* p, PassParams& a, int i, int kind, cudaStream_t s) {
   const PassPlan& q = p->pp[i];
-  const int64_t maxgrid = (int64_t)p->sms * q.bps;
+  const bool tma = q.tma && a.list == nullptr;
+  if (tma) {
+    a.nbuf = q.nbuf; a.buf_bytes = q.buf_bytes; a.err_flag = p->err_flag;
+    a.map_in = q.map_in; a.map_out = q.map_out;
+    const void* ptrs[2] = {a.in, a.out};
+    const MapGeom* geo[2] = {&q.gin, &q.gout};
+    const int kinds[2] = {q.map_in.kind, q.map_out.kind};
+    for (int d = 0; d < 2; d++) {
+      if (kinds[d] < 2) continue;
+      if (p->enc_ptr[i][d] != ptrs[d]) {
+        if (!encode_map(&p->enc_map[i][d], *geo[d], ptrs[d])) return TFFT_ERR_CUDA;
+        p->enc_ptr[i][d] = ptrs[d];
+      }
+      (d == 0 ? a.tmap_in : a.tmap_out) = p->enc_map[i][d];
+    }
+  }
+  const int64_t maxgrid = (int64_t)p->sms * (tma ? q.tbps : q.bps);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.nchunks, maxgrid));
   TimedLaunch tl{};
   if (p->timing) {
@@ -461,8 +623,11 @@ int launch_pass(tfft_plan_s* p, const PassParams& a, int i, int kind, cudaStream
     TFFT_CUDA(cudaEventCreate(&tl.a)); TFFT_CUDA(cudaEventCreate(&tl.b));
     TFFT_CUDA(cudaEventRecord(tl.a, s));
   }
-  cudaError_t e = p->dtype == TFFT_C64 ? launch_pass_f32(a, q.E, grid, q.smem, s)
-                                       : launch_pass_f64(a, q.E, grid, q.smem, s);
+  cudaError_t e;
+  if (tma)
+    e = p->dtype == TFFT_C64 ? launch_tile_f32(a, q.E, grid, q.tsmem, s) : launch_tile_f64(a, q.E, grid, q.tsmem, s);
+  else
+    e = p->dtype == TFFT_C64 ? launch_pass_f32(a, q.E, grid, q.smem, s) : launch_pass_f64(a, q.E, grid, q.smem, s);
   if (e != cudaSuccess) return cuda_fail(e);
   p->launches++;
   if (p->timing) {
@@ -594,6 +759,7 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   p->device = dev;
   p->sms = prop.multiProcessorCount;
   int rc = plan_build(p, o);
+  if (!rc) rc = plan_tma(p);
   if (!rc) rc = plan_tables(p);
   if (!rc) rc = plan_workspace(p);
   if (!rc) rc = plan_wtable(p);
@@ -643,6 +809,9 @@ int tfft_exec_host(tfft_plan_t p, const void* host_in, void* host_out, tfft_stre
 int tfft_report_ex(tfft_plan_t p, tfft_stats* st) {
   if (!p || !st) return TFFT_ERR_INVALID_ARG;
   if (p->used) TFFT_CUDA(cudaStreamSynchronize(p->last_stream));
+  int err = 0;
+  TFFT_CUDA(cudaMemcpy(&err, p->err_flag, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) return TFFT_ERR_TIMEOUT;
   Counters c;
   TFFT_CUDA(cudaMemcpy(&c, p->counters, sizeof(c), cudaMemcpyDeviceToHost));
   st->detected = (int64_t)c.detected;
@@ -776,6 +945,7 @@ const char* tfft_error_string(int status) {
     case TFFT_ERR_INPLACE: return "in-place transform with ABFT on";
     case TFFT_ERR_ALLOC: return "allocation failed";
     case TFFT_ERR_NO_DEVICE: return "no compute-capability 10.3 CUDA device";
+    case TFFT_ERR_TIMEOUT: return "a kernel timed out waiting for a tile copy";
     default: return "unknown status";
   }
 }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>            // CUtensorMap (the tensor-map type only; no driver call is linked)
 #include <cuda_runtime.h>
 
 namespace tfft {
@@ -87,6 +88,24 @@ struct Lists {
   int cap_fix, cap_rec;
 };
 
+// How a tile moves between global and shared memory in the TMA kernel.
+//   kind 1: one bulk copy of `rows` contiguous signals (single pass),
+//   kind 2 / 3: a 2-D / 3-D tensor-map box; coordinates of the tile whose
+//   signal is b, hi-line hi and first lo-line lo0 are
+//     x = ax*lo0,  y = ay*hi + by*b + cy*lo0,  z = az*hi + bz*b + cz*lo0
+//   (in 8-byte units along x), repeated `nbox` times with y advanced by
+//   `box_rows` and the shared-memory destination by `box_elems` elements.
+// layout: 0 line-major [C][nsub], 1 element-major [nsub][C] (the dense box).
+struct TileMap {
+  int kind;
+  int layout;
+  int nbox;
+  int box_rows;
+  int box_elems;
+  unsigned bytes;        // bytes of the whole tile (all boxes)
+  long long ax, ay, by, cy, az, bz, cz;
+};
+
 struct PassParams {
   // ---- geometry of the batched sub-transform of this pass ----
   int nsub, log2nsub;     // line length
@@ -140,6 +159,14 @@ struct PassParams {
 
   int64_t nchunks;
   FaultSite fault;
+
+  // ---- TMA tile pipeline (fft_tile_kernel only) ----
+  int nbuf;               // shared-memory tile buffers in the ring
+  unsigned buf_bytes;     // bytes per buffer (tile rounded up to 1 KiB)
+  int* err_flag;          // set when a bounded wait gives up
+  TileMap map_in, map_out;
+  CUtensorMap tmap_in;     // 64-byte aligned by its own type
+  CUtensorMap tmap_out;
 };
 
 // Launchers (one per element type), defined in fft_pass_f32.cu / _f64.cu.
@@ -147,6 +174,10 @@ cudaError_t launch_pass_f32(const PassParams& p, int E, int grid, size_t smem, c
 cudaError_t launch_pass_f64(const PassParams& p, int E, int grid, size_t smem, cudaStream_t s);
 cudaError_t pass_func_attrs_f32(int E, size_t smem, int block, int* blocks_per_sm);
 cudaError_t pass_func_attrs_f64(int E, size_t smem, int block, int* blocks_per_sm);
+cudaError_t launch_tile_f32(const PassParams& p, int E, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_tile_f64(const PassParams& p, int E, int grid, size_t smem, cudaStream_t s);
+cudaError_t tile_func_attrs_f32(int E, size_t smem, int block, int* blocks_per_sm);
+cudaError_t tile_func_attrs_f64(int E, size_t smem, int block, int* blocks_per_sm);
 
 // Verify / correction kernels (abft_fix.cu).
 struct VerifyParams {
