@@ -22,17 +22,20 @@
 
 namespace tfft {
 
-__global__ void verify_kernel(const VerifyParams v) {
-  const int lane = threadIdx.x & 31;
-  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Each group is reduced by `lanes_per_group` threads (one warp, or a whole
+// block of 256 when a group holds many records); lane 0 of the group decides.
+__global__ void verify_kernel(const VerifyParams v, int lanes_per_group) {
+  __shared__ double sred[8][11];
+  const int lane = threadIdx.x % lanes_per_group;
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / lanes_per_group;
   if (g >= v.ngroups) return;
   double s1r = 0, s1i = 0, s2r = 0, s2i = 0, en = 0, t1r = 0, t1i = 0, t2r = 0, t2i = 0;
   long long nfmin = 0x7fffffffffffffffLL, nfmax = -1;
-  for (int64_t k = lane; k < v.slots_in; k += 32) {
+  for (int64_t k = lane; k < v.slots_in; k += lanes_per_group) {
     const RecIn r = v.rec_in[g * v.slots_in + k];
     s1r += r.s1r; s1i += r.s1i; s2r += r.s2r; s2i += r.s2i; en += r.energy;
   }
-  for (int64_t k = lane; k < v.slots_out; k += 32) {
+  for (int64_t k = lane; k < v.slots_out; k += lanes_per_group) {
     const RecOut r = v.rec_out[g * v.slots_out + k];
     t1r += r.t1r; t1i += r.t1i; t2r += r.t2r; t2i += r.t2i;
     nfmin = min(nfmin, r.nf_min); nfmax = max(nfmax, r.nf_max);
@@ -45,6 +48,23 @@ __global__ void verify_kernel(const VerifyParams v) {
     t2r += __shfl_xor_sync(0xffffffffu, t2r, off); t2i += __shfl_xor_sync(0xffffffffu, t2i, off);
     nfmin = min(nfmin, __shfl_xor_sync(0xffffffffu, nfmin, off));
     nfmax = max(nfmax, __shfl_xor_sync(0xffffffffu, nfmax, off));
+  }
+  if (lanes_per_group > 32) {          // combine the warps of the block
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      sred[w][0] = s1r; sred[w][1] = s1i; sred[w][2] = s2r; sred[w][3] = s2i; sred[w][4] = en;
+      sred[w][5] = t1r; sred[w][6] = t1i; sred[w][7] = t2r; sred[w][8] = t2i;
+      sred[w][9] = __longlong_as_double(nfmin); sred[w][10] = __longlong_as_double(nfmax);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 1; q < lanes_per_group / 32; q++) {
+        s1r += sred[q][0]; s1i += sred[q][1]; s2r += sred[q][2]; s2i += sred[q][3]; en += sred[q][4];
+        t1r += sred[q][5]; t1i += sred[q][6]; t2r += sred[q][7]; t2i += sred[q][8];
+        nfmin = min(nfmin, __double_as_longlong(sred[q][9]));
+        nfmax = max(nfmax, __double_as_longlong(sred[q][10]));
+      }
+    }
   }
   if (lane != 0) return;
 
@@ -114,9 +134,9 @@ __global__ void verify_kernel(const VerifyParams v) {
 
 cudaError_t launch_verify(const VerifyParams& v, cudaStream_t s) {
   const int threads = 256;
-  const int64_t warps = v.ngroups;
-  const int64_t blocks = (warps * 32 + threads - 1) / threads;
-  verify_kernel<<<(unsigned)blocks, threads, 0, s>>>(v);
+  const int lanes = (v.slots_in + v.slots_out > 512) ? 256 : 32;
+  const int64_t blocks = (v.ngroups * lanes + threads - 1) / threads;
+  verify_kernel<<<(unsigned)blocks, threads, 0, s>>>(v, lanes);
   return cudaGetLastError();
 }
 

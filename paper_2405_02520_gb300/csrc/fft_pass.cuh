@@ -289,6 +289,36 @@ __device__ void reduce_and_store(Partials<real>& a, const PassParams& p, int64_t
 
 // Threads per block are capped so that the widest per-thread state (E complex
 // values of data and of checksum weights) fits in registers without spilling.
+// Warp-wide reduction of the partials; lane 0 writes the warp's records at
+// slot `slot` of group g (no block-wide synchronisation).
+template <typename real>
+__device__ void reduce_warp_and_store(Partials<real>& a, const PassParams& p, long long g, long long slot) {
+  const unsigned full = 0xffffffffu;
+  real v[9] = {a.s1r, a.s1i, a.s2r, a.s2i, a.en, a.t1r, a.t1i, a.t2r, a.t2i};
+  long long mn = a.nf_min, mx = a.nf_max;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 9; q++) v[q] += __shfl_xor_sync(full, v[q], off);
+    mn = min(mn, __shfl_xor_sync(full, mn, off));
+    mx = max(mx, __shfl_xor_sync(full, mx, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (p.abft_in) {
+      RecIn r;
+      r.s1r = v[0]; r.s1i = v[1]; r.s2r = v[2]; r.s2i = v[3]; r.energy = v[4];
+      r.pad0 = r.pad1 = r.pad2 = 0.0;
+      p.rec_in[g * p.slots + slot] = r;
+    }
+    if (p.abft_out) {
+      RecOut r;
+      r.t1r = v[5]; r.t1i = v[6]; r.t2r = v[7]; r.t2i = v[8];
+      r.nf_min = mn; r.nf_max = mx; r.pad0 = r.pad1 = 0.0;
+      p.rec_out[g * p.slots + slot] = r;
+    }
+  }
+}
+
 template <typename real, int E>
 constexpr int max_threads() { return sizeof(real) * E >= 64 ? 256 : 512; }
 

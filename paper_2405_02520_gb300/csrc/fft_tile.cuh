@@ -174,10 +174,12 @@ __device__ __forceinline__ void issue_load(const PassParams& p, const TileCursor
   const int y = (int)(m.ay * hi + m.by * b + m.cy * lo0);
   const int z = (int)(m.az * hi + m.bz * b + m.cz * lo0);
   mbar_expect_tx(bar, m.bytes);
-  for (int k = 0; k < m.nbox; k++) {
-    if (m.kind == 2) tma_load_2d(dst + k * m.box_elems, &p.tmap_in, x, y + k * m.box_rows, bar);
-    else tma_load_3d(dst + k * m.box_elems, &p.tmap_in, x, y + k * m.box_rows, z, bar);
-  }
+  for (int kx = 0; kx < m.nbx; kx++)
+    for (int k = 0; k < m.nbox; k++) {
+      cT* d = dst + kx * m.bx_elems + k * m.box_elems;
+      if (m.kind == 2) tma_load_2d(d, &p.tmap_in, x + kx * m.bx_step, y + k * m.box_rows, bar);
+      else tma_load_3d(d, &p.tmap_in, x + kx * m.bx_step, y + k * m.box_rows, z, bar);
+    }
 }
 
 template <typename cT>
@@ -193,13 +195,15 @@ __device__ __forceinline__ void issue_store(const PassParams& p, long long tb, l
   const int x = (int)(m.ax * lo0);
   const int y = (int)(m.ay * hi + m.by * tb + m.cy * lo0);
   const int z = (int)(m.az * hi + m.bz * tb + m.cz * lo0);
-  for (int k = 0; k < m.nbox; k++) {
-    if (m.kind == 2) tma_store_2d(&p.tmap_out, x, y + k * m.box_rows, src + k * m.box_elems);
-    else tma_store_3d(&p.tmap_out, x, y + k * m.box_rows, z, src + k * m.box_elems);
-  }
+  for (int kx = 0; kx < m.nbx; kx++)
+    for (int k = 0; k < m.nbox; k++) {
+      const cT* s = src + kx * m.bx_elems + k * m.box_elems;
+      if (m.kind == 2) tma_store_2d(&p.tmap_out, x + kx * m.bx_step, y + k * m.box_rows, s);
+      else tma_store_3d(&p.tmap_out, x + kx * m.bx_step, y + k * m.box_rows, z, s);
+    }
 }
 
-constexpr long long kWaitLimit = 1ll << 24;   // mbarrier polls before giving up
+constexpr long long kWaitLimit = 1ll << 20;   // mbarrier polls before giving up (~1 s)
 
 template <typename real, int E>
 __global__ void __launch_bounds__(max_threads<real, E>())

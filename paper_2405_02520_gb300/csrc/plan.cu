@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -75,6 +76,7 @@ bool is_pow2(int64_t v) { return v >= 1 && (v & (v - 1)) == 0; }
 // Geometry of one tensor map (in 8-byte units along the innermost dimension).
 struct MapGeom {
   int rank = 0;
+  int swizzle = 0;                 // CUtensorMapSwizzle
   uint64_t dims[3] = {0, 0, 0};
   uint64_t strides[2] = {0, 0};   // bytes, dimensions 1 and 2
   uint32_t box[3] = {1, 1, 1};
@@ -84,6 +86,9 @@ struct PassPlan {
   int nsub = 1, E = 1, C = 1, nthreads = 32, nstages = 1, pitch = 1;
   // TMA tile pipeline (fft_tile_kernel) for the main exec
   int tma = 0, nbuf = 0, tbps = 1;
+  int v3 = 0, role = 0;            // v3 kernel (compile-time geometry) and its role
+  int vC = 0;                      // v3 lines per tile
+  int64_t vLB = 0;                 // v3 line blocks per signal
   unsigned buf_bytes = 0;
   size_t tsmem = 0;
   TileMap map_in{}, map_out{};
@@ -214,8 +219,13 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
   const int64_t n = o->n;
   const bool c64 = o->dtype == TFFT_C64;
   p->esize = c64 ? 8 : 16;
-  const int E0 = c64 ? 16 : 8;
-  const int TILE = c64 ? 4096 : 2048;        // elements of one thread block's tile
+  int E0 = c64 ? 16 : 8;
+  int TILE = c64 ? 4096 : 2048;              // elements of one thread block's tile
+  // tuning overrides for measurement (radix per thread, tile elements)
+  if (c64) {
+    if (const char* s = std::getenv("TFFT_TUNE_E")) { const int v = std::atoi(s); if (v == 8 || v == 16) E0 = v; }
+    if (const char* s = std::getenv("TFFT_TUNE_TILE")) { const int v = std::atoi(s); if (v >= 1024 && v <= 8192 && !(v & (v - 1))) TILE = v; }
+  }
   const int S = c64 ? 16 : 8;                // elements per 128-byte shared-memory row
   const int CMIN = c64 ? 8 : 4;              // lines per tile for 64-byte column runs
   const int NSUBMAX = TILE / CMIN;
@@ -307,18 +317,27 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
     int rc = pass_attrs(p, q);
     if (rc) return rc;
   }
-  // chunks per group: enough thread blocks to fill the GPU when groups are few
-  for (int i = 0; i < passes; i++) {
+  return 0;
+}
+
+// Chunks per group (thread blocks sharing a group) and checksum record slots
+// per group: one record per chunk, or one per warp and chunk for v3 passes.
+void plan_slots(tfft_plan_s* p) {
+  for (int i = 0; i < p->passes; i++) {
     PassPlan& q = p->pp[i];
-    const int64_t target = (int64_t)2 * p->sms * q.bps;
-    const int64_t base = p->ngroups * q.line_blocks;
-    const int64_t tiles_per_group = q.lines_are_signals ? std::max<int64_t>(1, G / q.C) : G;
+    const int64_t target = (int64_t)2 * p->sms * std::max(1, q.v3 ? q.tbps : q.bps);
+    const int64_t lb = q.v3 ? q.vLB : q.line_blocks;
+    const int64_t cc = q.v3 ? q.vC : q.C;
+    const int64_t base = p->ngroups * lb;
+    const int64_t tiles_per_group = q.lines_are_signals ? std::max<int64_t>(1, p->G / cc) : p->G;
     q.parts = 1;
     if (base < target) q.parts = (int)std::min<int64_t>(tiles_per_group, (target + base - 1) / base);
   }
-  p->slots_in = (int64_t)p->pp[0].parts * p->pp[0].line_blocks;
-  p->slots_out = (int64_t)p->pp[passes - 1].parts * p->pp[passes - 1].line_blocks;
-  return 0;
+  const PassPlan& f = p->pp[0];
+  const PassPlan& l = p->pp[p->passes - 1];
+  // v3 writes one record per warp and chunk in the single pass, one per chunk otherwise
+  p->slots_in = (int64_t)f.parts * (f.v3 ? f.vLB * (f.role == 0 ? 8 : 1) : f.line_blocks);
+  p->slots_out = (int64_t)l.parts * (l.v3 ? l.vLB * (l.role == 0 ? 8 : 1) : l.line_blocks);
 }
 
 // cuTensorMapEncodeTiled, fetched from the driver through the runtime (no
@@ -350,7 +369,7 @@ bool encode_map(CUtensorMap* m, const MapGeom& g, const void* base) {
   for (int i = 0; i < g.rank; i++) { gd[i] = g.dims[i]; bd[i] = g.box[i]; }
   for (int i = 0; i + 1 < g.rank; i++) gs[i] = g.strides[i];
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)g.rank, const_cast<void*>(base), gd, gs, bd, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, (CUtensorMapSwizzle)g.swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -432,6 +451,9 @@ int plan_tma(tfft_plan_s* p) {
       if (!geom_ok(gi) || !geom_ok(go)) continue;
     }
     mi.bytes = mo.bytes = (unsigned)(C * nsub * es);
+    mi.nbx = mo.nbx = 1;
+    if (mi.nbox < 1) mi.nbox = 1;
+    if (mo.nbox < 1) mo.nbox = 1;
     q.map_in = mi; q.map_out = mo; q.gin = gi; q.gout = go;
     q.buf_bytes = (unsigned)((C * nsub * es + 1023) / 1024 * 1024);
     const size_t budget = 218 * 1024 - 1024;
@@ -443,6 +465,116 @@ int plan_tma(tfft_plan_s* p) {
     if (e != cudaSuccess) return cuda_fail(e);
     if (q.tbps < 1) continue;
     q.tma = 1;
+  }
+  return 0;
+}
+
+// The v3 kernel (compile-time geometry, warp-local lines) for every pass it
+// has an instantiation for: 256 threads x E values per tile (E = 16 for
+// complex64, 8 for complex128), element-major boxes split into column groups
+// of at most 128 bytes per row and moved with the matching TMA swizzle.
+int plan_v3(tfft_plan_s* p) {
+  if (!encode_fn()) return 0;
+  if (std::getenv("TFFT_TUNE_NO_V3")) return 0;
+  const bool c64 = p->dtype == TFFT_C64;
+  const int64_t u = (int64_t)p->esize / 8, es = (int64_t)p->esize;
+  const int64_t E = c64 ? 16 : 8, TILE = 256 * E;
+  const int64_t B = p->batch;
+  for (int i = 0; i < p->passes; i++) {
+    PassPlan& q = p->pp[i];
+    const int64_t nsub = q.nsub;
+    const int role = q.lines_are_signals ? 0 : (i == p->passes - 1 ? 2 : 1);
+    const int64_t C = TILE / nsub;
+    if (C < 1 || TILE % nsub) continue;
+    if (role == 0 && (C > p->G || p->G % C)) continue;
+    if (role != 0 && (C > q.LO || q.LO % C)) continue;
+    int bps = 0;
+    if (v3_attrs(p->dtype, role, (int)nsub, 48 * 1024, &bps) != cudaSuccess) { cudaGetLastError(); continue; }
+    TileMap mi{}, mo{};
+    MapGeom gi = q.gin, go = q.gout;
+    const int64_t rows = std::min<int64_t>(nsub, 256);
+    const int64_t CS = std::min<int64_t>(C, 128 / es);
+    const int rowb = (int)(CS * es);
+    const int swz = rowb >= 128 ? (int)CU_TENSOR_MAP_SWIZZLE_128B
+                  : rowb >= 64 ? (int)CU_TENSOR_MAP_SWIZZLE_64B
+                  : rowb >= 32 ? (int)CU_TENSOR_MAP_SWIZZLE_32B : (int)CU_TENSOR_MAP_SWIZZLE_NONE;
+    auto em = [&](TileMap& m, MapGeom& g) {
+      m.layout = 1;
+      m.nbox = (int)((nsub + rows - 1) / rows); m.box_rows = (int)rows; m.box_elems = (int)(rows * CS);
+      m.nbx = (int)(C / CS); m.bx_step = (int)(CS * u); m.bx_elems = (int)(nsub * CS);
+      g.box[0] = (uint32_t)(CS * u);
+      g.swizzle = swz;
+    };
+    const int64_t N1 = p->pp[0].nsub, M = p->n / N1;
+    if (role == 0) {
+      if (nsub * es % 16) continue;
+      mi.kind = mo.kind = 1; mi.layout = mo.layout = 0; mi.nbox = mo.nbox = 1; mi.nbx = mo.nbx = 1;
+      gi = MapGeom{}; go = MapGeom{};
+    } else if (role == 1) {
+      const bool first = i == 0;
+      mi.kind = mo.kind = first ? 2 : 3;
+      mi.ax = mo.ax = u;
+      if (first) {
+        mi.by = mo.by = N1;
+        gi = MapGeom{}; gi.rank = 2; gi.dims[0] = M * u; gi.dims[1] = B * N1; gi.strides[0] = M * es;
+        gi.box[1] = (uint32_t)rows;
+      } else {
+        const int64_t N3 = q.LO;
+        mi.az = mo.az = 1; mi.bz = mo.bz = N1;
+        gi = MapGeom{}; gi.rank = 3; gi.dims[0] = N3 * u; gi.dims[1] = nsub; gi.dims[2] = B * N1;
+        gi.strides[0] = N3 * es; gi.strides[1] = M * es; gi.box[1] = (uint32_t)rows; gi.box[2] = 1;
+      }
+      em(mi, gi);
+      go = gi;
+      em(mo, go);
+    } else {
+      // input: C rows of the line, line-major (rows split in runs of <= 256 units)
+      mi = TileMap{};
+      mi.kind = 3; mi.layout = 0; mi.nbox = 1; mi.nbx = 1;
+      gi = MapGeom{};
+      if (p->passes == 2) {
+        const int64_t S = std::min<int64_t>(nsub, 256 / u);
+        mi.bz = N1; mi.cz = 1;
+        gi.rank = 3; gi.dims[0] = S * u; gi.dims[1] = nsub / S; gi.dims[2] = B * N1;
+        gi.strides[0] = S * es; gi.strides[1] = nsub * es;
+        gi.box[0] = (uint32_t)(S * u); gi.box[1] = (uint32_t)(nsub / S); gi.box[2] = (uint32_t)C;
+      } else {
+        const int64_t N2 = q.HI;
+        if (nsub * u > 256) continue;
+        mi.ay = 1; mi.bz = N1; mi.cz = 1;
+        gi.rank = 3; gi.dims[0] = nsub * u; gi.dims[1] = N2; gi.dims[2] = B * N1;
+        gi.strides[0] = nsub * es; gi.strides[1] = M * es;
+        gi.box[0] = (uint32_t)(nsub * u); gi.box[1] = 1; gi.box[2] = (uint32_t)C;
+      }
+      if (p->passes == 2) {
+        mo.kind = 2; mo.ax = u; mo.by = nsub;
+        go = MapGeom{}; go.rank = 2; go.dims[0] = N1 * u; go.dims[1] = B * nsub; go.strides[0] = N1 * es;
+        go.box[1] = (uint32_t)rows;
+      } else {
+        const int64_t N3 = nsub, N2 = q.HI;
+        mo.kind = 3; mo.ax = u; mo.ay = 1; mo.bz = N3;
+        go = MapGeom{}; go.rank = 3; go.dims[0] = N1 * u; go.dims[1] = N2; go.dims[2] = B * N3;
+        go.strides[0] = N1 * es; go.strides[1] = N1 * N2 * es; go.box[1] = 1; go.box[2] = (uint32_t)rows;
+        // element-major rows along z for the three-pass output: one box of nsub rows
+        if (nsub > 256) continue;
+      }
+      em(mo, go);
+    }
+    if (role != 0 && (!geom_ok(gi) || !geom_ok(go))) continue;
+    mi.bytes = mo.bytes = (unsigned)(C * nsub * es);
+    const size_t scr = (size_t)v3_scratch_bytes(p->dtype, (int)nsub);
+    const unsigned buf = (unsigned)((C * nsub * es + 1023) / 1024 * 1024);
+    const size_t budget = 225 * 1024;
+    const size_t fixed = scr + 1024 + 1024;
+    if (fixed + 2 * (size_t)buf > budget) continue;
+    const int nbuf = (int)std::min<size_t>(6, (budget - fixed) / buf);
+    const size_t smem = (size_t)nbuf * buf + fixed;
+    if (v3_attrs(p->dtype, role, (int)nsub, smem, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
+    q.v3 = 1; q.role = role; q.tma = 1;
+    q.vC = (int)C;
+    q.vLB = q.lines_are_signals ? 1 : q.LO * q.HI / C;
+    q.map_in = mi; q.map_out = mo; q.gin = gi; q.gout = go;
+    q.nbuf = nbuf; q.buf_bytes = buf; q.tsmem = smem; q.tbps = bps;
   }
   return 0;
 }
@@ -617,6 +749,7 @@ int launch_pass(tfft_plan_s* p, PassParams& a, int i, int kind, cudaStream_t s) 
   }
   const int64_t maxgrid = (int64_t)p->sms * (tma ? q.tbps : q.bps);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.nchunks, maxgrid));
+  const bool v3 = tma && q.v3;
   TimedLaunch tl{};
   if (p->timing) {
     tl.kind = kind;
@@ -624,7 +757,9 @@ int launch_pass(tfft_plan_s* p, PassParams& a, int i, int kind, cudaStream_t s) 
     TFFT_CUDA(cudaEventRecord(tl.a, s));
   }
   cudaError_t e;
-  if (tma)
+  if (v3)
+    e = launch_v3(p->dtype, q.role, q.nsub, a, grid, q.tsmem, s);
+  else if (tma)
     e = p->dtype == TFFT_C64 ? launch_tile_f32(a, q.E, grid, q.tsmem, s) : launch_tile_f64(a, q.E, grid, q.tsmem, s);
   else
     e = p->dtype == TFFT_C64 ? launch_pass_f32(a, q.E, grid, q.smem, s) : launch_pass_f64(a, q.E, grid, q.smem, s);
@@ -670,6 +805,11 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
     a.batch = batch;
     a.in = (i == 0) ? in : p->tmp;
     a.out = (i == p->passes - 1) ? out : p->tmp;
+    if (main_exec && p->pp[i].v3) {
+      const PassPlan& q = p->pp[i];
+      a.C = q.vC; a.nthreads = 256; a.line_blocks = q.vLB;
+      a.nchunks = p->ngroups * q.parts * q.vLB;
+    }
     if (main_exec) {
       a.abft_in = p->abft && i == 0;
       a.abft_out = p->abft && i == p->passes - 1;
@@ -760,6 +900,8 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   p->sms = prop.multiProcessorCount;
   int rc = plan_build(p, o);
   if (!rc) rc = plan_tma(p);
+  if (!rc) rc = plan_v3(p);
+  if (!rc) plan_slots(p);
   if (!rc) rc = plan_tables(p);
   if (!rc) rc = plan_workspace(p);
   if (!rc) rc = plan_wtable(p);

@@ -99,9 +99,12 @@ struct Lists {
 struct TileMap {
   int kind;
   int layout;
-  int nbox;
+  int nbox;              // boxes along y (rows), y += box_rows, smem += box_elems
   int box_rows;
   int box_elems;
+  int nbx;               // boxes along x (column groups), x += bx_step, smem += bx_elems
+  int bx_step;
+  int bx_elems;
   unsigned bytes;        // bytes of the whole tile (all boxes)
   long long ax, ay, by, cy, az, bz, cz;
 };
@@ -178,6 +181,11 @@ cudaError_t launch_tile_f32(const PassParams& p, int E, int grid, size_t smem, c
 cudaError_t launch_tile_f64(const PassParams& p, int E, int grid, size_t smem, cudaStream_t s);
 cudaError_t tile_func_attrs_f32(int E, size_t smem, int block, int* blocks_per_sm);
 cudaError_t tile_func_attrs_f64(int E, size_t smem, int block, int* blocks_per_sm);
+// v3 kernels (fft_v3.cuh): role 0 single pass, 1 column pass, 2 last pass.
+// Return cudaErrorInvalidValue for an (nsub, role) without an instantiation.
+cudaError_t launch_v3(int dtype, int role, int nsub, const PassParams& p, int grid, size_t smem, cudaStream_t s);
+cudaError_t v3_attrs(int dtype, int role, int nsub, size_t smem, int* blocks_per_sm);
+int v3_scratch_bytes(int dtype, int nsub);
 
 // Verify / correction kernels (abft_fix.cu).
 struct VerifyParams {

@@ -1,0 +1,32 @@
+// v3_f64_single.cu -- instantiations of the v3 pass kernel: double values, role single.
+#include "fft_v3.cuh"
+
+namespace tfft {
+
+cudaError_t v3_launch_f64_single(int nsub, const PassParams& p, int grid, size_t smem, cudaStream_t s) {
+  switch (nsub) {
+    case 128: fft_v3_kernel<double, 128, 8, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
+    case 256: fft_v3_kernel<double, 256, 8, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
+    case 512: fft_v3_kernel<double, 512, 8, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
+    case 1024: fft_v3_kernel<double, 1024, 8, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
+    case 2048: fft_v3_kernel<double, 2048, 8, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t v3_attrs_f64_single(int nsub, size_t smem, int* bps) {
+  const void* f = nullptr;
+  switch (nsub) {
+    case 128: f = (const void*)fft_v3_kernel<double, 128, 8, 0>; break;
+    case 256: f = (const void*)fft_v3_kernel<double, 256, 8, 0>; break;
+    case 512: f = (const void*)fft_v3_kernel<double, 512, 8, 0>; break;
+    case 1024: f = (const void*)fft_v3_kernel<double, 1024, 8, 0>; break;
+    case 2048: f = (const void*)fft_v3_kernel<double, 2048, 8, 0>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, f, 256, smem);
+}
+
+}  // namespace tfft
