@@ -9,10 +9,17 @@
 //     per-thread base, the radix schedule is unrolled;
 //   * a tile has 256 threads x E values; when a line (NSUB values) is held by
 //     at most one warp, the warp owns whole lines and the radix stages
-//     exchange data through warp-private, padded ping-pong scratch with only
-//     __syncwarp; longer lines (single pass, NSUB > 32 E) share a named
-//     barrier among the warps of the line;
-//   * one block barrier per tile, before the TMA store of the output box;
+//     exchange data in place through the line's padded scratch with only
+//     __syncwarp; longer lines (NSUB > 32 E) share a named barrier among the
+//     warps of the line;
+//   * two blocks per SM for complex64 (at most 128 registers a thread, about
+//     100 KB of shared memory a block: two tile buffers and one scratch);
+//   * no block-wide barrier per tile: thread 0 starts the first tile loads,
+//     then each warp counts itself out of a tile with a shared-memory atomic
+//     and the last of the eight stores the tile and refills its buffer with
+//     the tile nbuf ahead; when the output box layout differs from the input
+//     box layout (the last pass), a second counter makes sure every warp has
+//     read its input before any output is written over it;
 //   * column tiles (element-major boxes) are moved by TMA with its 128-byte /
 //     64-byte shared-memory swizzle, which keeps the strided column reads of
 //     the first stage within two wavefronts;
@@ -60,35 +67,163 @@ struct V3 {
   // padded line-major scratch: one pad value per 128 bytes
   static constexpr int PG = 128 / ES;
   static constexpr int PITCH = NSUB + NSUB / PG + (NSUB < PG ? 1 : 0);
-  static constexpr int SCR = C * PITCH;                     // scratch values per buffer
+  static constexpr int SCR = C * PITCH;                     // scratch values
   static_assert(C >= 1 && TILE % NSUB == 0, "tile must hold whole lines");
   static_assert(WL || TPL % 32 == 0, "a line is held by whole warps");
 
-  // byte offset of value (c, i) in the dense input / output box
-  __device__ __forceinline__ static uint32_t box_off(bool lm, int c, int i) {
-    if (lm) return (uint32_t)((c * NSUB + i) * ES);
-    const uint32_t o = (uint32_t)(((c / CS) * NSUB + i) * ROWB + (c % CS) * ES);
-    return o ^ (((o >> 7) & SWZ) << 4);   // TMA 128 / 64 / 32-byte swizzle pattern
-  }
-  __device__ __forceinline__ static int scr_idx(int c, int i) { return c * PITCH + i + i / PG; }
 };
 
+__device__ __forceinline__ uint32_t atom_add_acq_rel(unsigned* a, unsigned v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_u32(a)), "r"(v)
+               : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void red_add_release(unsigned* a, unsigned v) {
+  asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_u32(a)), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* a) {
+  unsigned v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(a)) : "memory");
+  return v;
+}
+
+// Bounded wait on an mbarrier phase; gives up early once another warp has
+// recorded a timeout in *abort.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  for (long long it = 0; it < kWaitLimit; it++) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 1023) == 1023 && *abort) return false;
+  }
+  return false;
+}
+
+// Block reduction of the partials (256 threads), one record per chunk.
+template <typename real>
+__device__ void reduce_block_records(Partials<real>& a, const PassParams& p, long long g, long long slot,
+                                     double* red) {
+  const unsigned full = 0xffffffffu;
+  real v[9] = {a.s1r, a.s1i, a.s2r, a.s2i, a.en, a.t1r, a.t1i, a.t2r, a.t2i};
+  long long mn = a.nf_min, mx = a.nf_max;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 9; q++) v[q] += __shfl_xor_sync(full, v[q], off);
+    mn = min(mn, __shfl_xor_sync(full, mn, off));
+    mx = max(mx, __shfl_xor_sync(full, mx, off));
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 9; q++) red[warp * 12 + q] = (double)v[q];
+    reinterpret_cast<long long*>(red)[warp * 12 + 9] = mn;
+    reinterpret_cast<long long*>(red)[warp * 12 + 10] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    long long m0 = 0x7fffffffffffffffLL, m1 = -1;
+    for (int w = 0; w < 8; w++) {
+#pragma unroll
+      for (int q = 0; q < 9; q++) s[q] += red[w * 12 + q];
+      m0 = min(m0, reinterpret_cast<long long*>(red)[w * 12 + 9]);
+      m1 = max(m1, reinterpret_cast<long long*>(red)[w * 12 + 10]);
+    }
+    if (p.abft_in) {
+      RecIn r;
+      r.s1r = s[0]; r.s1i = s[1]; r.s2r = s[2]; r.s2i = s[3]; r.energy = s[4];
+      r.pad0 = r.pad1 = r.pad2 = 0.0;
+      p.rec_in[g * p.slots + slot] = r;
+    }
+    if (p.abft_out) {
+      RecOut r;
+      r.t1r = s[5]; r.t1i = s[6]; r.t2r = s[7]; r.t2i = s[8];
+      r.nf_min = m0; r.nf_max = m1; r.pad0 = r.pad1 = 0.0;
+      p.rec_out[g * p.slots + slot] = r;
+    }
+  }
+  __syncthreads();
+}
+
+// Shared-memory offsets of the per-thread access patterns.  Every pattern is
+// a per-thread base plus a compile-time offset: idx(x) = x + x / PG is
+// additive over the (base, offset) splits used below because each base is
+// a multiple of PG or each offset keeps the sum inside the base's PG group.
+template <typename G>
+struct V3Addr {
+  __host__ __device__ static constexpr int idx(int x) { return x + x / G::PG; }
+  // box byte offset of (c, j + m) for a compile-time m that is a multiple of TPL
+  // (base_swz is the swizzled base_lin; an offset that is a multiple of 1024
+  // bytes leaves the swizzle bits 7..9 alone)
+  template <bool LM>
+  __device__ __forceinline__ static uint32_t box(uint32_t base_lin, uint32_t base_swz, int m) {
+    if constexpr (LM) {
+      return base_lin + (uint32_t)(m * G::ES);
+    } else {
+      const uint32_t mo = (uint32_t)(m * G::ROWB);
+      if ((mo & 1023u) == 0) return base_swz + mo;
+      const uint32_t o = base_lin + mo;
+      return o ^ (((o >> 7) & G::SWZ) << 4);
+    }
+  }
+};
+
+// Blocks per SM the register budget targets: two for complex64 (at most 128
+// registers a thread), one for complex128, whose values take twice the registers.
+template <typename real>
+constexpr int v3_min_blocks() { return sizeof(real) == 4 ? 2 : 1; }
+
+// 256 threads (eight warps), two blocks per SM for complex64.  Thread 0 starts the first
+// nbuf tile loads; afterwards the last warp to finish a tile stores it and
+// refills its buffer with the tile nbuf ahead, so no warp waits for another
+// except on data that has not arrived yet.
 template <typename real, int NSUB, int E, int ROLE>
-__global__ void __launch_bounds__(256, 1)
-fft_v3_kernel(const __grid_constant__ PassParams p) {
+__global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(const __grid_constant__ PassParams p) {
   using G = V3<real, NSUB, E, ROLE>;
+  using A = V3Addr<G>;
   using cT = typename G::cT;
+  static_assert(E % G::PG == 0, "a thread's stage-0 values start on a pad group");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32 * 12];
+  __shared__ double red[8 * 12];
+  __shared__ TileCursor ldc[8];
+  __shared__ unsigned arrivals[8];   // per buffer: warps done with the tile, cumulative
+  __shared__ unsigned readers[8];    // per buffer: warps done reading the input box, cumulative
+  __shared__ int s_abort;
 
   const int t = threadIdx.x;
   const int warp = t >> 5, lane = t & 31;
   const int nbuf = p.nbuf;
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)nbuf * p.buf_bytes);
-  cT* scr0 = reinterpret_cast<cT*>(base + (size_t)nbuf * p.buf_bytes + 1024);
-  cT* scr1 = scr0 + G::SCR;
-  auto box = [&](int s) { return base + (size_t)s * p.buf_bytes; };
+  cT* scr = reinterpret_cast<cT*>(base + (size_t)nbuf * p.buf_bytes + 1024);
+  volatile int* abort_flag = &s_abort;
+
+  if (t == 0) {
+    for (int s = 0; s < nbuf; s++) {
+      mbar_init(&full[s], 1);
+      arrivals[s] = 0;
+      readers[s] = 0;
+    }
+    fence_mbar_init();
+    s_abort = 0;
+    if (blockIdx.x == 0) {
+      if (p.zero_on_entry[0]) *p.zero_on_entry[0] = 0;
+      if (p.zero_on_entry[1]) *p.zero_on_entry[1] = 0;
+    }
+  }
+  __syncthreads();
+  if (t == 0) {
+    TileCursor ld;
+    ld.start(p);
+    for (int s = 0; s < nbuf && ld.valid(p); s++) {
+      issue_load(p, ld, reinterpret_cast<cT*>(base + (size_t)s * p.buf_bytes), &full[s]);
+      ld.advance(p);
+    }
+    for (int w = 0; w < 8; w++) ldc[w] = ld;
+  }
+  __syncthreads();
+
   const cT* tws = reinterpret_cast<const cT*>(p.tw_sub);
   const bool abft = p.abft_in || p.abft_out;
   const bool inject = p.fault.mode != 0 && p.fault.pass == p.pass_index;
@@ -101,30 +236,22 @@ fft_v3_kernel(const __grid_constant__ PassParams p) {
     if constexpr (G::WL) {
       __syncwarp();
     } else if constexpr (G::WPL * 32 == G::T) {
-      __syncthreads();
+      asm volatile("bar.sync 1, 256;" ::: "memory");
     } else {
-      asm volatile("bar.sync %0, %1;" ::"r"(1 + c0), "r"(32 * G::WPL) : "memory");
+      asm volatile("bar.sync %0, %1;" ::"r"(2 + c0), "r"(32 * G::WPL) : "memory");
     }
   };
 
-  if (t == 0) {
-    for (int s = 0; s < nbuf; s++) mbar_init(&full[s], 1);
-    fence_mbar_init();
-    if (blockIdx.x == 0) {
-      if (p.zero_on_entry[0]) *p.zero_on_entry[0] = 0;
-      if (p.zero_on_entry[1]) *p.zero_on_entry[1] = 0;
-    }
-  }
-  __syncthreads();
-
-  TileCursor prod;
-  if (t == 0) {
-    prod.start(p);
-    for (int s = 0; s < nbuf - 1 && prod.valid(p); s++) {
-      issue_load(p, prod, reinterpret_cast<cT*>(box(s)), &full[s]);
-      prod.advance(p);
-    }
-  }
+  // per-thread shared-memory bases
+  const int scr_c = c0 * G::PITCH;
+  const int s_rd = scr_c + A::idx(j0);            // reads at j0 + m  (m a multiple of TPL)
+  const int s_wr0 = scr_c + A::idx(j0 * E);       // stage-0 writes at j0 E + q
+  auto lin_base = [&](bool lm) -> uint32_t {
+    return lm ? (uint32_t)((c0 * NSUB + j0) * G::ES)
+              : (uint32_t)(((c0 / G::CS) * NSUB + j0) * G::ROWB + (c0 % G::CS) * G::ES);
+  };
+  const uint32_t b_in = lin_base(G::LM_IN), b_out = lin_base(G::LM_OUT);
+  const uint32_t z_in = b_in ^ (((b_in >> 7) & G::SWZ) << 4), z_out = b_out ^ (((b_out >> 7) & G::SWZ) << 4);
 
   cT wv[E];
   unsigned smask = 0;
@@ -134,7 +261,7 @@ fft_v3_kernel(const __grid_constant__ PassParams p) {
   auto setup_positions = [&](long long hi, long long lo0) {
     if (p.abft_in) {
       const cT* wtab = reinterpret_cast<const cT*>(p.wtab);
-      const long long lo = G::LM_IN && ROLE == V3_SINGLE ? 0 : lo0 + c0;
+      const long long lo = ROLE == V3_SINGLE ? 0 : lo0 + c0;
 #pragma unroll
       for (int r = 0; r < E; r++) {
         const int i = j0 + r * G::TPL;
@@ -164,8 +291,10 @@ fft_v3_kernel(const __grid_constant__ PassParams p) {
     }
   };
   const int dl = (int)(((long long)G::NBL * p.out_es) % 3);   // 1 or 2
+  bool aborted = false;
 
-  int k = 0;
+  int s = 0;             // ring buffer of the current tile
+  unsigned wrap = 0;     // completed passes over the ring
   for (long long chunk = blockIdx.x; chunk < p.nchunks; chunk += gridDim.x) {
     TileCursor cur;
     cur.chunk = chunk;
@@ -175,7 +304,7 @@ fft_v3_kernel(const __grid_constant__ PassParams p) {
       if (abft && !p.list) {
         acc.zero();
         if constexpr (ROLE == V3_SINGLE) reduce_warp_and_store(acc, p, cur.g, slot0 + warp);
-        else reduce_and_store(acc, p, cur.g, slot0, red);
+        else reduce_block_records(acc, p, cur.g, slot0, red);
       }
       continue;
     }
@@ -185,33 +314,39 @@ fft_v3_kernel(const __grid_constant__ PassParams p) {
       setup_done = true;
     }
     if (abft) acc.zero();
-    const long long gb = cur.gb, se = cur.se;
+    const long long se = cur.se;
+    const long long lo_c = (ROLE == V3_SINGLE) ? 0 : lo0 + c0;
+    const long long line_c = (ROLE == V3_SINGLE) ? 0 : hi * p.LO + lo_c;
+    // checksum weight (b - first signal of the group + 1) of this thread's signal
+    real wgt = (real)(int)(cur.sb - cur.gb + (ROLE == V3_SINGLE ? c0 : 0) + 1);
+    constexpr int BSTEP = ROLE == V3_SINGLE ? G::C : 1;
 
-    for (long long tb = cur.sb; tb < se; tb += (ROLE == V3_SINGLE ? G::C : 1), k++) {
-      const int s = k % nbuf;
-      const uint32_t parity = (uint32_t)((k / nbuf) & 1);
-      unsigned char* tile = box(s);
-      {
-        bool ok = false;
-        for (long long it = 0; it < kWaitLimit && !ok; it++) ok = mbar_try_wait(&full[s], parity);
-        if (__syncthreads_or(!ok)) {
-          if (t == 0) {
-            atomicExch(p.err_flag, 1);
-            bulk_wait_0();
-          }
-          return;
-        }
+    for (long long tb = cur.sb; tb < se; tb += BSTEP, wgt += (real)BSTEP) {
+      unsigned char* tile = base + (size_t)s * p.buf_bytes;
+      if (!aborted && !mbar_wait_bounded(&full[s], wrap & 1u, abort_flag)) {
+        aborted = true;
+        *abort_flag = 1;
+        atomicExch(p.err_flag, 1);
       }
+      // after a timeout the warp still runs the tile (on whatever the buffer
+      // holds) so that every line barrier is reached; the error flag is set
       const long long b0 = (ROLE == V3_SINGLE) ? tb + c0 : tb;     // this thread's signal
       const bool valid = b0 < se;
-      const long long lo_c = (ROLE == V3_SINGLE) ? 0 : lo0 + c0;
-      const long long line_c = (ROLE == V3_SINGLE) ? 0 : hi * p.LO + lo_c;
+      // the stage at which this thread plants the test fault (none: -9)
+      const int fst = (inject && valid && fault_signal(p.fault, b0) && p.fault.line == line_c) ? p.fault.stage
+                                                                                               : -9;
 
       // ---------------- stage 0: box -> registers ----------------
       cT v[E];
 #pragma unroll
       for (int r = 0; r < E; r++)
-        v[r] = *reinterpret_cast<const cT*>(tile + G::box_off(G::LM_IN, c0, j0 + r * G::TPL));
+        v[r] = *reinterpret_cast<const cT*>(tile + A::template box<G::LM_IN>(b_in, z_in, r * G::TPL));
+      if constexpr (G::LM_IN != G::LM_OUT) {
+        // the output box overlaps other warps' input lines: announce that
+        // this warp's input values are in registers
+        __syncwarp();
+        if (lane == 0) red_add_release(&readers[s], 1u);
+      }
       if (p.abft_in && valid) {
         real sr = 0, si = 0, en = 0;
 #pragma unroll
@@ -220,69 +355,61 @@ fft_v3_kernel(const __grid_constant__ PassParams p) {
           si = fma(wv[r].x, v[r].y, si); si = fma(wv[r].y, v[r].x, si);
           en = fma(v[r].x, v[r].x, en); en = fma(v[r].y, v[r].y, en);
         }
-        const real wgt = (real)(b0 - gb + 1);
         acc.s1r += sr; acc.s1i += si;
         acc.s2r = fma(wgt, sr, acc.s2r); acc.s2i = fma(wgt, si, acc.s2i);
         acc.en += en;
       }
-      if (inject && p.fault.stage == -1 && valid && fault_signal(p.fault, b0) && p.fault.line == line_c) {
+      if (fst == -1) {
 #pragma unroll
         for (int r = 0; r < E; r++)
           if (p.fault.index == j0 + r * G::TPL) v[r] = faulted(v[r], p.fault);
       }
 
-      // ---------------- radix stages 0 .. S-2 (shared scratch) ----------------
+      // ---------------- radix stages 0 .. S-2 (in place in the line scratch) ----------------
       if constexpr (G::S > 1) {
         Dft<E>::run(v);
+        if (fst == 0) {
 #pragma unroll
-        for (int q = 0; q < E; q++) {
-          const int i = j0 * E + q;
-          if (inject && p.fault.stage == 0 && valid && fault_signal(p.fault, b0) && p.fault.line == line_c &&
-              p.fault.index == i)
-            v[q] = faulted(v[q], p.fault);
-          scr0[G::scr_idx(c0, i)] = v[q];
+          for (int q = 0; q < E; q++)
+            if (p.fault.index == j0 * E + q) v[q] = faulted(v[q], p.fault);
         }
+        if constexpr (!G::WL) line_sync();   // the previous tile's last-stage reads are done
+#pragma unroll
+        for (int q = 0; q < E; q++) scr[s_wr0 + A::idx(q)] = v[q];
         line_sync();
 #pragma unroll
         for (int st = 1; st < G::S - 1; st++) {
           const int Ns = v3_ipow(E, st);
-          const cT* src = (st & 1) ? scr0 : scr1;
-          cT* dst = (st & 1) ? scr1 : scr0;
 #pragma unroll
-          for (int r = 0; r < E; r++) v[r] = src[G::scr_idx(c0, j0 + r * G::TPL)];
+          for (int r = 0; r < E; r++) v[r] = scr[s_rd + A::idx(r * G::TPL)];
+          line_sync();                          // the whole line is read before it is overwritten
           const int kk = j0 % Ns;
           stage_twiddle<E>(v, tws, kk * (NSUB / (Ns * E)) * p.tw_sub_stride);
           Dft<E>::run(v);
           const int basei = (j0 / Ns) * Ns * E + kk;
+          if (fst == st) {
 #pragma unroll
-          for (int q = 0; q < E; q++) {
-            const int i = basei + q * Ns;
-            if (inject && p.fault.stage == st && valid && fault_signal(p.fault, b0) && p.fault.line == line_c &&
-                p.fault.index == i)
-              v[q] = faulted(v[q], p.fault);
-            dst[G::scr_idx(c0, i)] = v[q];
+            for (int q = 0; q < E; q++)
+              if (p.fault.index == basei + q * Ns) v[q] = faulted(v[q], p.fault);
           }
+          const int wb = scr_c + A::idx(basei);
+#pragma unroll
+          for (int q = 0; q < E; q++) scr[wb + A::idx(q * Ns)] = v[q];
           line_sync();
         }
-      }
-
-      // ---------------- last stage -> registers -> output box ----------------
-      cT u[E];
-      if constexpr (G::S > 1) {
-        const cT* src = ((G::S - 1) & 1) ? scr0 : scr1;
+        // last stage reads
 #pragma unroll
         for (int ub = 0; ub < G::BPT; ub++)
 #pragma unroll
           for (int r = 0; r < G::RL; r++)
-            u[ub * G::RL + r] = src[G::scr_idx(c0, j0 + ub * G::TPL + r * G::NBL)];
-      } else {
-#pragma unroll
-        for (int r = 0; r < E; r++) u[r] = v[r];
+            v[ub * G::RL + r] = scr[s_rd + A::idx(ub * G::TPL + r * G::NBL)];
       }
+
+      // ---------------- last stage -> registers -> output box ----------------
       constexpr int NsL = G::NBL;   // E^(S-1)
 #pragma unroll
       for (int ub = 0; ub < G::BPT; ub++) {
-        cT* w = u + ub * G::RL;
+        cT* w = v + ub * G::RL;
         const int jl = j0 + ub * G::TPL;
         if constexpr (G::S > 1) stage_twiddle<G::RL>(w, tws, jl * (NSUB / (NsL * G::RL)) * p.tw_sub_stride);
         Dft<G::RL>::run(w);
@@ -296,7 +423,7 @@ fft_v3_kernel(const __grid_constant__ PassParams p) {
             if (q + 1 < G::RL) f = c_mul(f, step);
           }
         }
-        if (inject && p.fault.stage == G::S - 1 && valid && fault_signal(p.fault, b0) && p.fault.line == line_c) {
+        if (fst == G::S - 1) {
 #pragma unroll
           for (int q = 0; q < G::RL; q++)
             if (p.fault.index == jl + q * G::NBL) w[q] = faulted(w[q], p.fault);
@@ -318,7 +445,6 @@ fft_v3_kernel(const __grid_constant__ PassParams p) {
           real ti = a0i + (hr * a1i + s1 * a1r) + (hr * a2i - s1 * a2r);
           if (kz == 1) { real x = hr * tr + hs * ti; ti = hr * ti - hs * tr; tr = x; }
           else if (kz == 2) { real x = hr * tr - hs * ti; ti = hr * ti + hs * tr; tr = x; }
-          const real wgt = (real)(b0 - gb + 1);
           acc.t1r += tr; acc.t1i += ti;
           acc.t2r = fma(wgt, tr, acc.t2r); acc.t2i = fma(wgt, ti, acc.t2i);
           if (!(isfinite(tr) && isfinite(ti))) {
@@ -327,32 +453,55 @@ fft_v3_kernel(const __grid_constant__ PassParams p) {
           }
         }
       }
-      if constexpr (G::S == 1 || !G::WL) line_sync();   // the box is still read by this line's threads
+      if constexpr (G::S == 1) line_sync();
+      if constexpr (G::LM_IN != G::LM_OUT) {
+        // every warp has read its input from the box before any output lands there
+        if (lane == 0) {
+          const unsigned want = 8u * (wrap + 1u);
+          long long it = 0;
+          while (ld_acquire(&readers[s]) < want) {
+            if (++it >= kWaitLimit || ((it & 1023) == 0 && *abort_flag)) {
+              *abort_flag = 1;
+              atomicExch(p.err_flag, 1);
+              break;
+            }
+          }
+        }
+        __syncwarp();
+      }
 #pragma unroll
       for (int ub = 0; ub < G::BPT; ub++)
 #pragma unroll
         for (int q = 0; q < G::RL; q++)
-          *reinterpret_cast<cT*>(tile + G::box_off(G::LM_OUT, c0, j0 + ub * G::TPL + q * G::NBL)) =
-              u[ub * G::RL + q];
+          *reinterpret_cast<cT*>(tile + A::template box<G::LM_OUT>(b_out, z_out, ub * G::TPL + q * G::NBL)) =
+              v[ub * G::RL + q];
+
+      // hand the tile back: this warp's box writes become visible to the TMA
+      // unit, the eighth warp to arrive stores the tile and refills the buffer
       fence_proxy_async();
-      __syncthreads();
-      if (t == 0) {
-        issue_store(p, tb, se, hi, lo0, reinterpret_cast<const cT*>(tile));
-        bulk_commit();
-        bulk_wait_read_1();
-        if (prod.valid(p)) {
-          const int sp = (k + nbuf - 1) % nbuf;
-          issue_load(p, prod, reinterpret_cast<cT*>(box(sp)), &full[sp]);
-          prod.advance(p);
+      __syncwarp();
+      if (lane == 0) {
+        const unsigned old = atom_add_acq_rel(&arrivals[s], 1u);
+        TileCursor& ld = ldc[warp];
+        if (old == 8u * wrap + 7u && !*abort_flag) {
+          issue_store(p, tb, se, hi, lo0, reinterpret_cast<const cT*>(tile));
+          bulk_commit();
+          if (ld.valid(p)) {
+            bulk_wait_read_0();               // the store has read the buffer
+            issue_load(p, ld, reinterpret_cast<cT*>(tile), &full[s]);
+          }
         }
+        ld.advance(p);
       }
+      __syncwarp();
+      if (++s == nbuf) { s = 0; wrap++; }
     }
     if (abft) {
       if constexpr (ROLE == V3_SINGLE) reduce_warp_and_store(acc, p, cur.g, slot0 + warp);
-      else reduce_and_store(acc, p, cur.g, slot0, red);
+      else reduce_block_records(acc, p, cur.g, slot0, red);
     }
   }
-  if (t == 0) bulk_wait_0();
+  if (lane == 0) bulk_wait_0();
 }
 
 }  // namespace tfft

@@ -88,6 +88,7 @@ struct PassPlan {
   int tma = 0, nbuf = 0, tbps = 1;
   int v3 = 0, role = 0;            // v3 kernel (compile-time geometry) and its role
   int vC = 0;                      // v3 lines per tile
+  int vdt = 0;                     // v3 kernel family (launch_v3 dtype code)
   int64_t vLB = 0;                 // v3 line blocks per signal
   unsigned buf_bytes = 0;
   size_t tsmem = 0;
@@ -478,6 +479,7 @@ int plan_v3(tfft_plan_s* p) {
   if (std::getenv("TFFT_TUNE_NO_V3")) return 0;
   const bool c64 = p->dtype == TFFT_C64;
   const int64_t u = (int64_t)p->esize / 8, es = (int64_t)p->esize;
+  const int vdt = c64 ? 0 : 1;
   const int64_t E = c64 ? 16 : 8, TILE = 256 * E;
   const int64_t B = p->batch;
   for (int i = 0; i < p->passes; i++) {
@@ -489,7 +491,7 @@ int plan_v3(tfft_plan_s* p) {
     if (role == 0 && (C > p->G || p->G % C)) continue;
     if (role != 0 && (C > q.LO || q.LO % C)) continue;
     int bps = 0;
-    if (v3_attrs(p->dtype, role, (int)nsub, 48 * 1024, &bps) != cudaSuccess) { cudaGetLastError(); continue; }
+    if (v3_attrs(vdt, role, (int)nsub, 48 * 1024, &bps) != cudaSuccess) { cudaGetLastError(); continue; }
     TileMap mi{}, mo{};
     MapGeom gi = q.gin, go = q.gout;
     const int64_t rows = std::min<int64_t>(nsub, 256);
@@ -562,15 +564,17 @@ int plan_v3(tfft_plan_s* p) {
     }
     if (role != 0 && (!geom_ok(gi) || !geom_ok(go))) continue;
     mi.bytes = mo.bytes = (unsigned)(C * nsub * es);
-    const size_t scr = (size_t)v3_scratch_bytes(p->dtype, (int)nsub);
+    const size_t scr = (size_t)v3_scratch_bytes(vdt, (int)nsub);
     const unsigned buf = (unsigned)((C * nsub * es + 1023) / 1024 * 1024);
-    const size_t budget = 225 * 1024;
+    // complex64: two blocks per SM, each with at most 110 KB of dynamic
+    // shared memory; complex128: one block per SM
+    const size_t budget = (c64 ? 110 : 220) * 1024;
     const size_t fixed = scr + 1024 + 1024;
     if (fixed + 2 * (size_t)buf > budget) continue;
-    const int nbuf = (int)std::min<size_t>(6, (budget - fixed) / buf);
+    const int nbuf = (int)std::min<size_t>(4, (budget - fixed) / buf);
     const size_t smem = (size_t)nbuf * buf + fixed;
-    if (v3_attrs(p->dtype, role, (int)nsub, smem, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
-    q.v3 = 1; q.role = role; q.tma = 1;
+    if (v3_attrs(vdt, role, (int)nsub, smem, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
+    q.v3 = 1; q.role = role; q.tma = 1; q.vdt = vdt;
     q.vC = (int)C;
     q.vLB = q.lines_are_signals ? 1 : q.LO * q.HI / C;
     q.map_in = mi; q.map_out = mo; q.gin = gi; q.gout = go;
@@ -758,7 +762,7 @@ int launch_pass(tfft_plan_s* p, PassParams& a, int i, int kind, cudaStream_t s) 
   }
   cudaError_t e;
   if (v3)
-    e = launch_v3(p->dtype, q.role, q.nsub, a, grid, q.tsmem, s);
+    e = launch_v3(q.vdt, q.role, q.nsub, a, grid, q.tsmem, s);
   else if (tma)
     e = p->dtype == TFFT_C64 ? launch_tile_f32(a, q.E, grid, q.tsmem, s) : launch_tile_f64(a, q.E, grid, q.tsmem, s);
   else

@@ -38,12 +38,12 @@ cudaError_t v3_attrs(int dtype, int role, int nsub, size_t smem, int* bps) {
   return v3_attrs_f64_last(nsub, smem, bps);
 }
 
-// Bytes of the two ping-pong scratch buffers of a v3 kernel.
+// Bytes of the padded line scratch of a v3 kernel.
 int v3_scratch_bytes(int dtype, int nsub) {
-  const int es = dtype == 0 ? 8 : 16, e = dtype == 0 ? 16 : 8;
+  const int es = dtype == 1 ? 16 : 8, e = dtype == 0 ? 16 : 8;
   const int tile = 256 * e, c = tile / nsub, pg = 128 / es;
   const int pitch = nsub + nsub / pg + (nsub < pg ? 1 : 0);
-  return 2 * c * pitch * es;
+  return c * pitch * es;
 }
 
 }  // namespace tfft
