@@ -158,8 +158,8 @@ struct TileCursor {
   }
 };
 
-template <typename cT>
-__device__ __forceinline__ void issue_load(const PassParams& p, const TileCursor& cur, cT* dst,
+template <typename cT, typename Cursor>
+__device__ __forceinline__ void issue_load(const PassParams& p, const Cursor& cur, cT* dst,
                                            uint64_t* bar) {
   const TileMap& m = p.map_in;
   if (m.kind == 1) {

@@ -55,9 +55,8 @@ struct V3 {
   static constexpr int LPW = WL ? 32 / TPL : 1;             // lines per warp
   static constexpr int WPL = WL ? 1 : TPL / 32;             // warps per line
   static constexpr int S = v3_stages(NSUB, E);              // radix stages
-  static constexpr int RL = NSUB / v3_ipow(E, S - 1);       // last radix
-  static constexpr int NBL = NSUB / RL;                     // last-stage butterflies per line
-  static constexpr int BPT = E / RL;                        // last-stage butterflies per thread
+  static constexpr int R0 = NSUB / v3_ipow(E, S - 1);       // radix of stage 0; later stages radix E
+  static constexpr int BPT0 = E / R0;                       // stage-0 butterflies per thread
   static constexpr bool LM_IN = (ROLE == V3_SINGLE || ROLE == V3_LAST);
   static constexpr bool LM_OUT = (ROLE == V3_SINGLE);
   // element-major boxes: columns in groups of CS (<= 128 bytes per row)
@@ -70,6 +69,10 @@ struct V3 {
   static constexpr int SCR = C * PITCH;                     // scratch values
   static_assert(C >= 1 && TILE % NSUB == 0, "tile must hold whole lines");
   static_assert(WL || TPL % 32 == 0, "a line is held by whole warps");
+  static_assert(S >= 2, "at least two radix stages");
+  // scratch offsets split into a per-thread base and a compile-time part
+  // (idx(x) = x + x / PG is additive over these splits; see V3Addr)
+  static constexpr bool SPLIT0 = (TPL * R0) % PG == 0 && PG % R0 == 0;
 
 };
 
@@ -99,52 +102,112 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
-// Block reduction of the partials (256 threads), one record per chunk.
+// One warp's checksum record (single pass): the nine partial sums are
+// reduced by recursive halving -- at each of four shuffle rounds a lane keeps
+// half of its values and receives its partner's copy of them -- and a last
+// exchange completes the sums, so lane L ends with the warp total of value
+// idx(L) = 5 b4 + 3 b3 + 2 b2 + b1 (b_k = bit k of L; a few lanes hold a
+// padding value).  Twelve shuffles instead of 45; every lane that holds a
+// value writes its word of the record.  The nonfinite range is reduced only
+// when some lane has one.
 template <typename real>
-__device__ void reduce_block_records(Partials<real>& a, const PassParams& p, long long g, long long slot,
-                                     double* red) {
+__device__ __forceinline__ void warp_records(const Partials<real>& a, const PassParams& p, long long g,
+                                             long long slot) {
   const unsigned full = 0xffffffffu;
-  real v[9] = {a.s1r, a.s1i, a.s2r, a.s2i, a.en, a.t1r, a.t1i, a.t2r, a.t2i};
+  const int lane = threadIdx.x & 31;
+  const real v[10] = {a.s1r, a.s1i, a.s2r, a.s2i, a.en, a.t1r, a.t1i, a.t2r, a.t2i, (real)0};
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+  real u[6];
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+    u[i] = (h4 ? v[i + 5] : v[i]) + __shfl_xor_sync(full, h4 ? v[i] : v[i + 5], 16);
+  u[5] = (real)0;
+  real w[4];
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+    w[i] = (h3 ? u[i + 3] : u[i]) + __shfl_xor_sync(full, h3 ? u[i] : u[i + 3], 8);
+  w[3] = (real)0;
+  real x[2];
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+    x[i] = (h2 ? w[i + 2] : w[i]) + __shfl_xor_sync(full, h2 ? w[i] : w[i + 2], 4);
+  real y = (h1 ? x[1] : x[0]) + __shfl_xor_sync(full, h1 ? x[0] : x[1], 2);
+  y += __shfl_xor_sync(full, y, 1);
+  const int r1 = (h3 ? 3 : 0) + (h2 ? 2 : 0) + (h1 ? 1 : 0);
+  const int idx = (h4 ? 5 : 0) + r1;
+  const bool holds = !(lane & 1) && !(h2 && h1) && !(h3 && h2) && idx < 9;
+
   long long mn = a.nf_min, mx = a.nf_max;
+  if (__any_sync(full, mx >= 0)) {
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-    for (int q = 0; q < 9; q++) v[q] += __shfl_xor_sync(full, v[q], off);
-    mn = min(mn, __shfl_xor_sync(full, mn, off));
-    mx = max(mx, __shfl_xor_sync(full, mx, off));
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < 9; q++) red[warp * 12 + q] = (double)v[q];
-    reinterpret_cast<long long*>(red)[warp * 12 + 9] = mn;
-    reinterpret_cast<long long*>(red)[warp * 12 + 10] = mx;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    long long m0 = 0x7fffffffffffffffLL, m1 = -1;
-    for (int w = 0; w < 8; w++) {
-#pragma unroll
-      for (int q = 0; q < 9; q++) s[q] += red[w * 12 + q];
-      m0 = min(m0, reinterpret_cast<long long*>(red)[w * 12 + 9]);
-      m1 = max(m1, reinterpret_cast<long long*>(red)[w * 12 + 10]);
-    }
-    if (p.abft_in) {
-      RecIn r;
-      r.s1r = s[0]; r.s1i = s[1]; r.s2r = s[2]; r.s2i = s[3]; r.energy = s[4];
-      r.pad0 = r.pad1 = r.pad2 = 0.0;
-      p.rec_in[g * p.slots + slot] = r;
-    }
-    if (p.abft_out) {
-      RecOut r;
-      r.t1r = s[5]; r.t1i = s[6]; r.t2r = s[7]; r.t2i = s[8];
-      r.nf_min = m0; r.nf_max = m1; r.pad0 = r.pad1 = 0.0;
-      p.rec_out[g * p.slots + slot] = r;
+    for (int off = 16; off > 0; off >>= 1) {
+      mn = min(mn, __shfl_xor_sync(full, mn, off));
+      mx = max(mx, __shfl_xor_sync(full, mx, off));
     }
   }
-  __syncthreads();
+  if (holds) {
+    if (idx < 5) {
+      if (p.abft_in) reinterpret_cast<double*>(p.rec_in + g * p.slots + slot)[idx] = (double)y;
+    } else if (p.abft_out) {
+      reinterpret_cast<double*>(p.rec_out + g * p.slots + slot)[idx - 5] = (double)y;
+    }
+  }
+  if (p.abft_out && lane == 1) {
+    RecOut* r = p.rec_out + g * p.slots + slot;
+    r->nf_min = mn;
+    r->nf_max = mx;
+  }
 }
+
+// The chunks of one thread block and their tiles, as TileCursor, for the v3
+// kernels (never a work list): C, LO and the line-block count are powers of
+// two, so the decomposition is shifts and masks except for the split of a
+// group into parts, and the one-part, one-line-block cases skip even that.
+struct V3Cursor {
+  long long tb, gb, sb, se;
+  long long chunk;
+  unsigned lb, part, g;
+  __device__ __forceinline__ bool decode(const PassParams& p) {
+    const unsigned c = (unsigned)chunk;
+    unsigned rest = c;
+    lb = 0;
+    if (p.log2LB) { rest = c >> p.log2LB; lb = c & ((1u << p.log2LB) - 1u); }
+    part = 0;
+    g = rest;
+    if (p.parts != 1) { g = rest / (unsigned)p.parts; part = rest - g * (unsigned)p.parts; }
+    gb = (long long)g * p.group;
+    const long long ge = min((long long)p.batch, gb + (long long)p.group);
+    if (p.parts == 1) {
+      sb = gb;
+      se = ge;
+    } else {
+      const int lu = p.lines_are_signals ? p.log2C : 0;
+      const unsigned ntiles = (unsigned)((ge - gb + (1ll << lu) - 1) >> lu);
+      const unsigned per = (ntiles + (unsigned)p.parts - 1u) / (unsigned)p.parts;
+      sb = gb + ((long long)(part * per) << lu);
+      se = min(ge, sb + ((long long)per << lu));
+    }
+    return sb < se;
+  }
+  __device__ __forceinline__ void settle(const PassParams& p) {
+    while (chunk < p.nchunks) {
+      if (decode(p)) { tb = sb; return; }
+      chunk += gridDim.x;
+    }
+  }
+  __device__ __forceinline__ void start(const PassParams& p) { chunk = blockIdx.x; settle(p); }
+  __device__ __forceinline__ bool valid(const PassParams& p) const { return chunk < p.nchunks; }
+  __device__ __forceinline__ void advance(const PassParams& p) {
+    tb += p.lines_are_signals ? p.C : 1;
+    if (tb >= se) { chunk += gridDim.x; settle(p); }
+  }
+  __device__ __forceinline__ long long hi(const PassParams& p) const {
+    return p.lines_are_signals ? 0 : ((long long)lb << p.log2C) >> p.log2LO;
+  }
+  __device__ __forceinline__ long long lo0(const PassParams& p) const {
+    return p.lines_are_signals ? 0 : ((long long)lb << p.log2C) & ((1ll << p.log2LO) - 1);
+  }
+};
 
 // Shared-memory offsets of the per-thread access patterns.  Every pattern is
 // a per-thread base plus a compile-time offset: idx(x) = x + x / PG is
@@ -185,8 +248,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
   using cT = typename G::cT;
   static_assert(E % G::PG == 0, "a thread's stage-0 values start on a pad group");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[8 * 12];
-  __shared__ TileCursor ldc[8];
+  __shared__ V3Cursor ldc[8];
   __shared__ unsigned arrivals[8];   // per buffer: warps done with the tile, cumulative
   __shared__ unsigned readers[8];    // per buffer: warps done reading the input box, cumulative
   __shared__ int s_abort;
@@ -214,7 +276,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
   }
   __syncthreads();
   if (t == 0) {
-    TileCursor ld;
+    V3Cursor ld;
     ld.start(p);
     for (int s = 0; s < nbuf && ld.valid(p); s++) {
       issue_load(p, ld, reinterpret_cast<cT*>(base + (size_t)s * p.buf_bytes), &full[s]);
@@ -245,7 +307,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
   // per-thread shared-memory bases
   const int scr_c = c0 * G::PITCH;
   const int s_rd = scr_c + A::idx(j0);            // reads at j0 + m  (m a multiple of TPL)
-  const int s_wr0 = scr_c + A::idx(j0 * E);       // stage-0 writes at j0 E + q
+  const int s_wr0 = scr_c + A::idx(j0 * G::R0);   // stage-0 writes at j0 R0 + (u TPL R0 + q)
   auto lin_base = [&](bool lm) -> uint32_t {
     return lm ? (uint32_t)((c0 * NSUB + j0) * G::ES)
               : (uint32_t)(((c0 / G::CS) * NSUB + j0) * G::ROWB + (c0 % G::CS) * G::ES);
@@ -253,9 +315,11 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
   const uint32_t b_in = lin_base(G::LM_IN), b_out = lin_base(G::LM_OUT);
   const uint32_t z_in = b_in ^ (((b_in >> 7) & G::SWZ) << 4), z_out = b_out ^ (((b_out >> 7) & G::SWZ) << 4);
 
+  // The output stage is radix E with one butterfly per thread: thread j0 of
+  // a line produces the outputs k = j0 + q TPL, q < E, of its line.
   cT wv[E];
-  unsigned smask = 0;
-  unsigned k0mask = 0;          // (k mod 3) of each last-stage butterfly, 2 bits each
+  unsigned smask = 0;           // sign bit of r_k for each of the thread's outputs
+  int k0 = 0;                   // (k of output q = 0) mod 3
   Partials<real> acc;
   bool setup_done = false;
   auto setup_positions = [&](long long hi, long long lo0) {
@@ -271,40 +335,35 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
       }
     }
     smask = 0;
-    k0mask = 0;
+    k0 = 0;
     if (p.abft_out) {
       const long long lo = (ROLE == V3_SINGLE) ? 0 : lo0 + c0;
-      const long long kb = hi * p.out_hi + lo * p.out_lo;
+      const long long kp0 = hi * p.out_hi + lo * p.out_lo + (long long)j0 * p.out_es;
+      k0 = (int)(kp0 % 3);
+      if (p.rvec == RVEC_SIGNED_WANG) {
 #pragma unroll
-      for (int u = 0; u < G::BPT; u++) {
-        const int jl = j0 + u * G::TPL;
-        const long long kp0 = kb + (long long)jl * p.out_es;
-        k0mask |= (unsigned)(kp0 % 3) << (2 * u);
-        if (p.rvec == RVEC_SIGNED_WANG) {
-#pragma unroll
-          for (int q = 0; q < G::RL; q++) {
-            const long long kpos = kp0 + (long long)(q * G::NBL) * p.out_es;
-            smask |= (unsigned)(splitmix64_at(p.rseed, (unsigned long long)kpos) >> 63) << (u * G::RL + q);
-          }
+        for (int q = 0; q < E; q++) {
+          const long long kpos = kp0 + (long long)(q * G::TPL) * p.out_es;
+          smask |= (unsigned)(splitmix64_at(p.rseed, (unsigned long long)kpos) >> 63) << q;
         }
       }
     }
   };
-  const int dl = (int)(((long long)G::NBL * p.out_es) % 3);   // 1 or 2
+  const int dl = (int)(((long long)G::TPL * p.out_es) % 3);   // 1 or 2: k steps by TPL out_es
   bool aborted = false;
 
   int s = 0;             // ring buffer of the current tile
   unsigned wrap = 0;     // completed passes over the ring
   for (long long chunk = blockIdx.x; chunk < p.nchunks; chunk += gridDim.x) {
-    TileCursor cur;
+    V3Cursor cur;
     cur.chunk = chunk;
     const bool nonempty = cur.decode(p);
-    const long long slot0 = (long long)(cur.part * p.line_blocks + cur.lb) * (ROLE == V3_SINGLE ? 8 : 1);
+    // one checksum record per warp and chunk
+    const long long slot = (long long)(cur.part * p.line_blocks + cur.lb) * 8 + warp;
     if (!nonempty) {
       if (abft && !p.list) {
         acc.zero();
-        if constexpr (ROLE == V3_SINGLE) reduce_warp_and_store(acc, p, cur.g, slot0 + warp);
-        else reduce_block_records(acc, p, cur.g, slot0, red);
+        warp_records(acc, p, cur.g, slot);
       }
       continue;
     }
@@ -317,6 +376,13 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
     const long long se = cur.se;
     const long long lo_c = (ROLE == V3_SINGLE) ? 0 : lo0 + c0;
     const long long line_c = (ROLE == V3_SINGLE) ? 0 : hi * p.LO + lo_c;
+    // inter-pass twiddles of the column pass: output q of this thread is
+    // multiplied by omega^(lo (j0 + q TPL)) = tw_base tw_step^q
+    cT tw_base = {(real)1, (real)0}, tw_step = {(real)1, (real)0};
+    if (ROLE == V3_COLS && p.twiddle) {
+      tw_base = twN<cT>(p, lo_c * (long long)j0 * p.tw_scale);
+      tw_step = twN<cT>(p, lo_c * (long long)G::TPL * p.tw_scale);
+    }
     // checksum weight (b - first signal of the group + 1) of this thread's signal
     real wgt = (real)(int)(cur.sb - cur.gb + (ROLE == V3_SINGLE ? c0 : 0) + 1);
     constexpr int BSTEP = ROLE == V3_SINGLE ? G::C : 1;
@@ -336,7 +402,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
       const int fst = (inject && valid && fault_signal(p.fault, b0) && p.fault.line == line_c) ? p.fault.stage
                                                                                                : -9;
 
-      // ---------------- stage 0: box -> registers ----------------
+      // ---------------- stage 0: box -> registers, radix R0 -> scratch ----------------
       cT v[E];
 #pragma unroll
       for (int r = 0; r < E; r++)
@@ -364,96 +430,100 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
         for (int r = 0; r < E; r++)
           if (p.fault.index == j0 + r * G::TPL) v[r] = faulted(v[r], p.fault);
       }
+      // butterfly u of stage 0 takes v[u + m BPT0] (inputs j0 + u TPL + m NSUB / R0)
+      // and writes its output q to position (j0 + u TPL) R0 + q
+#pragma unroll
+      for (int u = 0; u < G::BPT0; u++) {
+        cT w[G::R0];
+#pragma unroll
+        for (int m = 0; m < G::R0; m++) w[m] = v[u + m * G::BPT0];
+        Dft<G::R0>::run(w);
+#pragma unroll
+        for (int m = 0; m < G::R0; m++) v[u + m * G::BPT0] = w[m];
+      }
+      if (fst == 0) {
+#pragma unroll
+        for (int u = 0; u < G::BPT0; u++)
+#pragma unroll
+          for (int q = 0; q < G::R0; q++)
+            if (p.fault.index == (j0 + u * G::TPL) * G::R0 + q) v[u + q * G::BPT0] = faulted(v[u + q * G::BPT0], p.fault);
+      }
+      if constexpr (!G::WL) line_sync();   // the previous tile's last-stage reads are done
+#pragma unroll
+      for (int u = 0; u < G::BPT0; u++)
+#pragma unroll
+        for (int q = 0; q < G::R0; q++) {
+          if constexpr (G::SPLIT0)
+            scr[s_wr0 + A::idx(u * G::TPL * G::R0 + q)] = v[u + q * G::BPT0];
+          else
+            scr[scr_c + A::idx((j0 + u * G::TPL) * G::R0 + q)] = v[u + q * G::BPT0];
+        }
+      line_sync();
 
-      // ---------------- radix stages 0 .. S-2 (in place in the line scratch) ----------------
-      if constexpr (G::S > 1) {
+      // ---------------- stages 1 .. S-2: radix E, in place in the line scratch ----------------
+#pragma unroll
+      for (int st = 1; st < G::S - 1; st++) {
+        const int Ns = G::R0 * v3_ipow(E, st - 1);
+#pragma unroll
+        for (int r = 0; r < E; r++) v[r] = scr[s_rd + A::idx(r * G::TPL)];
+        line_sync();                          // the whole line is read before it is overwritten
+        const int kk = j0 % Ns;
+        stage_twiddle<E>(v, tws, kk * (NSUB / (Ns * E)) * p.tw_sub_stride);
         Dft<E>::run(v);
-        if (fst == 0) {
+        const int basei = (j0 / Ns) * Ns * E + kk;
+        if (fst == st) {
 #pragma unroll
           for (int q = 0; q < E; q++)
-            if (p.fault.index == j0 * E + q) v[q] = faulted(v[q], p.fault);
+            if (p.fault.index == basei + q * Ns) v[q] = faulted(v[q], p.fault);
         }
-        if constexpr (!G::WL) line_sync();   // the previous tile's last-stage reads are done
+        const int wb = scr_c + A::idx(basei);
 #pragma unroll
-        for (int q = 0; q < E; q++) scr[s_wr0 + A::idx(q)] = v[q];
+        for (int q = 0; q < E; q++) scr[wb + A::idx(q * Ns)] = v[q];
         line_sync();
-#pragma unroll
-        for (int st = 1; st < G::S - 1; st++) {
-          const int Ns = v3_ipow(E, st);
-#pragma unroll
-          for (int r = 0; r < E; r++) v[r] = scr[s_rd + A::idx(r * G::TPL)];
-          line_sync();                          // the whole line is read before it is overwritten
-          const int kk = j0 % Ns;
-          stage_twiddle<E>(v, tws, kk * (NSUB / (Ns * E)) * p.tw_sub_stride);
-          Dft<E>::run(v);
-          const int basei = (j0 / Ns) * Ns * E + kk;
-          if (fst == st) {
-#pragma unroll
-            for (int q = 0; q < E; q++)
-              if (p.fault.index == basei + q * Ns) v[q] = faulted(v[q], p.fault);
-          }
-          const int wb = scr_c + A::idx(basei);
-#pragma unroll
-          for (int q = 0; q < E; q++) scr[wb + A::idx(q * Ns)] = v[q];
-          line_sync();
-        }
-        // last stage reads
-#pragma unroll
-        for (int ub = 0; ub < G::BPT; ub++)
-#pragma unroll
-          for (int r = 0; r < G::RL; r++)
-            v[ub * G::RL + r] = scr[s_rd + A::idx(ub * G::TPL + r * G::NBL)];
       }
 
-      // ---------------- last stage -> registers -> output box ----------------
-      constexpr int NsL = G::NBL;   // E^(S-1)
+      // ---------------- last stage: radix E -> registers -> output box ----------------
 #pragma unroll
-      for (int ub = 0; ub < G::BPT; ub++) {
-        cT* w = v + ub * G::RL;
-        const int jl = j0 + ub * G::TPL;
-        if constexpr (G::S > 1) stage_twiddle<G::RL>(w, tws, jl * (NSUB / (NsL * G::RL)) * p.tw_sub_stride);
-        Dft<G::RL>::run(w);
-        if (ROLE == V3_COLS && p.twiddle) {
-          const cT base_t = twN<cT>(p, lo_c * (long long)jl * p.tw_scale);
-          const cT step = twN<cT>(p, lo_c * (long long)G::NBL * p.tw_scale);
-          cT f = base_t;
+      for (int r = 0; r < E; r++) v[r] = scr[s_rd + A::idx(r * G::TPL)];
+      stage_twiddle<E>(v, tws, j0 * p.tw_sub_stride);     // Ns = TPL, kk = j0
+      Dft<E>::run(v);
+      if (ROLE == V3_COLS && p.twiddle) {
+        cT f = tw_base;
 #pragma unroll
-          for (int q = 0; q < G::RL; q++) {
-            w[q] = c_mul(w[q], f);
-            if (q + 1 < G::RL) f = c_mul(f, step);
-          }
-        }
-        if (fst == G::S - 1) {
-#pragma unroll
-          for (int q = 0; q < G::RL; q++)
-            if (p.fault.index == jl + q * G::NBL) w[q] = faulted(w[q], p.fault);
-        }
-        if (p.abft_out && valid) {
-          real a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
-#pragma unroll
-          for (int q = 0; q < G::RL; q++) {
-            const bool neg = (smask >> (ub * G::RL + q)) & 1u;
-            const real yr = neg ? -w[q].x : w[q].x, yi = neg ? -w[q].y : w[q].y;
-            if (q % 3 == 0) { a0r += yr; a0i += yi; }
-            else if (q % 3 == 1) { a1r += yr; a1i += yi; }
-            else { a2r += yr; a2i += yi; }
-          }
-          const int kz = (k0mask >> (2 * ub)) & 3;
-          const real hr = (real)-0.5, hs = (real)0.86602540378443864676;
-          const real s1 = (dl == 1) ? -hs : hs;
-          real tr = a0r + (hr * a1r - s1 * a1i) + (hr * a2r + s1 * a2i);
-          real ti = a0i + (hr * a1i + s1 * a1r) + (hr * a2i - s1 * a2r);
-          if (kz == 1) { real x = hr * tr + hs * ti; ti = hr * ti - hs * tr; tr = x; }
-          else if (kz == 2) { real x = hr * tr - hs * ti; ti = hr * ti + hs * tr; tr = x; }
-          acc.t1r += tr; acc.t1i += ti;
-          acc.t2r = fma(wgt, tr, acc.t2r); acc.t2i = fma(wgt, ti, acc.t2i);
-          if (!(isfinite(tr) && isfinite(ti))) {
-            acc.nf_min = min(acc.nf_min, (long long)b0);
-            acc.nf_max = max(acc.nf_max, (long long)b0);
-          }
+        for (int q = 0; q < E; q++) {
+          v[q] = c_mul(v[q], f);
+          if (q + 1 < E) f = c_mul(f, tw_step);
         }
       }
-      if constexpr (G::S == 1) line_sync();
+      if (fst == G::S - 1) {
+#pragma unroll
+        for (int q = 0; q < E; q++)
+          if (p.fault.index == j0 + q * G::TPL) v[q] = faulted(v[q], p.fault);
+      }
+      if (p.abft_out && valid) {
+        // T += sum_q s_q w3^(k0 + q dl) y_q: group the outputs by q mod 3
+        real a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
+#pragma unroll
+        for (int q = 0; q < E; q++) {
+          const bool neg = (smask >> q) & 1u;
+          const real yr = neg ? -v[q].x : v[q].x, yi = neg ? -v[q].y : v[q].y;
+          if (q % 3 == 0) { a0r += yr; a0i += yi; }
+          else if (q % 3 == 1) { a1r += yr; a1i += yi; }
+          else { a2r += yr; a2i += yi; }
+        }
+        const real hr = (real)-0.5, hs = (real)0.86602540378443864676;
+        const real s1 = (dl == 1) ? -hs : hs;
+        real tr = a0r + (hr * a1r - s1 * a1i) + (hr * a2r + s1 * a2i);
+        real ti = a0i + (hr * a1i + s1 * a1r) + (hr * a2i - s1 * a2r);
+        if (k0 == 1) { real x = hr * tr + hs * ti; ti = hr * ti - hs * tr; tr = x; }
+        else if (k0 == 2) { real x = hr * tr - hs * ti; ti = hr * ti + hs * tr; tr = x; }
+        acc.t1r += tr; acc.t1i += ti;
+        acc.t2r = fma(wgt, tr, acc.t2r); acc.t2i = fma(wgt, ti, acc.t2i);
+        if (!(isfinite(tr) && isfinite(ti))) {
+          acc.nf_min = min(acc.nf_min, (long long)b0);
+          acc.nf_max = max(acc.nf_max, (long long)b0);
+        }
+      }
       if constexpr (G::LM_IN != G::LM_OUT) {
         // every warp has read its input from the box before any output lands there
         if (lane == 0) {
@@ -470,11 +540,8 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
         __syncwarp();
       }
 #pragma unroll
-      for (int ub = 0; ub < G::BPT; ub++)
-#pragma unroll
-        for (int q = 0; q < G::RL; q++)
-          *reinterpret_cast<cT*>(tile + A::template box<G::LM_OUT>(b_out, z_out, ub * G::TPL + q * G::NBL)) =
-              v[ub * G::RL + q];
+      for (int q = 0; q < E; q++)
+        *reinterpret_cast<cT*>(tile + A::template box<G::LM_OUT>(b_out, z_out, q * G::TPL)) = v[q];
 
       // hand the tile back: this warp's box writes become visible to the TMA
       // unit, the eighth warp to arrive stores the tile and refills the buffer
@@ -482,7 +549,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
       __syncwarp();
       if (lane == 0) {
         const unsigned old = atom_add_acq_rel(&arrivals[s], 1u);
-        TileCursor& ld = ldc[warp];
+        V3Cursor& ld = ldc[warp];
         if (old == 8u * wrap + 7u && !*abort_flag) {
           issue_store(p, tb, se, hi, lo0, reinterpret_cast<const cT*>(tile));
           bulk_commit();
@@ -496,10 +563,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
       __syncwarp();
       if (++s == nbuf) { s = 0; wrap++; }
     }
-    if (abft) {
-      if constexpr (ROLE == V3_SINGLE) reduce_warp_and_store(acc, p, cur.g, slot0 + warp);
-      else reduce_block_records(acc, p, cur.g, slot0, red);
-    }
+    if (abft) warp_records(acc, p, cur.g, slot);
   }
   if (lane == 0) bulk_wait_0();
 }

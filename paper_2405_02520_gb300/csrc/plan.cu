@@ -336,9 +336,9 @@ void plan_slots(tfft_plan_s* p) {
   }
   const PassPlan& f = p->pp[0];
   const PassPlan& l = p->pp[p->passes - 1];
-  // v3 writes one record per warp and chunk in the single pass, one per chunk otherwise
-  p->slots_in = (int64_t)f.parts * (f.v3 ? f.vLB * (f.role == 0 ? 8 : 1) : f.line_blocks);
-  p->slots_out = (int64_t)l.parts * (l.v3 ? l.vLB * (l.role == 0 ? 8 : 1) : l.line_blocks);
+  // v3 writes one record per warp and chunk, the other kernels one per chunk
+  p->slots_in = (int64_t)f.parts * (f.v3 ? f.vLB * 8 : f.line_blocks);
+  p->slots_out = (int64_t)l.parts * (l.v3 ? l.vLB * 8 : l.line_blocks);
 }
 
 // cuTensorMapEncodeTiled, fetched from the driver through the runtime (no
@@ -490,6 +490,8 @@ int plan_v3(tfft_plan_s* p) {
     if (C < 1 || TILE % nsub) continue;
     if (role == 0 && (C > p->G || p->G % C)) continue;
     if (role != 0 && (C > q.LO || q.LO % C)) continue;
+    // chunk indices are 32-bit in the v3 kernels (chunks <= groups x line blocks x G)
+    if (p->ngroups * (q.lines_are_signals ? 1 : q.LO * q.HI / C) * (int64_t)p->G >= (int64_t(1) << 31)) continue;
     int bps = 0;
     if (v3_attrs(vdt, role, (int)nsub, 48 * 1024, &bps) != cudaSuccess) { cudaGetLastError(); continue; }
     TileMap mi{}, mo{};
@@ -813,6 +815,7 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
       const PassPlan& q = p->pp[i];
       a.C = q.vC; a.nthreads = 256; a.line_blocks = q.vLB;
       a.nchunks = p->ngroups * q.parts * q.vLB;
+      a.log2C = ilog2(q.vC); a.log2LO = ilog2(q.LO); a.log2LB = ilog2(q.vLB);
     }
     if (main_exec) {
       a.abft_in = p->abft && i == 0;

@@ -161,6 +161,7 @@ struct PassParams {
   int64_t list_block;     // signals per listed block
 
   int64_t nchunks;
+  int log2C, log2LO, log2LB;   // log2 of C, LO and line_blocks (all powers of two; v3 kernels)
   FaultSite fault;
 
   // ---- TMA tile pipeline (fft_tile_kernel only) ----
