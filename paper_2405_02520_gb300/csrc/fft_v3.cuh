@@ -42,11 +42,28 @@ __host__ __device__ constexpr int v3_stages(int nsub, int e) {
   return s < 1 ? 1 : s;
 }
 __host__ __device__ constexpr int v3_ipow(int b, int k) { return k == 0 ? 1 : b * v3_ipow(b, k - 1); }
+// Entries of the stage-twiddle table: stages 1 .. S-1 (radix e, Ns = R0 e^(st-1))
+// each hold omega_{Ns e}^(q kk) for q = 1 .. e-1, kk < Ns, as [q-1][kk].
+__host__ __device__ constexpr int v3_tw_entries(int nsub, int e) {
+  const int s = v3_stages(nsub, e), r0 = nsub / v3_ipow(e, s - 1);
+  int n = 0;
+  for (int st = 1; st < s; st++) n += (e - 1) * r0 * v3_ipow(e, st - 1);
+  return n;
+}
+__host__ __device__ constexpr int v3_tw_offset(int nsub, int e, int stage) {
+  const int s = v3_stages(nsub, e), r0 = nsub / v3_ipow(e, s - 1);
+  int n = 0;
+  for (int st = 1; st < stage; st++) n += (e - 1) * r0 * v3_ipow(e, st - 1);
+  return n;
+}
+// The table is staged in shared memory when it takes at most this many bytes.
+constexpr int kV3TwSmemMax = 8192;
 
 template <typename real, int NSUB, int E, int ROLE>
 struct V3 {
   using cT = typename Cplx<real>::T;
   static constexpr int ES = (int)sizeof(cT);                // 8 or 16 bytes
+  static constexpr int NSUBV = NSUB;
   static constexpr int T = 256;                             // threads per block
   static constexpr int TILE = T * E;                        // values per tile
   static constexpr int C = TILE / NSUB;                     // lines per tile
@@ -67,6 +84,8 @@ struct V3 {
   static constexpr int PG = 128 / ES;
   static constexpr int PITCH = NSUB + NSUB / PG + (NSUB < PG ? 1 : 0);
   static constexpr int SCR = C * PITCH;                     // scratch values
+  static constexpr int TWN = v3_tw_entries(NSUB, E);        // stage-twiddle table entries
+  static constexpr bool TWS = TWN * ES <= kV3TwSmemMax;     // ... staged in shared memory
   static_assert(C >= 1 && TILE % NSUB == 0, "tile must hold whole lines");
   static_assert(WL || TPL % 32 == 0, "a line is held by whole warps");
   static_assert(S >= 2, "at least two radix stages");
@@ -232,6 +251,59 @@ struct V3Addr {
   }
 };
 
+// Copies a finished tile (or rows [r_begin, r_end) of an element-major box)
+// from its shared-memory box to the output, one warp, 16 bytes a lane per
+// access.  The box is laid out as the TMA would store it:
+// line-major (single pass: the tile's signals are contiguous in memory), or
+// element-major rows of ROWB bytes in column groups of CS lines with the TMA
+// swizzle (column and last passes: row i of group gx holds element i of lines
+// lo0 + gx CS .. + CS - 1, which are adjacent in memory).  Plain loads and
+// stores leave nothing in flight that still reads the box, so the buffer can be
+// refilled right after.
+template <typename G, int ROLE>
+__device__ __forceinline__ void copy_out(const PassParams& p, long long tb, long long se, long long hi,
+                                         long long lo0, const unsigned char* tile, int lane, int r_begin = 0,
+                                         int r_end = G::NSUBV) {
+  using cT = typename G::cT;
+  unsigned char* out = reinterpret_cast<unsigned char*>(p.out);
+  if constexpr (ROLE == V3_SINGLE) {
+    const long long rows = min((long long)G::C, se - tb);
+    const int chunks = (int)(rows * (G::NSUBV * G::ES / 16));
+    unsigned char* dst = out + tb * p.n * G::ES;
+    int i = lane;
+    for (; i + 96 < chunks; i += 128) {
+      const float4 a = *reinterpret_cast<const float4*>(tile + 16 * i);
+      const float4 b = *reinterpret_cast<const float4*>(tile + 16 * (i + 32));
+      const float4 c = *reinterpret_cast<const float4*>(tile + 16 * (i + 64));
+      const float4 d = *reinterpret_cast<const float4*>(tile + 16 * (i + 96));
+      __stcs(reinterpret_cast<float4*>(dst + 16 * i), a);
+      __stcs(reinterpret_cast<float4*>(dst + 16 * (i + 32)), b);
+      __stcs(reinterpret_cast<float4*>(dst + 16 * (i + 64)), c);
+      __stcs(reinterpret_cast<float4*>(dst + 16 * (i + 96)), d);
+    }
+    for (; i < chunks; i += 32)
+      __stcs(reinterpret_cast<float4*>(dst + 16 * i), *reinterpret_cast<const float4*>(tile + 16 * i));
+  } else {
+    constexpr int CPR = G::ROWB / 16;           // 16-byte chunks per box row
+    constexpr int RPI = 32 / CPR;               // rows per warp access
+    static_assert(G::ROWB % 16 == 0 && CPR <= 32, "box rows are whole 16-byte chunks");
+    const int j = lane % CPR, rr = lane / CPR;
+    const long long row_stride = p.out_es * G::ES;
+#pragma unroll 1
+    for (int gx = 0; gx < G::C / G::CS; gx++) {
+      unsigned char* dst = out + (tb * p.n + hi * p.out_hi + (lo0 + gx * G::CS) * p.out_lo) * G::ES +
+                           rr * row_stride + 16 * j;
+      const uint32_t o0 = (uint32_t)((gx * G::NSUBV + rr) * G::ROWB + 16 * j);
+#pragma unroll 4
+      for (int r0 = r_begin; r0 < r_end; r0 += RPI) {
+        const uint32_t o = o0 + (uint32_t)(r0 * G::ROWB);
+        const float4 v = *reinterpret_cast<const float4*>(tile + (o ^ (((o >> 7) & G::SWZ) << 4)));
+        __stcs(reinterpret_cast<float4*>(dst + (long long)r0 * row_stride), v);
+      }
+    }
+  }
+}
+
 // Blocks per SM the register budget targets: two for complex64 (at most 128
 // registers a thread), one for complex128, whose values take twice the registers.
 template <typename real>
@@ -251,6 +323,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
   __shared__ V3Cursor ldc[8];
   __shared__ unsigned arrivals[8];   // per buffer: warps done with the tile, cumulative
   __shared__ unsigned readers[8];    // per buffer: warps done reading the input box, cumulative
+  __shared__ unsigned copied[8];     // per buffer: warps done copying the tile out (last pass), cumulative
   __shared__ int s_abort;
 
   const int t = threadIdx.x;
@@ -266,6 +339,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
       mbar_init(&full[s], 1);
       arrivals[s] = 0;
       readers[s] = 0;
+      copied[s] = 0;
     }
     fence_mbar_init();
     s_abort = 0;
@@ -284,9 +358,15 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
     }
     for (int w = 0; w < 8; w++) ldc[w] = ld;
   }
+  // stage twiddles: from the plan's table, staged next to the scratch when small
+  const cT* twt = reinterpret_cast<const cT*>(p.tw_stage);
+  if constexpr (G::TWS) {
+    cT* tsm = scr + G::SCR;
+    for (int i = t; i < G::TWN; i += G::T) tsm[i] = twt[i];
+    twt = tsm;
+  }
   __syncthreads();
 
-  const cT* tws = reinterpret_cast<const cT*>(p.tw_sub);
   const bool abft = p.abft_in || p.abft_out;
   const bool inject = p.fault.mode != 0 && p.fault.pass == p.pass_index;
 
@@ -468,7 +548,11 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
         for (int r = 0; r < E; r++) v[r] = scr[s_rd + A::idx(r * G::TPL)];
         line_sync();                          // the whole line is read before it is overwritten
         const int kk = j0 % Ns;
-        stage_twiddle<E>(v, tws, kk * (NSUB / (Ns * E)) * p.tw_sub_stride);
+        {
+          const cT* tw = twt + v3_tw_offset(NSUB, E, st) + kk;
+#pragma unroll
+          for (int q = 1; q < E; q++) v[q] = c_mul(v[q], G::TWS ? tw[(q - 1) * Ns] : ldg_c(tw + (q - 1) * Ns));
+        }
         Dft<E>::run(v);
         const int basei = (j0 / Ns) * Ns * E + kk;
         if (fst == st) {
@@ -485,7 +569,12 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
       // ---------------- last stage: radix E -> registers -> output box ----------------
 #pragma unroll
       for (int r = 0; r < E; r++) v[r] = scr[s_rd + A::idx(r * G::TPL)];
-      stage_twiddle<E>(v, tws, j0 * p.tw_sub_stride);     // Ns = TPL, kk = j0
+      {
+        // Ns = TPL, kk = j0
+        const cT* tw = twt + v3_tw_offset(NSUB, E, G::S - 1) + j0;
+#pragma unroll
+        for (int q = 1; q < E; q++) v[q] = c_mul(v[q], G::TWS ? tw[(q - 1) * G::TPL] : ldg_c(tw + (q - 1) * G::TPL));
+      }
       Dft<E>::run(v);
       if (ROLE == V3_COLS && p.twiddle) {
         cT f = tw_base;
@@ -543,24 +632,57 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
       for (int q = 0; q < E; q++)
         *reinterpret_cast<cT*>(tile + A::template box<G::LM_OUT>(b_out, z_out, q * G::TPL)) = v[q];
 
-      // hand the tile back: this warp's box writes become visible to the TMA
-      // unit, the eighth warp to arrive stores the tile and refills the buffer
-      fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) {
-        const unsigned old = atom_add_acq_rel(&arrivals[s], 1u);
-        V3Cursor& ld = ldc[warp];
-        if (old == 8u * wrap + 7u && !*abort_flag) {
-          issue_store(p, tb, se, hi, lo0, reinterpret_cast<const cT*>(tile));
-          bulk_commit();
-          if (ld.valid(p)) {
-            bulk_wait_read_0();               // the store has read the buffer
-            issue_load(p, ld, reinterpret_cast<cT*>(tile), &full[s]);
+      if constexpr (ROLE != V3_LAST) {
+        // hand the tile back: this warp's box writes become visible to the TMA
+        // unit, the eighth warp to arrive stores the tile and refills the buffer
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+          const unsigned old = atom_add_acq_rel(&arrivals[s], 1u);
+          V3Cursor& ld = ldc[warp];
+          if (old == 8u * wrap + 7u && !*abort_flag) {
+            issue_store(p, tb, se, hi, lo0, reinterpret_cast<const cT*>(tile));
+            bulk_commit();
+            if (ld.valid(p)) {
+              bulk_wait_read_0();               // the store has read the buffer
+              issue_load(p, ld, reinterpret_cast<cT*>(tile), &full[s]);
+            }
+          }
+          ld.advance(p);
+        }
+        __syncwarp();
+      } else {
+        // the last pass's element-major box is written by all warps: once all
+        // eight have written, each copies out its eighth of the rows with
+        // plain stores, and the last to finish refills the buffer (no store
+        // in flight holds the box)
+        __syncwarp();
+        if (lane == 0) {
+          red_add_release(&arrivals[s], 1u);
+          const unsigned want = 8u * (wrap + 1u);
+          long long it = 0;
+          while (ld_acquire(&arrivals[s]) < want) {
+            if (++it >= kWaitLimit || ((it & 1023) == 0 && *abort_flag)) {
+              *abort_flag = 1;
+              atomicExch(p.err_flag, 1);
+              break;
+            }
           }
         }
-        ld.advance(p);
+        __syncwarp();
+        copy_out<G, ROLE>(p, tb, se, hi, lo0, tile, lane, warp * (NSUB / 8), (warp + 1) * (NSUB / 8));
+        __syncwarp();
+        if (lane == 0) {
+          V3Cursor& ld = ldc[warp];
+          const unsigned old = atom_add_acq_rel(&copied[s], 1u);
+          if (old == 8u * wrap + 7u && !*abort_flag && ld.valid(p)) {
+            fence_proxy_async();
+            issue_load(p, ld, reinterpret_cast<cT*>(tile), &full[s]);
+          }
+          ld.advance(p);
+        }
+        __syncwarp();
       }
-      __syncwarp();
       if (++s == nbuf) { s = 0; wrap++; }
     }
     if (abft) warp_records(acc, p, cur.g, slot);

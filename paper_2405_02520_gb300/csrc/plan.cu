@@ -101,6 +101,7 @@ struct PassPlan {
   int64_t tw_scale = 1;
   size_t smem = 0;
   int bps = 1;       // resident blocks per SM
+  void* vtw = nullptr;               // v3 stage-twiddle table
 };
 
 struct TimedLaunch {
@@ -180,6 +181,8 @@ void free_plan(tfft_plan_s* p) {
                   p->err_flag};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  for (auto& q : p->pp)
+    if (q.vtw) cudaFree(q.vtw);
   for (auto& t : p->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
   for (auto e : p->event_pool) cudaEventDestroy(e);
   delete p;
@@ -571,7 +574,7 @@ int plan_v3(tfft_plan_s* p) {
     // complex64: two blocks per SM, each with at most 110 KB of dynamic
     // shared memory; complex128: one block per SM
     const size_t budget = (c64 ? 110 : 220) * 1024;
-    const size_t fixed = scr + 1024 + 1024;
+    const size_t fixed = scr + (size_t)v3_twiddle_smem_bytes(vdt, (int)nsub) + 1024 + 1024;
     if (fixed + 2 * (size_t)buf > budget) continue;
     const int nbuf = (int)std::min<size_t>(4, (budget - fixed) / buf);
     const size_t smem = (size_t)nbuf * buf + fixed;
@@ -596,6 +599,30 @@ int plan_tables(tfft_plan_s* p) {
     std::vector<double> re(T), im(T);
     for (int m = 0; m < T; m++) unit_root(m, T, &re[m], &im[m]);
     if ((rc = upload(p, &p->tw_sub, re, im))) return rc;
+  }
+  // v3 stage twiddles: for stages st = 1 .. S-1 (radix E, Ns = R0 E^(st-1)),
+  // omega_{Ns E}^(q kk) for q = 1 .. E-1, kk < Ns, laid out [q-1][kk]
+  for (int i = 0; i < p->passes; i++) {
+    PassPlan& q = p->pp[i];
+    if (!q.v3) continue;
+    const int E = p->dtype == TFFT_C64 ? 16 : 8;
+    int S = 0;
+    for (int64_t v = 1; v < q.nsub; v *= E) S++;
+    S = std::max(S, 1);
+    int64_t EP = 1;
+    for (int k = 0; k < S - 1; k++) EP *= E;
+    const int64_t R0 = q.nsub / EP;
+    std::vector<double> re, im;
+    int64_t Ns = R0;
+    for (int st = 1; st < S; st++, Ns *= E)
+      for (int qq = 1; qq < E; qq++)
+        for (int64_t kk = 0; kk < Ns; kk++) {
+          double a, b;
+          unit_root((qq * kk) % (Ns * E), Ns * E, &a, &b);
+          re.push_back(a); im.push_back(b);
+        }
+    if (re.empty()) { re.push_back(1.0); im.push_back(0.0); }
+    if ((rc = upload(p, &q.vtw, re, im))) return rc;
   }
   // omega_N^m two-level table (inter-pass twiddles)
   {
@@ -722,6 +749,7 @@ PassParams base_params(const tfft_plan_s* p, int i) {
   a.in_es = q.in_es; a.in_lo = q.in_lo; a.in_hi = q.in_hi;
   a.out_es = q.out_es; a.out_lo = q.out_lo; a.out_hi = q.out_hi;
   a.tw_sub = p->tw_sub; a.tw_sub_stride = p->tw_sub_n / q.nsub;
+  a.tw_stage = q.vtw;
   a.twiddle = q.twiddle; a.tw_scale = q.tw_scale;
   a.twN_lo = p->twN_lo; a.twN_hi = p->twN_hi; a.twN_lbits = p->twN_lbits;
   a.group = p->G; a.parts = q.parts; a.ngroups = p->ngroups; a.line_blocks = q.line_blocks;
@@ -855,6 +883,7 @@ int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
     v.kappa_u_log2n_sqrtn = p->kappa * u * lg * std::sqrt((double)p->n);
     v.detect_only = p->detect_only;
     v.lists = p->lists; v.counters = p->counters; v.log = p->log; v.exec_index = p->execs;
+    v.max_blocks = 8 * p->sms;
     if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
     FixParams f{};
     f.n = p->n; f.batch = p->batch; f.group = p->G; f.dtype = p->dtype;

@@ -129,6 +129,7 @@ struct PassParams {
 
   // ---- twiddles ----
   const void* tw_sub;     // omega_{tw_sub_n}^m, m < tw_sub_n (stage twiddles)
+  const void* tw_stage;   // v3 kernels: per-stage table omega_{Ns R}^(q kk) (see fft_v3.cuh)
   int tw_sub_stride;      // tw_sub_n / nsub
   int twiddle;            // multiply output i of line lo by omega_{tw_n}^{lo*i}
   int64_t tw_scale;       // N / tw_n
@@ -187,6 +188,7 @@ cudaError_t tile_func_attrs_f64(int E, size_t smem, int block, int* blocks_per_s
 cudaError_t launch_v3(int dtype, int role, int nsub, const PassParams& p, int grid, size_t smem, cudaStream_t s);
 cudaError_t v3_attrs(int dtype, int role, int nsub, size_t smem, int* blocks_per_sm);
 int v3_scratch_bytes(int dtype, int nsub);
+int v3_twiddle_smem_bytes(int dtype, int nsub);
 
 // Verify / correction kernels (abft_fix.cu).
 struct VerifyParams {
@@ -202,6 +204,7 @@ struct VerifyParams {
   Counters* counters;
   LogEvent* log;
   long long exec_index;
+  int max_blocks;               // grid cap (blocks stride over the groups)
 };
 cudaError_t launch_verify(const VerifyParams& v, cudaStream_t s);
 

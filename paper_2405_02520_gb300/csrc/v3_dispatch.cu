@@ -46,4 +46,12 @@ int v3_scratch_bytes(int dtype, int nsub) {
   return c * pitch * es;
 }
 
+// Bytes of shared memory the stage-twiddle table takes in a v3 kernel (0 when
+// the kernel reads it from global memory).
+int v3_twiddle_smem_bytes(int dtype, int nsub) {
+  const int es = dtype == 1 ? 16 : 8, e = dtype == 0 ? 16 : 8;
+  const int b = v3_tw_entries(nsub, e) * es;
+  return b <= kV3TwSmemMax ? b : 0;
+}
+
 }  // namespace tfft
