@@ -241,8 +241,13 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
   else passes = 3;
   const int m = ilog2(n);
   int mf[3] = {m, 0, 0};
-  if (passes == 2) { mf[0] = (m + 1) / 2; mf[1] = m - mf[0]; }
-  if (passes == 3) { mf[0] = (m + 2) / 3; mf[1] = (m - mf[0] + 1) / 2; mf[2] = m - mf[0] - mf[1]; }
+  // the largest factor goes to the last pass, whose line-major input rows
+  // read with fewer shared-memory bank conflicts the longer they are
+  if (passes == 2) { mf[0] = m / 2; mf[1] = m - mf[0]; }
+  if (passes == 3) { mf[0] = m / 3; mf[1] = (m - mf[0]) / 2; mf[2] = m - mf[0] - mf[1]; }
+  // ... except a 512-point last pass (three radix stages and 64-byte output
+  // rows), which runs slower than a 512-point first pass
+  if (passes > 1 && mf[passes - 1] == 9 && mf[0] < 9) std::swap(mf[0], mf[passes - 1]);
   if (passes == 1 && n > TILE) return TFFT_ERR_INVALID_ARG;
   for (int i = 1; i < passes; i++)
     if (mf[i] < 1) return TFFT_ERR_INVALID_ARG;
