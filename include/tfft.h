@@ -115,7 +115,17 @@ typedef struct tfft_plan_opts {
                                   TFFT_R_WANG r_k = e^{-2 pi i k/3} (e_Wang,
                                     Section II; w in closed form)             */
     uint64_t checksum_seed;    /* seed of the signs (0: the default 20240502)  */
+    int direction;      /* TFFT_FORWARD (default): y_j = sum_n x_n e^{-2 pi i jn/N};
+                           TFFT_INVERSE: y_j = sum_n x_n e^{+2 pi i jn/N}
+                           (the inverse DFT of Section II without its 1/N)      */
+    int normalize;      /* 1: multiply the output by 1/N (with TFFT_INVERSE the
+                           exact inverse of the forward transform); 0: none    */
 } tfft_plan_opts;
+
+/* The inverse runs the forward machinery on conj(x) and stores conj(.)/N:
+ * the checksums of Section III check that forward transform, so detection,
+ * location and correction work unchanged in both directions. */
+enum tfft_direction { TFFT_FORWARD = 0, TFFT_INVERSE = 1 };
 
 enum tfft_checksum_vector { TFFT_R_SIGNED_WANG = 0, TFFT_R_WANG = 1 };
 
@@ -231,6 +241,8 @@ typedef struct tfft_info {
     int launches_per_exec;   /* kernels one tfft_exec launches                 */
     int checksum_vector;
     uint64_t checksum_seed;
+    int direction;           /* TFFT_FORWARD / TFFT_INVERSE                    */
+    int normalize;           /* 1: output scaled by 1/N                        */
 } tfft_info;
 
 int tfft_plan_info(tfft_plan_t p, tfft_info *info);

@@ -21,6 +21,7 @@ from . import build as _build
 TFFT_C64, TFFT_C128 = 0, 1
 TFFT_ABFT_OFF, TFFT_ABFT_TWO_SIDED = 0, 2
 TFFT_R_SIGNED_WANG, TFFT_R_WANG = 0, 1
+TFFT_FORWARD, TFFT_INVERSE = 0, 1
 TFFT_FAULT_NONE, TFFT_FAULT_BITFLIP, TFFT_FAULT_SCALE, TFFT_FAULT_ADD, TFFT_FAULT_ADD_PAIR = 0, 1, 2, 3, 4
 TIMING_KINDS = ("first_pass", "middle_pass", "last_pass", "single_pass", "verify", "correction")
 
@@ -43,7 +44,7 @@ class PlanOpts(ctypes.Structure):
                 ("abft_mode", ctypes.c_int), ("group", ctypes.c_int), ("kappa", ctypes.c_double),
                 ("detect_only", ctypes.c_int), ("max_faults", ctypes.c_int),
                 ("force_passes", ctypes.c_int), ("checksum_vector", ctypes.c_int),
-                ("checksum_seed", ctypes.c_uint64)]
+                ("checksum_seed", ctypes.c_uint64), ("direction", ctypes.c_int), ("normalize", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -72,7 +73,8 @@ class Info(ctypes.Structure):
                 ("lines_per_signal", ctypes.c_int64 * 3), ("group", ctypes.c_int),
                 ("max_faults", ctypes.c_int), ("kappa", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_int64), ("launches_per_exec", ctypes.c_int),
-                ("checksum_vector", ctypes.c_int), ("checksum_seed", ctypes.c_uint64)]
+                ("checksum_vector", ctypes.c_int), ("checksum_seed", ctypes.c_uint64),
+                ("direction", ctypes.c_int), ("normalize", ctypes.c_int)]
 
 
 def lib() -> ctypes.CDLL:
@@ -152,9 +154,10 @@ def tfft_plan(n: int, batch: int, dtype: int = TFFT_C64, abft_mode: int = TFFT_A
 
 def tfft_plan_ex(n: int, batch: int, dtype: int = TFFT_C64, abft_mode: int = TFFT_ABFT_TWO_SIDED,
                  group: int = 0, kappa: float = 0.0, detect_only: bool = False, max_faults: int = 0,
-                 force_passes: int = 0, checksum_vector: int = TFFT_R_SIGNED_WANG, checksum_seed: int = 0) -> int:
+                 force_passes: int = 0, checksum_vector: int = TFFT_R_SIGNED_WANG, checksum_seed: int = 0,
+                 direction: int = TFFT_FORWARD, normalize: bool = False) -> int:
     o = PlanOpts(n, batch, dtype, abft_mode, group, kappa, int(detect_only), max_faults, force_passes,
-                 checksum_vector, checksum_seed)
+                 checksum_vector, checksum_seed, direction, int(normalize))
     h = ctypes.c_void_p()
     _check(lib().tfft_plan_ex(ctypes.byref(h), ctypes.byref(o)), "tfft_plan_ex")
     return h.value
@@ -247,11 +250,13 @@ class Plan:
     force_passes: int = 0
     checksum_vector: int = TFFT_R_SIGNED_WANG
     checksum_seed: int = 0
+    direction: int = TFFT_FORWARD
+    normalize: bool = False
 
     def __post_init__(self):
         self.handle = tfft_plan_ex(self.n, self.batch, self.dtype, self.abft_mode, self.group,
                                    self.kappa, self.detect_only, self.max_faults, self.force_passes,
-                                   self.checksum_vector, self.checksum_seed)
+                                   self.checksum_vector, self.checksum_seed, self.direction, self.normalize)
 
     def exec(self, x, y, stream=None):
         tfft_exec(self.handle, x, y, stream)

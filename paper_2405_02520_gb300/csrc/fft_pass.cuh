@@ -120,6 +120,19 @@ template <> struct Dft<1> {
 template <typename cT>
 __device__ __forceinline__ cT ldg_c(const cT* p) { return __ldg(p); }
 
+// The stored form of an output value: conjugated for the inverse transform,
+// scaled by 1/N when normalising (the checksums use the value before this).
+template <typename cT>
+__device__ __forceinline__ cT out_xform(cT v, const PassParams& p) {
+  using real = decltype(v.x);
+  if (p.conj_out || p.out_scale != 1.0) {
+    const real sc = (real)p.out_scale;
+    v.x *= sc;
+    v.y *= p.conj_out ? -sc : sc;
+  }
+  return v;
+}
+
 // Multiply v[1..R-1] by omega_{Ns R}^{r k}.  tab holds omega_T^m, T = the
 // table length; m1 = k * nsub / (Ns R), scaled by `stride` = T / nsub.
 // Four table reads (r = 1, 2, 4, 8); the other powers are products of at
@@ -438,6 +451,10 @@ fft_pass_kernel(const __grid_constant__ PassParams p) {
           const int i = j0 + r * (nsub / E);
           v[r] = valid ? gin[base + (int64_t)i * p.in_es] : cT{(real)0, (real)0};
         }
+        if (p.conj_in) {
+#pragma unroll
+          for (int r = 0; r < E; r++) v[r].y = -v[r].y;
+        }
         if (p.abft_in) {
           real sr = 0, si = 0, en = 0;
 #pragma unroll
@@ -551,7 +568,7 @@ fft_pass_kernel(const __grid_constant__ PassParams p) {
           const int64_t obase = b * p.n + hi * p.out_hi + lo * p.out_lo;
           if (valid) {
 #pragma unroll
-            for (int q = 0; q < RL; q++) gout[obase + (int64_t)(j + q * nb) * p.out_es] = w[q];
+            for (int q = 0; q < RL; q++) gout[obase + (int64_t)(j + q * nb) * p.out_es] = out_xform(w[q], p);
           }
           if (p.abft_out && valid) {
             // r_k = s_k w3^(k mod 3), k = hi*out_hi + lo*out_lo + (j + q nb) out_es,

@@ -327,6 +327,10 @@ fft_tile_kernel(const __grid_constant__ PassParams p) {
         const bool valid = b < se;
 #pragma unroll
         for (int r = 0; r < E; r++) v[r] = tile[box_index(lin, c0, j0 + r * (nsub / E), C, nsub)];
+        if (p.conj_in) {
+#pragma unroll
+          for (int r = 0; r < E; r++) v[r].y = -v[r].y;
+        }
         if (p.abft_in && valid) {
           real sr = 0, si = 0, en = 0;
 #pragma unroll
@@ -470,7 +474,7 @@ fft_tile_kernel(const __grid_constant__ PassParams p) {
         for (int ub = 0; ub < NB; ub++)
 #pragma unroll
           for (int q = 0; q < RL; q++)
-            tile[box_index(lout, cc[ub], jj[ub] + q * nb, C, nsub)] = u[ub * RL + q];
+            tile[box_index(lout, cc[ub], jj[ub] + q * nb, C, nsub)] = out_xform(u[ub * RL + q], p);
       };
       switch (p.nstages > 1 ? R_last : E) {
         case 1: if constexpr (E == 1) last_stage(std::integral_constant<int, 1>{}); break;

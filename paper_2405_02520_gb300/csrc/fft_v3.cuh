@@ -487,6 +487,10 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
 #pragma unroll
       for (int r = 0; r < E; r++)
         v[r] = *reinterpret_cast<const cT*>(tile + A::template box<G::LM_IN>(b_in, z_in, r * G::TPL));
+      if (p.conj_in) {
+#pragma unroll
+        for (int r = 0; r < E; r++) v[r].y = -v[r].y;
+      }
       if constexpr (G::LM_IN != G::LM_OUT) {
         // the output box overlaps other warps' input lines: announce that
         // this warp's input values are in registers
@@ -627,6 +631,11 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
           }
         }
         __syncwarp();
+      }
+      if (p.conj_out || p.out_scale != 1.0) {
+        const real sc = (real)p.out_scale, si = p.conj_out ? -sc : sc;
+#pragma unroll
+        for (int q = 0; q < E; q++) { v[q].x *= sc; v[q].y *= si; }
       }
 #pragma unroll
       for (int q = 0; q < E; q++)

@@ -120,6 +120,7 @@ struct tfft_plan_s {
   unsigned long long rseed = 20240502ull;
   void* wtab = nullptr;
   int detect_only = 0;
+  int inverse = 0, normalize = 0;
   int cap_fix = 1, cap_rec = 1;
   int passes = 1;
   PassPlan pp[3];
@@ -764,6 +765,9 @@ PassParams base_params(const tfft_plan_s* p, int i) {
   a.wk_im = nmod3 == 1 ? 0.86602540378443864676 : (nmod3 == 2 ? -0.86602540378443864676 : 0.0);
   if (nmod3 == 0) a.wk_re = 0.0;
   a.rvec = p->rvec; a.rseed = p->rseed; a.wtab = p->wtab;
+  a.conj_in = p->inverse && i == 0;
+  a.conj_out = p->inverse && i == p->passes - 1;
+  a.out_scale = (p->normalize && i == p->passes - 1) ? 1.0 / (double)p->n : 1.0;
   a.nchunks = p->ngroups * q.parts * q.line_blocks;
   return a;
 }
@@ -922,6 +926,8 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   if (o->group < 0 || o->kappa < 0 || o->max_faults < 0 || o->force_passes < 0 || o->force_passes > 3)
     return TFFT_ERR_INVALID_ARG;
   if (o->checksum_vector != TFFT_R_SIGNED_WANG && o->checksum_vector != TFFT_R_WANG) return TFFT_ERR_INVALID_ARG;
+  if ((o->direction != TFFT_FORWARD && o->direction != TFFT_INVERSE) || (o->normalize != 0 && o->normalize != 1))
+    return TFFT_ERR_INVALID_ARG;
   int dev = 0, count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) return TFFT_ERR_NO_DEVICE;
   TFFT_CUDA(cudaGetDevice(&dev));
@@ -937,6 +943,8 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   p->cap_fix = o->max_faults;
   p->rvec = o->checksum_vector == TFFT_R_WANG ? RVEC_WANG : RVEC_SIGNED_WANG;
   if (o->checksum_seed) p->rseed = (unsigned long long)o->checksum_seed;
+  p->inverse = o->direction == TFFT_INVERSE;
+  p->normalize = o->normalize;
   p->device = dev;
   p->sms = prop.multiProcessorCount;
   int rc = plan_build(p, o);
@@ -1088,6 +1096,8 @@ int tfft_plan_info(tfft_plan_t p, tfft_info* info) {
   info->launches_per_exec = p->passes + (p->abft ? 3 + 2 * p->passes : 0);
   info->checksum_vector = p->rvec == RVEC_WANG ? TFFT_R_WANG : TFFT_R_SIGNED_WANG;
   info->checksum_seed = p->rseed;
+  info->direction = p->inverse ? TFFT_INVERSE : TFFT_FORWARD;
+  info->normalize = p->normalize;
   return TFFT_SUCCESS;
 }
 

@@ -162,6 +162,10 @@ struct PassParams {
   int64_t list_block;     // signals per listed block
 
   int64_t nchunks;
+  // inverse / normalised transforms: conj on load (first pass), conj and
+  // scale on store (last pass); the checksums see the forward transform
+  int conj_in, conj_out;
+  double out_scale;       // 1 unless normalising on the last pass
   int log2C, log2LO, log2LB;   // log2 of C, LO and line_blocks (all powers of two; v3 kernels)
   FaultSite fault;
 

@@ -53,7 +53,7 @@ def test_error_strings_and_no_device_status():
 def test_struct_layouts_match_header_sizes():
     """The ctypes mirrors must have the C sizes (8-byte aligned fields)."""
     import paper_2405_02520_gb300 as t
-    assert ctypes.sizeof(t.PlanOpts) == 64
+    assert ctypes.sizeof(t.PlanOpts) == 72
     assert ctypes.sizeof(t.Stats) == 7 * 8
     assert ctypes.sizeof(t.FaultEvent) == 3 * 8 + 2 * 4 + 4 * 8
     assert ctypes.sizeof(t.Fault) == 4 * 4 + 3 * 8 + 8
@@ -65,3 +65,32 @@ def test_invalid_arguments_rejected_before_device_query():
         with pytest.raises(t.TfftError) as e:
             t.tfft_plan(n, b)
         assert e.value.code == -1
+
+
+def test_struct_layouts_match_compiled_header(tmp_path):
+    """Sizes and field offsets of the ctypes mirrors equal those a C compiler
+    gives the structs of include/tfft.h."""
+    import shutil
+    import subprocess
+    import paper_2405_02520_gb300 as t
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"tfft_plan_opts": t.PlanOpts, "tfft_info": t.Info, "tfft_stats": t.Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tfft.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
