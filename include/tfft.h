@@ -54,8 +54,15 @@ enum tfft_dtype { TFFT_C64 = 0, TFFT_C128 = 1 };
 
 enum tfft_abft_mode {
     TFFT_ABFT_OFF = 0,        /* plain FFT                                   */
-    TFFT_ABFT_TWO_SIDED = 2   /* Section III two-sided checksums; 1 is kept
-                                 free for a one-sided mode                    */
+    TFFT_ABFT_ONE_SIDED = 1,  /* Section III one-sided scheme: the left-side
+                                 checksum of every signal alone (w^T x_b vs
+                                 r^T y_b); a flagged signal is recomputed from
+                                 its input.  Kept as an ablation of the
+                                 two-sided scheme; available when every pass
+                                 runs on the tile kernels (complex64 n >= 256,
+                                 complex128 n >= 128, and all multi-pass n),
+                                 otherwise TFFT_ERR_UNSUPPORTED              */
+    TFFT_ABFT_TWO_SIDED = 2   /* Section III two-sided checksums             */
 };
 
 enum tfft_status {

@@ -19,7 +19,7 @@ from dataclasses import dataclass
 from . import build as _build
 
 TFFT_C64, TFFT_C128 = 0, 1
-TFFT_ABFT_OFF, TFFT_ABFT_TWO_SIDED = 0, 2
+TFFT_ABFT_OFF, TFFT_ABFT_ONE_SIDED, TFFT_ABFT_TWO_SIDED = 0, 1, 2
 TFFT_R_SIGNED_WANG, TFFT_R_WANG = 0, 1
 TFFT_FORWARD, TFFT_INVERSE = 0, 1
 TFFT_FAULT_NONE, TFFT_FAULT_BITFLIP, TFFT_FAULT_SCALE, TFFT_FAULT_ADD, TFFT_FAULT_ADD_PAIR = 0, 1, 2, 3, 4

@@ -178,6 +178,37 @@ __device__ __forceinline__ void warp_records(const Partials<real>& a, const Pass
   }
 }
 
+// One-sided mode: the records of one signal from the threads that hold it --
+// `width` consecutive lanes (a whole warp, or the TPL lanes of a warp-local
+// line) -- reduced by shuffles within those lanes and written by the first.
+template <typename real>
+__device__ __forceinline__ void line_records(const Partials<real>& a, const PassParams& p, long long sig,
+                                             long long slot, int width) {
+  const unsigned full = 0xffffffffu;
+  real v[9] = {a.s1r, a.s1i, a.s2r, a.s2i, a.en, a.t1r, a.t1i, a.t2r, a.t2i};
+  long long mn = a.nf_min, mx = a.nf_max;
+  for (int off = width >> 1; off > 0; off >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 9; q++) v[q] += __shfl_xor_sync(full, v[q], off);
+    mn = min(mn, __shfl_xor_sync(full, mn, off));
+    mx = max(mx, __shfl_xor_sync(full, mx, off));
+  }
+  if ((threadIdx.x & (width - 1)) == 0 && sig >= 0) {
+    if (p.abft_in) {
+      RecIn r;
+      r.s1r = v[0]; r.s1i = v[1]; r.s2r = v[2]; r.s2i = v[3]; r.energy = v[4];
+      r.pad0 = r.pad1 = r.pad2 = 0.0;
+      p.rec_in[sig * p.slots + slot] = r;
+    }
+    if (p.abft_out) {
+      RecOut r;
+      r.t1r = v[5]; r.t1i = v[6]; r.t2r = v[7]; r.t2i = v[8];
+      r.nf_min = mn; r.nf_max = mx; r.pad0 = r.pad1 = 0.0;
+      p.rec_out[sig * p.slots + slot] = r;
+    }
+  }
+}
+
 // The chunks of one thread block and their tiles, as TileCursor, for the v3
 // kernels (never a work list): C, LO and the line-block count are powers of
 // two, so the decomposition is shifts and masks except for the split of a
@@ -441,7 +472,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
     // one checksum record per warp and chunk
     const long long slot = (long long)(cur.part * p.line_blocks + cur.lb) * 8 + warp;
     if (!nonempty) {
-      if (abft && !p.list) {
+      if (abft && !p.list && !p.per_signal) {
         acc.zero();
         warp_records(acc, p, cur.g, slot);
       }
@@ -464,10 +495,12 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
       tw_step = twN<cT>(p, lo_c * (long long)G::TPL * p.tw_scale);
     }
     // checksum weight (b - first signal of the group + 1) of this thread's signal
-    real wgt = (real)(int)(cur.sb - cur.gb + (ROLE == V3_SINGLE ? c0 : 0) + 1);
+    // (one-sided mode: every signal is its own group, weight 1)
+    real wgt = p.per_signal ? (real)1 : (real)(int)(cur.sb - cur.gb + (ROLE == V3_SINGLE ? c0 : 0) + 1);
     constexpr int BSTEP = ROLE == V3_SINGLE ? G::C : 1;
+    const real wstep = p.per_signal ? (real)0 : (real)BSTEP;
 
-    for (long long tb = cur.sb; tb < se; tb += BSTEP, wgt += (real)BSTEP) {
+    for (long long tb = cur.sb; tb < se; tb += BSTEP, wgt += wstep) {
       unsigned char* tile = base + (size_t)s * p.buf_bytes;
       if (!aborted && !mbar_wait_bounded(&full[s], wrap & 1u, abort_flag)) {
         aborted = true;
@@ -617,6 +650,16 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
           acc.nf_max = max(acc.nf_max, (long long)b0);
         }
       }
+      if (abft && p.per_signal) {
+        // one-sided mode: this tile's records, per signal
+        if constexpr (ROLE == V3_SINGLE) {
+          if constexpr (G::WL) line_records(acc, p, valid ? b0 : -1, 0, G::TPL);
+          else line_records(acc, p, valid ? b0 : -1, warp % G::WPL, 32);
+        } else {
+          line_records(acc, p, tb, (long long)cur.lb * 8 + warp, 32);
+        }
+        acc.zero();
+      }
       if constexpr (G::LM_IN != G::LM_OUT) {
         // every warp has read its input from the box before any output lands there
         if (lane == 0) {
@@ -694,7 +737,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
       }
       if (++s == nbuf) { s = 0; wrap++; }
     }
-    if (abft) warp_records(acc, p, cur.g, slot);
+    if (abft && !p.per_signal) warp_records(acc, p, cur.g, slot);
   }
   if (lane == 0) bulk_wait_0();
 }

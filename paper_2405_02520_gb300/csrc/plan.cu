@@ -121,6 +121,9 @@ struct tfft_plan_s {
   void* wtab = nullptr;
   int detect_only = 0;
   int inverse = 0, normalize = 0;
+  int one_sided = 0;                 // per-signal checksums (verification groups of one)
+  int vG = 16;                       // signals per verification group
+  int64_t vgroups = 0;               // verification groups
   int cap_fix = 1, cap_rec = 1;
   int passes = 1;
   PassPlan pp[3];
@@ -348,6 +351,22 @@ void plan_slots(tfft_plan_s* p) {
   // v3 writes one record per warp and chunk, the other kernels one per chunk
   p->slots_in = (int64_t)f.parts * (f.v3 ? f.vLB * 8 : f.line_blocks);
   p->slots_out = (int64_t)l.parts * (l.v3 ? l.vLB * 8 : l.line_blocks);
+  p->vG = p->G;
+  p->vgroups = p->ngroups;
+  if (p->one_sided) {
+    // records per signal: the single pass writes one per warp holding a part
+    // of the line, the column and last passes one per warp and line block
+    auto per_signal = [&](const PassPlan& q) -> int64_t {
+      if (q.role != 0) return q.vLB * 8;
+      const int E = p->dtype == TFFT_C64 ? 16 : 8;
+      const int64_t tpl = q.nsub / E;
+      return tpl > 32 ? tpl / 32 : 1;
+    };
+    p->slots_in = per_signal(f);
+    p->slots_out = per_signal(l);
+    p->vG = 1;
+    p->vgroups = p->batch;
+  }
 }
 
 // cuTensorMapEncodeTiled, fetched from the driver through the runtime (no
@@ -710,8 +729,8 @@ int plan_workspace(tfft_plan_s* p) {
     int64_t cap = (int64_t(1) << 30) / (int64_t)(2 * sig);
     p->cap_fix = (int)std::max<int64_t>(1, std::min<int64_t>(8, cap));
   }
-  p->cap_fix = (int)std::min<int64_t>(p->cap_fix, std::max<int64_t>(1, p->ngroups));
-  p->cap_rec = (int)std::min<int64_t>(8, std::max<int64_t>(1, p->ngroups));
+  p->cap_fix = (int)std::min<int64_t>(p->cap_fix, std::max<int64_t>(1, p->vgroups));
+  p->cap_rec = (int)std::min<int64_t>(8, std::max<int64_t>(1, p->vgroups));
   if (p->passes > 1) {
     const int64_t rows = std::max<int64_t>(p->batch, p->abft ? p->cap_fix : 0);
     TFFT_CUDA(cudaMalloc(&p->tmp, rows * sig));
@@ -733,12 +752,12 @@ int plan_workspace(tfft_plan_s* p) {
   TFFT_CUDA(cudaMemset(p->log, 0, sizeof(LogEvent) * kLogRing));
   p->workspace_bytes += nl * sizeof(long long) + sizeof(Counters) + sizeof(LogEvent) * kLogRing;
   if (p->abft) {
-    TFFT_CUDA(cudaMalloc(&p->rec_in, sizeof(RecIn) * p->ngroups * p->slots_in));
-    TFFT_CUDA(cudaMalloc(&p->rec_out, sizeof(RecOut) * p->ngroups * p->slots_out));
+    TFFT_CUDA(cudaMalloc(&p->rec_in, sizeof(RecIn) * p->vgroups * p->slots_in));
+    TFFT_CUDA(cudaMalloc(&p->rec_out, sizeof(RecOut) * p->vgroups * p->slots_out));
     TFFT_CUDA(cudaMalloc(&p->ws_c1, p->cap_fix * sig));
     TFFT_CUDA(cudaMalloc(&p->ws_acc, p->cap_fix * sig));
-    p->workspace_bytes += sizeof(RecIn) * p->ngroups * p->slots_in +
-                          sizeof(RecOut) * p->ngroups * p->slots_out + 2 * p->cap_fix * (int64_t)sig;
+    p->workspace_bytes += sizeof(RecIn) * p->vgroups * p->slots_in +
+                          sizeof(RecOut) * p->vgroups * p->slots_out + 2 * p->cap_fix * (int64_t)sig;
   }
   return 0;
 }
@@ -765,6 +784,7 @@ PassParams base_params(const tfft_plan_s* p, int i) {
   a.wk_im = nmod3 == 1 ? 0.86602540378443864676 : (nmod3 == 2 ? -0.86602540378443864676 : 0.0);
   if (nmod3 == 0) a.wk_re = 0.0;
   a.rvec = p->rvec; a.rseed = p->rseed; a.wtab = p->wtab;
+  a.per_signal = p->one_sided;
   a.conj_in = p->inverse && i == 0;
   a.conj_out = p->inverse && i == p->passes - 1;
   a.out_scale = (p->normalize && i == p->passes - 1) ? 1.0 / (double)p->n : 1.0;
@@ -880,7 +900,7 @@ int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
   if (rc) return rc;
   if (p->abft) {
     VerifyParams v{};
-    v.n = p->n; v.batch = p->batch; v.group = p->G; v.ngroups = p->ngroups;
+    v.n = p->n; v.batch = p->batch; v.group = p->vG; v.ngroups = p->vgroups;
     v.slots_in = p->slots_in; v.slots_out = p->slots_out;
     v.rec_in = p->rec_in; v.rec_out = p->rec_out;
     const double u = p->dtype == TFFT_C64 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
@@ -895,7 +915,7 @@ int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
     v.max_blocks = 8 * p->sms;
     if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
     FixParams f{};
-    f.n = p->n; f.batch = p->batch; f.group = p->G; f.dtype = p->dtype;
+    f.n = p->n; f.batch = p->batch; f.group = p->vG; f.dtype = p->dtype;
     f.in = in; f.out = out; f.ws_c1 = p->ws_c1; f.ws_acc = p->ws_acc; f.lists = p->lists;
     if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_gather(f, s); }))) return rc;
     // W X e_1 of every queued group, in place in ws_c1
@@ -904,7 +924,7 @@ int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
       return rc;
     if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_apply(f, s); }))) return rc;
     // groups that could not be located: recompute from the input
-    if ((rc = run_passes(p, in, out, s, false, p->lists.rec, 0, p->cap_rec, p->G, p->batch, 5)))
+    if ((rc = run_passes(p, in, out, s, false, p->lists.rec, 0, p->cap_rec, p->vG, p->batch, 5)))
       return rc;
   }
   return 0;
@@ -922,7 +942,8 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   *out = nullptr;
   if (!is_pow2(o->n) || o->n > (int64_t(1) << 26) || o->batch < 1) return TFFT_ERR_INVALID_ARG;
   if (o->dtype != TFFT_C64 && o->dtype != TFFT_C128) return TFFT_ERR_UNSUPPORTED;
-  if (o->abft_mode != TFFT_ABFT_OFF && o->abft_mode != TFFT_ABFT_TWO_SIDED) return TFFT_ERR_UNSUPPORTED;
+  if (o->abft_mode != TFFT_ABFT_OFF && o->abft_mode != TFFT_ABFT_TWO_SIDED && o->abft_mode != TFFT_ABFT_ONE_SIDED)
+    return TFFT_ERR_UNSUPPORTED;
   if (o->group < 0 || o->kappa < 0 || o->max_faults < 0 || o->force_passes < 0 || o->force_passes > 3)
     return TFFT_ERR_INVALID_ARG;
   if (o->checksum_vector != TFFT_R_SIGNED_WANG && o->checksum_vector != TFFT_R_WANG) return TFFT_ERR_INVALID_ARG;
@@ -937,7 +958,8 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
 
   tfft_plan_s* p = new (std::nothrow) tfft_plan_s();
   if (!p) return TFFT_ERR_ALLOC;
-  p->n = o->n; p->batch = o->batch; p->dtype = o->dtype; p->abft = o->abft_mode == TFFT_ABFT_TWO_SIDED;
+  p->n = o->n; p->batch = o->batch; p->dtype = o->dtype; p->abft = o->abft_mode != TFFT_ABFT_OFF;
+  p->one_sided = o->abft_mode == TFFT_ABFT_ONE_SIDED;
   p->kappa = o->kappa > 0 ? o->kappa : 2.0;
   p->detect_only = o->detect_only ? 1 : 0;
   p->cap_fix = o->max_faults;
@@ -951,6 +973,9 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   if (!rc) rc = plan_tma(p);
   if (!rc) rc = plan_v3(p);
   if (!rc) plan_slots(p);
+  if (!rc && p->one_sided)
+    for (int i = 0; i < p->passes; i++)
+      if (!p->pp[i].v3) rc = TFFT_ERR_UNSUPPORTED;   // per-signal records live in the tile kernels
   if (!rc) rc = plan_tables(p);
   if (!rc) rc = plan_workspace(p);
   if (!rc) rc = plan_wtable(p);
@@ -1081,7 +1106,7 @@ int tfft_plan_info(tfft_plan_t p, tfft_info* info) {
   if (!p || !info) return TFFT_ERR_INVALID_ARG;
   std::memset(info, 0, sizeof(*info));
   info->n = p->n; info->batch = p->batch; info->dtype = p->dtype;
-  info->abft_mode = p->abft ? TFFT_ABFT_TWO_SIDED : TFFT_ABFT_OFF;
+  info->abft_mode = !p->abft ? TFFT_ABFT_OFF : (p->one_sided ? TFFT_ABFT_ONE_SIDED : TFFT_ABFT_TWO_SIDED);
   info->passes = p->passes;
   for (int i = 0; i < p->passes; i++) {
     info->nsub[i] = p->pp[i].nsub;

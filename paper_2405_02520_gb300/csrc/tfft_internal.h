@@ -165,6 +165,7 @@ struct PassParams {
   // inverse / normalised transforms: conj on load (first pass), conj and
   // scale on store (last pass); the checksums see the forward transform
   int conj_in, conj_out;
+  int per_signal;         // one-sided ABFT: one checksum record set per signal (group = 1)
   double out_scale;       // 1 unless normalising on the last pass
   int log2C, log2LO, log2LB;   // log2 of C, LO and line_blocks (all powers of two; v3 kernels)
   FaultSite fault;
