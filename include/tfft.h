@@ -67,7 +67,7 @@ enum tfft_abft_mode {
 
 enum tfft_status {
     TFFT_SUCCESS = 0,
-    TFFT_ERR_INVALID_ARG = -1,  /* n not a power of two in [2^0, 2^26], batch
+    TFFT_ERR_INVALID_ARG = -1,  /* n not a power of two in [2^0, 2^29], batch
                                    < 1, null or misaligned pointer, bad option */
     TFFT_ERR_UNSUPPORTED = -2,  /* dtype or abft_mode not implemented         */
     TFFT_ERR_CUDA = -3,         /* a CUDA runtime call failed; see
@@ -84,7 +84,7 @@ enum tfft_status {
 
 /*
  * tfft_plan -- plan a batched forward FFT of `batch` signals of length `n`
- * (a power of two, 1 <= n <= 2^26), element type `dtype` (TFFT_C64 or
+ * (a power of two, 1 <= n <= 2^29), element type `dtype` (TFFT_C64 or
  * TFFT_C128), fault tolerance `abft_mode` (TFFT_ABFT_OFF or
  * TFFT_ABFT_TWO_SIDED).  Chooses the pass decomposition (one pass when a
  * signal fits one thread block's tile, otherwise the kernel-level tiling of

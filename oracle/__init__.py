@@ -101,6 +101,27 @@ def dft_naive(x, sign: int = -1) -> np.ndarray:
     return y
 
 
+def dft_bins(x, bins, sign: int = -1, chunk: int = 1 << 22) -> np.ndarray:
+    """Selected outputs y_k = sum_n x_n e^{sign 2 pi i n k / N} of one signal
+    by the definition (Section II), FP64.  The phase index n k is reduced
+    modulo N in exact integer arithmetic before the angle is formed, so the
+    twiddles carry no error from a large argument.  For spot checks of
+    transforms too long for the full oracle."""
+    x = _as_c128(np.asarray(x).reshape(-1))
+    n = x.size
+    out = np.zeros(len(bins), dtype=np.complex128)
+    for j, k in enumerate(bins):
+        k = int(k) % n
+        acc = 0j
+        for s0 in range(0, n, chunk):
+            idx = np.arange(s0, min(n, s0 + chunk), dtype=np.int64)
+            m = (idx * k) % n
+            ang = (2.0 * np.pi / n) * m.astype(np.float64)
+            acc += np.sum(x[s0:s0 + idx.size] * (np.cos(ang) + sign * 1j * np.sin(ang)))
+        out[j] = acc
+    return out
+
+
 def fft_faulty(x, prec: int, stage: int = -2, elem: int = 0, comp: int = 0,
                bit: int = -1) -> np.ndarray:
     """Forward radix-2 FFT of ONE signal in FP32 (prec=32) or FP64 (prec=64)

@@ -227,16 +227,13 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
   const int64_t n = o->n;
   const bool c64 = o->dtype == TFFT_C64;
   p->esize = c64 ? 8 : 16;
-  int E0 = c64 ? 16 : 8;
-  int TILE = c64 ? 4096 : 2048;              // elements of one thread block's tile
-  // tuning overrides for measurement (radix per thread, tile elements)
-  if (c64) {
-    if (const char* s = std::getenv("TFFT_TUNE_E")) { const int v = std::atoi(s); if (v == 8 || v == 16) E0 = v; }
-    if (const char* s = std::getenv("TFFT_TUNE_TILE")) { const int v = std::atoi(s); if (v >= 1024 && v <= 8192 && !(v & (v - 1))) TILE = v; }
-  }
+  const int E0 = c64 ? 16 : 8;
+  const int TILE = c64 ? 4096 : 2048;        // elements of one thread block's tile
   const int S = c64 ? 16 : 8;                // elements per 128-byte shared-memory row
   const int CMIN = c64 ? 8 : 4;              // lines per tile for 64-byte column runs
-  const int NSUBMAX = TILE / CMIN;
+  // longest sub-transform of a multi-pass plan; beyond NSUBMAX^3 elements the
+  // three passes take sub-transforms up to twice that (32-byte column runs)
+  const int NSUBMAX = n > (int64_t)(TILE / CMIN) * (TILE / CMIN) * (TILE / CMIN) ? 2 * TILE / CMIN : TILE / CMIN;
 
   int passes;
   if (o->force_passes) passes = o->force_passes;
@@ -504,7 +501,6 @@ int plan_tma(tfft_plan_s* p) {
 // of at most 128 bytes per row and moved with the matching TMA swizzle.
 int plan_v3(tfft_plan_s* p) {
   if (!encode_fn()) return 0;
-  if (std::getenv("TFFT_TUNE_NO_V3")) return 0;
   const bool c64 = p->dtype == TFFT_C64;
   const int64_t u = (int64_t)p->esize / 8, es = (int64_t)p->esize;
   const int vdt = c64 ? 0 : 1;
@@ -940,7 +936,7 @@ extern "C" {
 int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   if (!out || !o) return TFFT_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!is_pow2(o->n) || o->n > (int64_t(1) << 26) || o->batch < 1) return TFFT_ERR_INVALID_ARG;
+  if (!is_pow2(o->n) || o->n > (int64_t(1) << 29) || o->batch < 1) return TFFT_ERR_INVALID_ARG;
   if (o->dtype != TFFT_C64 && o->dtype != TFFT_C128) return TFFT_ERR_UNSUPPORTED;
   if (o->abft_mode != TFFT_ABFT_OFF && o->abft_mode != TFFT_ABFT_TWO_SIDED && o->abft_mode != TFFT_ABFT_ONE_SIDED)
     return TFFT_ERR_UNSUPPORTED;

@@ -61,7 +61,7 @@ def test_struct_layouts_match_header_sizes():
 
 def test_invalid_arguments_rejected_before_device_query():
     import paper_2405_02520_gb300 as t
-    for n, b in ((12, 4), (0, 4), (1 << 27, 1), (8, 0)):
+    for n, b in ((12, 4), (0, 4), (1 << 30, 1), (8, 0)):
         with pytest.raises(t.TfftError) as e:
             t.tfft_plan(n, b)
         assert e.value.code == -1

@@ -310,3 +310,20 @@ def test_random_vector_detects_early_stage_fault_wang_misses():
         cr = abft.group_checksums(x, yf, w=wr, r=rr)
         v = abft.verify_group(cr, n, g, u, 1.0)
         assert v.detected and v.located == 1
+
+
+def test_dft_bins_matches_definition_and_fft():
+    """The spot-check oracle for long transforms equals the long-double
+    definition and the radix-2 oracle on short ones, in both directions."""
+    rng = np.random.default_rng(77)
+    for n in (1, 2, 8, 256, 4096):
+        x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        ks = sorted(set(rng.integers(0, n, size=min(n, 12)).tolist()) | {0, n - 1})
+        for sign in ((-1, 1) if n <= 256 else ()):
+            # the definition oracle scales its inverse by 1/N; dft_bins does not
+            ref = oracle.dft_naive(x[None, :], sign)[0] * (n if sign > 0 else 1)
+            got = oracle.dft_bins(x, ks, sign, chunk=97)
+            scale = np.linalg.norm(ref) / np.sqrt(n)
+            assert np.max(np.abs(got - ref[ks])) <= 1e-12 * max(scale, 1e-300) * max(1, np.log2(n))
+        y = oracle.fft(x[None, :])[0]
+        assert np.allclose(oracle.dft_bins(x, ks), y[ks], rtol=0, atol=1e-11 * np.linalg.norm(y))
