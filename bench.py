@@ -356,6 +356,9 @@ def run_ours(args):
     for lg in sweep:
         t.tfft_destroy(off[lg])
 
+    ragged = None if args.no_ragged else ragged_measure(t, torch, stream, args, peak)
+    ablation = None if args.no_ragged else one_sided_measure(t, torch, x, y, stream, args)
+
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e:
@@ -450,9 +453,83 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "ragged": ragged,
+        "one_sided": ablation,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+RAGGED_COUNT, RAGGED_LOG2 = 20000, (6, 16)
+
+
+def ragged_measure(t, torch, stream, args, peak):
+    """A ragged batch: 20,000 signals, log2 length uniform over {6..16},
+    U[-1,1) re/im, seed 5, packed back to back; autotuned plan, graph-replayed
+    execs, ABFT on and off.  Bytes counted as algorithmic: 16 B per element per
+    pass of each bucket's plan (the gather and scatter copies are overhead)."""
+    rng = np.random.default_rng(5)
+    lengths = (1 << rng.integers(RAGGED_LOG2[0], RAGGED_LOG2[1] + 1, size=RAGGED_COUNT)).astype(np.int64)
+    total = int(lengths.sum())
+    xr = torch.empty(total, dtype=torch.complex64, device=stream.device)
+    g = torch.Generator(device=stream.device).manual_seed(5)
+    xr.real.uniform_(-1, 1, generator=g)
+    xr.imag.uniform_(-1, 1, generator=g)
+    yr = torch.empty_like(xr)
+    out = {"signals": RAGGED_COUNT, "log2_lengths": list(RAGGED_LOG2), "elements": total, "seed": 5}
+    for mode, key in ((t.TFFT_ABFT_TWO_SIDED, "ms"), (t.TFFT_ABFT_OFF, "ms_abft_off")):
+        r = t.Ragged(lengths.tolist(), abft_mode=mode, autotune=True)
+        for _ in range(max(3, args.warmup)):
+            r.exec(xr, yr, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = max(5, args.steps)
+        e0.record(stream)
+        for _ in range(k):
+            r.exec(xr, yr, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[key] = round(e0.elapsed_time(e1) / k, 4)
+        if mode == t.TFFT_ABFT_TWO_SIDED:
+            info = dict(r.info())
+            st = r.report()
+            out["detected"] = st["detected"]
+            out["buckets"] = {str(n): p for n, p in sorted(info.items())}
+        r.destroy()
+    fl = sum(float(flops(int(n), 1)) for n in lengths)
+    passes = {int(n): p for n, p in ((int(k), v) for k, v in out["buckets"].items())}
+    alg = sum(16.0 * passes[int(n)] * int(n) for n in lengths)
+    out["gflops"] = round(fl / (out["ms"] / 1e3) / 1e9, 1)
+    out["hbm_frac"] = round(alg / (out["ms"] / 1e3) / 1e9 / peak, 4)
+    out["abft_overhead_pct"] = round((out["ms"] - out["ms_abft_off"]) / out["ms_abft_off"] * 100, 2)
+    return out
+
+
+def one_sided_measure(t, torch, x, y, stream, args):
+    """The one-sided ABFT mode (per-signal checks, recompute on detection) as
+    an ablation of the two-sided scheme: N = 2^10 and 2^16, 2^28 elements."""
+    out = {}
+    total = x.numel()
+    for lg in (10, 16):
+        n = 1 << lg
+        ms = {}
+        for name, mode in (("two_sided", t.TFFT_ABFT_TWO_SIDED), ("one_sided", t.TFFT_ABFT_ONE_SIDED),
+                           ("off", t.TFFT_ABFT_OFF)):
+            pl = t.tfft_plan(n, total // n, t.TFFT_C64, mode)
+            for _ in range(3):
+                t.tfft_exec(pl, x, y, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                t.tfft_exec(pl, x, y, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms[name] = e0.elapsed_time(e1) / 5
+            t.tfft_destroy(pl)
+        out[str(lg)] = {k: round(v, 4) for k, v in ms.items()}
+        out[str(lg)]["overhead_pct"] = {k: round((ms[k] - ms["off"]) / ms["off"] * 100, 2)
+                                        for k in ("two_sided", "one_sided")}
+    return out
 
 
 def main(argv=None):
@@ -467,6 +544,8 @@ def main(argv=None):
                     help="log2 of the elements per transform (default 28; smaller for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true",
+                    help="skip the ragged-batch and one-sided-mode measurements")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)      # at least three untimed warm-up steps
     if args.impl == "reference":

@@ -288,6 +288,44 @@ int tfft_destroy(tfft_plan_t p);
  */
 int tfft_exec_noalloc(int64_t n, int64_t batch, const void *in, void *out, tfft_stream_t stream);
 
+/*
+ * Ragged batches: `count` signals of different power-of-two lengths
+ * `lengths[i]` (2 <= n <= 2^26 for complex64, 1 <= n for complex128), packed
+ * back to back in that order -- signal i starts at element
+ * sum_{j<i} lengths[j] of `in` and of `out`.  Section II's batched transform
+ * is applied to every signal.  No counterpart in the paper, which batches
+ * equal lengths only; the two-sided checksums (Section III) run over groups
+ * of G consecutive signals of equal length.
+ *
+ * tfft_ragged_plan: buckets the signals by length, plans one batched
+ * transform per bucket and allocates two staging areas of the total size.
+ * autotune = 1 times every pass count (one, two or three launches) a
+ * bucket's length admits and keeps the fastest; 0 takes the planner's
+ * choice.  The caller's `lengths` array is not kept.
+ *
+ * tfft_ragged_exec: asynchronous on `stream`; gathers each bucket into
+ * staging, runs the bucket plans (each on its own stream, joined to
+ * `stream`), scatters the results.  The sequence is captured into a CUDA
+ * graph on the first exec with given (in, out) and replayed on the
+ * next ones.  `in` and `out` must not overlap (TFFT_ERR_INPLACE).
+ *
+ * tfft_ragged_report: synchronises the device and sums the bucket plans'
+ * counters (execs counts tfft_ragged_exec calls).
+ * tfft_ragged_set_fault: test hook, arms a fault (tfft_fault, with `signal`
+ * ignored) on caller signal `signal` for the next exec, which then runs
+ * uncaptured.
+ * tfft_ragged_info: number of buckets, and up to `capacity` of their
+ * lengths and pass counts (longest first).
+ */
+typedef struct tfft_ragged_s *tfft_ragged_t;
+int tfft_ragged_plan(tfft_ragged_t *out, const int64_t *lengths, int64_t count, int dtype, int abft_mode,
+                     int autotune);
+int tfft_ragged_exec(tfft_ragged_t r, const void *in, void *out, tfft_stream_t stream);
+int tfft_ragged_report(tfft_ragged_t r, tfft_stats *stats);
+int tfft_ragged_set_fault(tfft_ragged_t r, int64_t signal, const tfft_fault *fault);
+int tfft_ragged_info(tfft_ragged_t r, int64_t *buckets, int64_t *lengths, int *passes, int64_t capacity);
+int tfft_ragged_destroy(tfft_ragged_t r);
+
 /* Static string for a status code. */
 const char *tfft_error_string(int status);
 /* The last cudaError_t value seen by the library in this process. */

@@ -103,6 +103,12 @@ def lib() -> ctypes.CDLL:
                 "tfft_timing": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I],
                 "tfft_destroy": [P],
                 "tfft_exec_noalloc": [I64, I64, P, P, P],
+                "tfft_ragged_plan": [PP, ctypes.POINTER(I64), I64, I, I, I],
+                "tfft_ragged_exec": [P, P, P, P],
+                "tfft_ragged_report": [P, ctypes.POINTER(Stats)],
+                "tfft_ragged_set_fault": [P, I64, ctypes.POINTER(Fault)],
+                "tfft_ragged_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I), I64],
+                "tfft_ragged_destroy": [P],
                 "tfft_error_string": [I],
                 "tfft_last_cuda_error": [],
             }
@@ -225,6 +231,46 @@ def tfft_timing(plan: int) -> dict:
 
 def tfft_destroy(plan: int) -> None:
     _check(lib().tfft_destroy(plan), "tfft_destroy")
+
+
+class Ragged:
+    """A ragged batch: signals of different power-of-two lengths packed back
+    to back (see include/tfft.h, tfft_ragged_*)."""
+
+    def __init__(self, lengths, dtype: int = TFFT_C64, abft_mode: int = TFFT_ABFT_TWO_SIDED,
+                 autotune: bool = True):
+        arr = (ctypes.c_int64 * len(lengths))(*[int(v) for v in lengths])
+        h = ctypes.c_void_p()
+        _check(lib().tfft_ragged_plan(ctypes.byref(h), arr, len(lengths), dtype, abft_mode, int(autotune)),
+               "tfft_ragged_plan")
+        self.handle = h.value
+        self.lengths = [int(v) for v in lengths]
+
+    def exec(self, x, y, stream=None) -> None:
+        _check(lib().tfft_ragged_exec(self.handle, _ptr(x), _ptr(y), _stream(stream)), "tfft_ragged_exec")
+
+    def report(self) -> dict:
+        s = Stats()
+        _check(lib().tfft_ragged_report(self.handle, ctypes.byref(s)), "tfft_ragged_report")
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def set_fault(self, signal: int, mode: int, pass_: int = 0, stage: int = -1, line: int = 0, index: int = 0,
+                  bit: int = 0, factor: float = 0.0) -> None:
+        f = Fault(mode, pass_, stage, bit, 0, line, index, factor)
+        _check(lib().tfft_ragged_set_fault(self.handle, signal, ctypes.byref(f)), "tfft_ragged_set_fault")
+
+    def info(self) -> list:
+        nb = ctypes.c_int64()
+        _check(lib().tfft_ragged_info(self.handle, ctypes.byref(nb), None, None, 0), "tfft_ragged_info")
+        ln = (ctypes.c_int64 * nb.value)()
+        ps = (ctypes.c_int * nb.value)()
+        _check(lib().tfft_ragged_info(self.handle, ctypes.byref(nb), ln, ps, nb.value), "tfft_ragged_info")
+        return [(ln[k], ps[k]) for k in range(nb.value)]
+
+    def destroy(self) -> None:
+        if self.handle:
+            _check(lib().tfft_ragged_destroy(self.handle), "tfft_ragged_destroy")
+            self.handle = None
 
 
 def tfft_exec_noalloc(n: int, batch: int, x, y, stream=None) -> None:

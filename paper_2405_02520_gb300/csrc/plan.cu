@@ -37,6 +37,14 @@ int cuda_fail(cudaError_t e) {
   return TFFT_ERR_CUDA;
 }
 
+}  // namespace
+
+namespace tfft {
+int record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+}  // namespace tfft
+
+namespace {
+
 #define TFFT_CUDA(call)                       \
   do {                                        \
     cudaError_t e_ = (call);                  \

@@ -1,0 +1,361 @@
+// ragged.cu -- batches of signals of different lengths (tfft_ragged_*).
+//
+// The signals of a ragged batch are packed back to back in the caller's
+// order.  The plan sorts them into buckets of equal length; each bucket is an
+// ordinary batched plan (with the two-sided checksums over groups of G
+// consecutive signals of the bucket).  An exec
+//
+//   1. gathers every bucket into a contiguous staging area ([count][n] per
+//      bucket) with one copy kernel over 16-byte chunks;
+//   2. runs the bucket plans, each on its own stream so that the short
+//      transforms of small buckets overlap;
+//   3. scatters the results back to the caller's layout.
+//
+// The whole sequence is captured into a CUDA graph on the first exec with a
+// given (in, out) and replayed afterwards (no per-kernel launch cost;
+// the small buckets are launch-bound).  An exec with a test fault armed runs
+// uncaptured.  At plan time an optional autotuner times the pass counts a
+// bucket's length admits (one, two or three launches) and keeps the fastest.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tfft.h"
+#include "tfft_internal.h"
+
+using tfft::record_cuda_error;
+
+namespace {
+
+struct Segment {        // one block's share of a gather or scatter
+  long long src, dst;   // byte offsets
+  long long bytes;      // a multiple of 16
+};
+
+__global__ void ragged_copy_kernel(const Segment* seg, long long nseg, const unsigned char* src,
+                                   unsigned char* dst) {
+  for (long long s = blockIdx.x; s < nseg; s += gridDim.x) {
+    const Segment g = seg[s];
+    const uint4* a = reinterpret_cast<const uint4*>(src + g.src);
+    uint4* b = reinterpret_cast<uint4*>(dst + g.dst);
+    const long long n16 = g.bytes >> 4;
+    for (long long i = threadIdx.x; i < n16; i += blockDim.x) b[i] = a[i];
+  }
+}
+
+struct Bucket {
+  int64_t n = 0;
+  std::vector<int64_t> sig;   // caller indices of the bucket's signals, in order
+  int64_t base = 0;           // element offset of the bucket in the staging areas
+  tfft_plan_t plan = nullptr;
+  int passes = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+}  // namespace
+
+struct tfft_ragged_s {
+  int dtype = 0, abft = 0;
+  size_t esize = 8;
+  int64_t count = 0, total = 0;
+  std::vector<int64_t> off;          // caller element offset of every signal
+  std::vector<int64_t> local;        // index of every signal inside its bucket
+  std::vector<int> bucket_of;        // bucket of every signal
+  std::vector<Bucket> buckets;
+  void* stage_in = nullptr;
+  void* stage_out = nullptr;
+  Segment* d_gather = nullptr;
+  Segment* d_scatter = nullptr;
+  long long nseg = 0;
+  int sms = 0;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;        // private stream the graph is captured on
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_in = nullptr;
+  void* g_out = nullptr;
+  bool fault_armed = false;
+  int64_t execs = 0;
+  std::mutex mu;
+};
+
+namespace {
+
+void free_ragged(tfft_ragged_s* r) {
+  if (r->gexec) cudaGraphExecDestroy(r->gexec);
+  if (r->graph) cudaGraphDestroy(r->graph);
+  for (auto& b : r->buckets) {
+    if (b.plan) tfft_destroy(b.plan);
+    if (b.stream) cudaStreamDestroy(b.stream);
+    if (b.done) cudaEventDestroy(b.done);
+  }
+  if (r->fork) cudaEventDestroy(r->fork);
+  if (r->cap) cudaStreamDestroy(r->cap);
+  for (void* p : {r->stage_in, r->stage_out, (void*)r->d_gather, (void*)r->d_scatter})
+    if (p) cudaFree(p);
+  delete r;
+}
+
+bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Median-free timing of one plan: the mean of a few execs after a warm-up.
+float time_plan(tfft_plan_t p, const void* in, void* out, cudaStream_t s) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  tfft_exec(p, in, out, s);
+  cudaEventRecord(a, s);
+  for (int i = 0; i < 3; i++) tfft_exec(p, in, out, s);
+  cudaEventRecord(b, s);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms;
+}
+
+int launch_copy(const tfft_ragged_s* r, const Segment* seg, const void* src, void* dst, cudaStream_t s) {
+  if (r->nseg == 0) return TFFT_SUCCESS;
+  const long long grid = std::min<long long>(r->nseg, (long long)r->sms * 8);
+  ragged_copy_kernel<<<(unsigned)grid, 256, 0, s>>>(seg, r->nseg, static_cast<const unsigned char*>(src),
+                                                     static_cast<unsigned char*>(dst));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TFFT_SUCCESS : record_cuda_error(e);
+}
+
+// gather, bucket plans on their streams, scatter -- all on or joined to `s`
+int enqueue(tfft_ragged_s* r, const void* in, void* out, cudaStream_t s) {
+  int rc;
+  if ((rc = launch_copy(r, r->d_gather, in, r->stage_in, s))) return rc;
+  cudaError_t e;
+  if ((e = cudaEventRecord(r->fork, s)) != cudaSuccess) return record_cuda_error(e);
+  for (auto& b : r->buckets) {
+    if ((e = cudaStreamWaitEvent(b.stream, r->fork, 0)) != cudaSuccess) return record_cuda_error(e);
+    const size_t boff = (size_t)b.base * r->esize;
+    if ((rc = tfft_exec(b.plan, static_cast<const unsigned char*>(r->stage_in) + boff,
+                        static_cast<unsigned char*>(r->stage_out) + boff, (tfft_stream_t)b.stream)))
+      return rc;
+    if ((e = cudaEventRecord(b.done, b.stream)) != cudaSuccess) return record_cuda_error(e);
+    if ((e = cudaStreamWaitEvent(s, b.done, 0)) != cudaSuccess) return record_cuda_error(e);
+  }
+  return launch_copy(r, r->d_scatter, r->stage_out, out, s);
+}
+
+}  // namespace
+
+extern "C" int tfft_ragged_plan(tfft_ragged_t* out, const int64_t* lengths, int64_t count, int dtype,
+                                int abft_mode, int autotune) {
+  if (!out || !lengths || count < 1) return TFFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (dtype != TFFT_C64 && dtype != TFFT_C128) return TFFT_ERR_UNSUPPORTED;
+  const int64_t nmin = dtype == TFFT_C64 ? 2 : 1;   // every signal starts on a 16-byte boundary
+  for (int64_t i = 0; i < count; i++)
+    if (!pow2(lengths[i]) || lengths[i] < nmin || lengths[i] > (int64_t(1) << 26)) return TFFT_ERR_INVALID_ARG;
+  tfft_ragged_s* r = new (std::nothrow) tfft_ragged_s();
+  if (!r) return TFFT_ERR_ALLOC;
+  r->dtype = dtype;
+  r->abft = abft_mode;
+  r->esize = dtype == TFFT_C64 ? 8 : 16;
+  r->count = count;
+  r->off.resize(count);
+  r->local.resize(count);
+  r->bucket_of.resize(count);
+  std::map<int64_t, int> index;
+  for (int64_t i = 0; i < count; i++) {
+    r->off[i] = r->total;
+    r->total += lengths[i];
+    auto it = index.find(lengths[i]);
+    if (it == index.end()) {
+      it = index.emplace(lengths[i], (int)r->buckets.size()).first;
+      r->buckets.emplace_back();
+      r->buckets.back().n = lengths[i];
+    }
+    Bucket& b = r->buckets[it->second];
+    r->bucket_of[i] = it->second;
+    r->local[i] = (int64_t)b.sig.size();
+    b.sig.push_back(i);
+  }
+  // staging: buckets back to back, longest first (the big transforms start first)
+  std::sort(r->buckets.begin(), r->buckets.end(), [](const Bucket& a, const Bucket& b) { return a.n > b.n; });
+  for (size_t k = 0; k < r->buckets.size(); k++)
+    for (int64_t s : r->buckets[k].sig) r->bucket_of[s] = (int)k;
+  int64_t base = 0;
+  for (auto& b : r->buckets) {
+    b.base = base;
+    base += (int64_t)b.sig.size() * b.n;
+  }
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    free_ragged(r);
+    return TFFT_ERR_NO_DEVICE;
+  }
+  r->sms = prop.multiProcessorCount;
+  const size_t bytes = (size_t)r->total * r->esize;
+  if (cudaMalloc(&r->stage_in, bytes) != cudaSuccess || cudaMalloc(&r->stage_out, bytes) != cudaSuccess ||
+      cudaMemset(r->stage_in, 0, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    free_ragged(r);
+    return TFFT_ERR_ALLOC;
+  }
+  // copy segments of at most 64 KiB: caller layout <-> staging
+  std::vector<Segment> gat, sca;
+  const long long kSeg = 64 * 1024;
+  for (const auto& b : r->buckets)
+    for (size_t j = 0; j < b.sig.size(); j++) {
+      const long long src = (long long)r->off[b.sig[j]] * (long long)r->esize;
+      const long long dst = (long long)(b.base + (int64_t)j * b.n) * (long long)r->esize;
+      const long long len = (long long)b.n * (long long)r->esize;
+      for (long long o = 0; o < len; o += kSeg) {
+        const long long L = std::min(kSeg, len - o);
+        gat.push_back(Segment{src + o, dst + o, L});
+        sca.push_back(Segment{dst + o, src + o, L});
+      }
+    }
+  r->nseg = (long long)gat.size();
+  if (cudaMalloc(&r->d_gather, gat.size() * sizeof(Segment)) != cudaSuccess ||
+      cudaMalloc(&r->d_scatter, sca.size() * sizeof(Segment)) != cudaSuccess ||
+      cudaMemcpy(r->d_gather, gat.data(), gat.size() * sizeof(Segment), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(r->d_scatter, sca.data(), sca.size() * sizeof(Segment), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    free_ragged(r);
+    return TFFT_ERR_ALLOC;
+  }
+  // bucket plans; the autotuner times every pass count the length admits
+  for (auto& b : r->buckets) {
+    if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      free_ragged(r);
+      return TFFT_ERR_CUDA;
+    }
+    tfft_plan_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.n = b.n; o.batch = (int64_t)b.sig.size(); o.dtype = dtype; o.abft_mode = abft_mode;
+    int rc = tfft_plan_ex(&b.plan, &o);
+    if (rc) { free_ragged(r); return rc; }
+    tfft_info info;
+    tfft_plan_info(b.plan, &info);
+    b.passes = info.passes;
+    if (autotune) {
+      const size_t boff = (size_t)b.base * r->esize;
+      const void* in = static_cast<unsigned char*>(r->stage_in) + boff;
+      void* o2 = static_cast<unsigned char*>(r->stage_out) + boff;
+      float best = time_plan(b.plan, in, o2, b.stream);
+      for (int passes = 1; passes <= 3; passes++) {
+        if (passes == b.passes) continue;
+        tfft_plan_opts f = o;
+        f.force_passes = passes;
+        tfft_plan_t alt = nullptr;
+        if (tfft_plan_ex(&alt, &f) != TFFT_SUCCESS) { cudaGetLastError(); continue; }
+        const float ms = time_plan(alt, in, o2, b.stream);
+        if (ms < best) {
+          tfft_destroy(b.plan);
+          b.plan = alt;
+          b.passes = passes;
+          best = ms;
+        } else {
+          tfft_destroy(alt);
+        }
+      }
+      tfft_reset_counters(b.plan);
+    }
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) { free_ragged(r); return TFFT_ERR_CUDA; }
+  *out = r;
+  return TFFT_SUCCESS;
+}
+
+extern "C" int tfft_ragged_exec(tfft_ragged_t r, const void* in, void* out, tfft_stream_t stream) {
+  if (!r || !in || !out || (((uintptr_t)in | (uintptr_t)out) & 15u)) return TFFT_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)r->total * r->esize;
+  const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
+  if (a < b + bytes && b < a + bytes) return TFFT_ERR_INPLACE;
+  std::lock_guard<std::mutex> lk(r->mu);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  r->execs++;
+  if (r->fault_armed) {                  // a test fault: run once, uncaptured
+    r->fault_armed = false;
+    return enqueue(r, in, out, s);
+  }
+  if (!r->gexec || r->g_in != in || r->g_out != out) {
+    // captured on a private stream (the legacy default stream cannot be
+    // captured), launched on the caller's
+    if (r->gexec) { cudaGraphExecDestroy(r->gexec); r->gexec = nullptr; }
+    if (r->graph) { cudaGraphDestroy(r->graph); r->graph = nullptr; }
+    cudaError_t e = cudaStreamBeginCapture(r->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    const int rc = enqueue(r, in, out, r->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(r->cap, &g);
+    if (rc || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return rc ? rc : record_cuda_error(e);
+    }
+    r->graph = g;
+    if ((e = cudaGraphInstantiate(&r->gexec, g, 0)) != cudaSuccess) {
+      r->gexec = nullptr;
+      return record_cuda_error(e);
+    }
+    r->g_in = in; r->g_out = out;
+  }
+  const cudaError_t e = cudaGraphLaunch(r->gexec, s);
+  return e == cudaSuccess ? TFFT_SUCCESS : record_cuda_error(e);
+}
+
+extern "C" int tfft_ragged_report(tfft_ragged_t r, tfft_stats* st) {
+  if (!r || !st) return TFFT_ERR_INVALID_ARG;
+  std::memset(st, 0, sizeof(*st));
+  if (cudaDeviceSynchronize() != cudaSuccess) return TFFT_ERR_CUDA;
+  for (auto& b : r->buckets) {
+    tfft_stats s;
+    const int rc = tfft_report_ex(b.plan, &s);
+    if (rc) return rc;
+    st->detected += s.detected;
+    st->corrected += s.corrected;
+    st->recomputed += s.recomputed;
+    st->uncorrectable += s.uncorrectable;
+    st->launches += s.launches;
+    st->max_clean_ratio = std::max(st->max_clean_ratio, s.max_clean_ratio);
+  }
+  st->execs = r->execs;
+  return TFFT_SUCCESS;
+}
+
+extern "C" int tfft_ragged_set_fault(tfft_ragged_t r, int64_t signal, const tfft_fault* fault) {
+  if (!r || !fault || signal < 0 || signal >= r->count) return TFFT_ERR_INVALID_ARG;
+  tfft_fault f = *fault;
+  f.signal = r->local[signal];
+  const int rc = tfft_set_fault(r->buckets[r->bucket_of[signal]].plan, &f);
+  if (rc == TFFT_SUCCESS) r->fault_armed = true;
+  return rc;
+}
+
+extern "C" int tfft_ragged_info(tfft_ragged_t r, int64_t* buckets, int64_t* lengths, int* passes,
+                                int64_t capacity) {
+  if (!r || !buckets) return TFFT_ERR_INVALID_ARG;
+  *buckets = (int64_t)r->buckets.size();
+  for (int64_t k = 0; k < std::min<int64_t>(capacity, *buckets); k++) {
+    if (lengths) lengths[k] = r->buckets[k].n;
+    if (passes) passes[k] = r->buckets[k].passes;
+  }
+  return TFFT_SUCCESS;
+}
+
+extern "C" int tfft_ragged_destroy(tfft_ragged_t r) {
+  if (!r) return TFFT_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  free_ragged(r);
+  return TFFT_SUCCESS;
+}

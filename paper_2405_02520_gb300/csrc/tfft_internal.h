@@ -195,6 +195,9 @@ cudaError_t v3_attrs(int dtype, int role, int nsub, size_t smem, int* blocks_per
 int v3_scratch_bytes(int dtype, int nsub);
 int v3_twiddle_smem_bytes(int dtype, int nsub);
 
+// Keeps `e` as the value tfft_last_cuda_error() reports; returns TFFT_ERR_CUDA.
+int record_cuda_error(cudaError_t e);
+
 // Verify / correction kernels (abft_fix.cu).
 struct VerifyParams {
   int64_t n, batch;

@@ -1,0 +1,80 @@
+"""Ragged batches (signals of different lengths packed back to back) on the
+GPU against the oracle, with graph replay, re-capture and corrected faults."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2405_02520_gb300 as t
+from tests.gpu_util import rel_err_rows, tol
+
+pytestmark = pytest.mark.gpu
+
+
+def _ragged_input(count, seed, lo=6, hi=16):
+    rng = np.random.default_rng(seed)
+    lengths = (1 << rng.integers(lo, hi + 1, size=count)).astype(np.int64)
+    total = int(lengths.sum())
+    x = np.empty(total, dtype=np.complex64)
+    x.real = rng.uniform(-1, 1, total).astype(np.float32)
+    x.imag = rng.uniform(-1, 1, total).astype(np.float32)
+    return lengths, x
+
+
+def _check(lengths, x, y):
+    off = np.concatenate([[0], np.cumsum(lengths)])
+    worst = 0.0
+    for n in np.unique(lengths):
+        idx = np.nonzero(lengths == n)[0]
+        xs = np.stack([x[off[i]:off[i] + n] for i in idx])
+        ys = np.stack([y[off[i]:off[i] + n] for i in idx])
+        err = rel_err_rows(ys, oracle.fft(xs.astype(np.complex128))).max()
+        assert err <= tol(int(n), t.TFFT_C64), (int(n), err)
+        worst = max(worst, err)
+    return worst
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_ragged_matches_oracle_and_replays(autotune):
+    import torch
+    lengths, x = _ragged_input(400, seed=5)
+    r = t.Ragged(lengths.tolist(), autotune=autotune)
+    assert sorted(n for n, _ in r.info()) == sorted(set(lengths.tolist()))
+    xt = torch.from_numpy(x).cuda()
+    yt = torch.empty_like(xt)
+    r.exec(xt, yt)                       # captured
+    torch.cuda.synchronize()
+    y1 = yt.cpu().numpy()
+    _check(lengths, x, y1)
+    yt.zero_()
+    r.exec(xt, yt)                       # replayed
+    torch.cuda.synchronize()
+    assert np.array_equal(yt.cpu().numpy(), y1)
+    y2t = torch.empty_like(xt)
+    r.exec(xt, y2t)                      # new output pointer: re-captured
+    torch.cuda.synchronize()
+    assert np.array_equal(y2t.cpu().numpy(), y1)
+    st = r.report()
+    assert st["detected"] == 0 and st["execs"] == 3
+    r.destroy()
+
+
+def test_ragged_faults_in_two_buckets_corrected():
+    import torch
+    lengths, x = _ragged_input(300, seed=55)
+    r = t.Ragged(lengths.tolist(), autotune=False)
+    xt = torch.from_numpy(x).cuda()
+    yt = torch.empty_like(xt)
+    r.exec(xt, yt)
+    torch.cuda.synchronize()
+    small = int(np.nonzero(lengths == 256)[0][3])
+    large = int(np.nonzero(lengths == 1 << 15)[0][2])
+    passes = dict(r.info())
+    r.set_fault(small, mode=t.TFFT_FAULT_SCALE, pass_=0, stage=0, line=0, index=9, factor=2.0)
+    r.set_fault(large, mode=t.TFFT_FAULT_SCALE, pass_=passes[1 << 15] - 1, stage=0, line=1, index=4,
+                factor=2.0)
+    r.exec(xt, yt)
+    torch.cuda.synchronize()
+    _check(lengths, x, yt.cpu().numpy())
+    st = r.report()
+    assert st["detected"] == 2 and st["corrected"] + st["recomputed"] == 2
+    r.destroy()
