@@ -326,6 +326,18 @@ int tfft_ragged_set_fault(tfft_ragged_t r, int64_t signal, const tfft_fault *fau
 int tfft_ragged_info(tfft_ragged_t r, int64_t *buckets, int64_t *lengths, int *passes, int64_t capacity);
 int tfft_ragged_destroy(tfft_ragged_t r);
 
+/*
+ * tfft_tc_selftest -- one 128 x 32 x 32 product D = A B on the 5th-generation
+ * tensor cores through the same code the split-precision DFT uses (no
+ * counterpart in the paper, which has no tensor-core path): `a` 128 x 32 and
+ * `d` 128 x 32 row-major FP32, `bt` 32 x 32 FP32 holding B transposed (row n
+ * = column n of B), all device pointers; `terms` 1 multiplies the TF32-rounded
+ * operands, 3 adds the products of the high and low TF32 parts
+ * (a_hi b_hi + a_hi b_lo + a_lo b_hi).  Synchronous; returns
+ * TFFT_ERR_TIMEOUT if the product did not complete within the wait bound.
+ */
+int tfft_tc_selftest(const float *a, const float *bt, float *d, int terms);
+
 /* Static string for a status code. */
 const char *tfft_error_string(int status);
 /* The last cudaError_t value seen by the library in this process. */

@@ -109,6 +109,7 @@ def lib() -> ctypes.CDLL:
                 "tfft_ragged_set_fault": [P, I64, ctypes.POINTER(Fault)],
                 "tfft_ragged_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I), I64],
                 "tfft_ragged_destroy": [P],
+                "tfft_tc_selftest": [P, P, P, I],
                 "tfft_error_string": [I],
                 "tfft_last_cuda_error": [],
             }
@@ -271,6 +272,11 @@ class Ragged:
         if self.handle:
             _check(lib().tfft_ragged_destroy(self.handle), "tfft_ragged_destroy")
             self.handle = None
+
+
+def tfft_tc_selftest(a, bt, d, terms: int) -> None:
+    """D = A B for one 128 x 32 x 32 tile on the tensor cores (see include/tfft.h)."""
+    _check(lib().tfft_tc_selftest(_ptr(a), _ptr(bt), _ptr(d), terms), "tfft_tc_selftest")
 
 
 def tfft_exec_noalloc(n: int, batch: int, x, y, stream=None) -> None:
