@@ -127,7 +127,20 @@ typedef struct tfft_plan_opts {
                            (the inverse DFT of Section II without its 1/N)      */
     int normalize;      /* 1: multiply the output by 1/N (with TFFT_INVERSE the
                            exact inverse of the forward transform); 0: none    */
+    int precision;      /* arithmetic of the radix-16 butterflies (complex64):
+                           TFFT_PREC_FP32 (default) FP32 CUDA cores;
+                           TFFT_PREC_TF32X3 tensor cores, operands split into
+                             TF32 high and low parts, three products summed in
+                             FP32 (about 21 significant bits);
+                           TFFT_PREC_TF32 tensor cores, one TF32 product
+                             (about 11 bits).
+                           The tensor-core forms cover n = 2^8..2^12 and 2^16;
+                           other n return TFFT_ERR_UNSUPPORTED.  The detection
+                           threshold uses the form's unit roundoff (2^-20 and
+                           2^-10 in place of 2^-24).                         */
 } tfft_plan_opts;
+
+enum tfft_precision { TFFT_PREC_FP32 = 0, TFFT_PREC_TF32X3 = 1, TFFT_PREC_TF32 = 2 };
 
 /* The inverse runs the forward machinery on conj(x) and stores conj(.)/N:
  * the checksums of Section III check that forward transform, so detection,
@@ -250,6 +263,7 @@ typedef struct tfft_info {
     uint64_t checksum_seed;
     int direction;           /* TFFT_FORWARD / TFFT_INVERSE                    */
     int normalize;           /* 1: output scaled by 1/N                        */
+    int precision;           /* TFFT_PREC_*                                    */
 } tfft_info;
 
 int tfft_plan_info(tfft_plan_t p, tfft_info *info);

@@ -22,6 +22,7 @@ TFFT_C64, TFFT_C128 = 0, 1
 TFFT_ABFT_OFF, TFFT_ABFT_ONE_SIDED, TFFT_ABFT_TWO_SIDED = 0, 1, 2
 TFFT_R_SIGNED_WANG, TFFT_R_WANG = 0, 1
 TFFT_FORWARD, TFFT_INVERSE = 0, 1
+TFFT_PREC_FP32, TFFT_PREC_TF32X3, TFFT_PREC_TF32 = 0, 1, 2
 TFFT_FAULT_NONE, TFFT_FAULT_BITFLIP, TFFT_FAULT_SCALE, TFFT_FAULT_ADD, TFFT_FAULT_ADD_PAIR = 0, 1, 2, 3, 4
 TIMING_KINDS = ("first_pass", "middle_pass", "last_pass", "single_pass", "verify", "correction")
 
@@ -44,7 +45,8 @@ class PlanOpts(ctypes.Structure):
                 ("abft_mode", ctypes.c_int), ("group", ctypes.c_int), ("kappa", ctypes.c_double),
                 ("detect_only", ctypes.c_int), ("max_faults", ctypes.c_int),
                 ("force_passes", ctypes.c_int), ("checksum_vector", ctypes.c_int),
-                ("checksum_seed", ctypes.c_uint64), ("direction", ctypes.c_int), ("normalize", ctypes.c_int)]
+                ("checksum_seed", ctypes.c_uint64), ("direction", ctypes.c_int), ("normalize", ctypes.c_int),
+                ("precision", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -74,7 +76,7 @@ class Info(ctypes.Structure):
                 ("max_faults", ctypes.c_int), ("kappa", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_int64), ("launches_per_exec", ctypes.c_int),
                 ("checksum_vector", ctypes.c_int), ("checksum_seed", ctypes.c_uint64),
-                ("direction", ctypes.c_int), ("normalize", ctypes.c_int)]
+                ("direction", ctypes.c_int), ("normalize", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 def lib() -> ctypes.CDLL:
@@ -162,9 +164,9 @@ def tfft_plan(n: int, batch: int, dtype: int = TFFT_C64, abft_mode: int = TFFT_A
 def tfft_plan_ex(n: int, batch: int, dtype: int = TFFT_C64, abft_mode: int = TFFT_ABFT_TWO_SIDED,
                  group: int = 0, kappa: float = 0.0, detect_only: bool = False, max_faults: int = 0,
                  force_passes: int = 0, checksum_vector: int = TFFT_R_SIGNED_WANG, checksum_seed: int = 0,
-                 direction: int = TFFT_FORWARD, normalize: bool = False) -> int:
+                 direction: int = TFFT_FORWARD, normalize: bool = False, precision: int = TFFT_PREC_FP32) -> int:
     o = PlanOpts(n, batch, dtype, abft_mode, group, kappa, int(detect_only), max_faults, force_passes,
-                 checksum_vector, checksum_seed, direction, int(normalize))
+                 checksum_vector, checksum_seed, direction, int(normalize), precision)
     h = ctypes.c_void_p()
     _check(lib().tfft_plan_ex(ctypes.byref(h), ctypes.byref(o)), "tfft_plan_ex")
     return h.value
@@ -304,11 +306,13 @@ class Plan:
     checksum_seed: int = 0
     direction: int = TFFT_FORWARD
     normalize: bool = False
+    precision: int = TFFT_PREC_FP32
 
     def __post_init__(self):
         self.handle = tfft_plan_ex(self.n, self.batch, self.dtype, self.abft_mode, self.group,
                                    self.kappa, self.detect_only, self.max_faults, self.force_passes,
-                                   self.checksum_vector, self.checksum_seed, self.direction, self.normalize)
+                                   self.checksum_vector, self.checksum_seed, self.direction, self.normalize,
+                                   self.precision)
 
     def exec(self, x, y, stream=None):
         tfft_exec(self.handle, x, y, stream)

@@ -30,6 +30,7 @@
 #pragma once
 
 #include "fft_tile.cuh"
+#include "tc.cuh"
 
 namespace tfft {
 
@@ -335,6 +336,13 @@ __device__ __forceinline__ void copy_out(const PassParams& p, long long tb, long
   }
 }
 
+// Shared memory of the tensor-core operands: per warpgroup the A rows (high,
+// and low for the split form) of its 128 butterflies, and the DFT-16 matrix
+// (high and low); 1024-byte aligned.
+__host__ __device__ constexpr int v3_tc_smem_bytes(int tc) {
+  return tc == 0 ? 0 : 1024 + 2 * (tc == 3 ? 2 : 1) * 16384 + 2 * 4096;
+}
+
 // Blocks per SM the register budget targets: two for complex64 (at most 128
 // registers a thread), one for complex128, whose values take twice the registers.
 template <typename real>
@@ -344,8 +352,16 @@ constexpr int v3_min_blocks() { return sizeof(real) == 4 ? 2 : 1; }
 // nbuf tile loads; afterwards the last warp to finish a tile stores it and
 // refills its buffer with the tile nbuf ahead, so no warp waits for another
 // except on data that has not arrived yet.
-template <typename real, int NSUB, int E, int ROLE>
-__global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(const __grid_constant__ PassParams p) {
+//
+// TC != 0 (complex64, E = 16): every radix-16 butterfly is a row of a dense
+// 128 x 32 x 32 real product on the tensor cores -- the 16 complex inputs of
+// a butterfly interleaved (re, im) times the real 32 x 32 form of the DFT-16
+// matrix -- one product per warpgroup and stage, the accumulator in tensor
+// memory; TC = 1 multiplies TF32-rounded operands, TC = 3 the three-term
+// split (x_hi w_hi + x_hi w_lo + x_lo w_hi) that keeps about 21 bits.
+template <typename real, int NSUB, int E, int ROLE, int TC = 0>
+__global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_kernel(const __grid_constant__ PassParams p) {
+  static_assert(TC == 0 || (sizeof(real) == 4 && E == 16), "tensor-core DFT: complex64, radix 16");
   using G = V3<real, NSUB, E, ROLE>;
   using A = V3Addr<G>;
   using cT = typename G::cT;
@@ -396,7 +412,48 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
     for (int i = t; i < G::TWN; i += G::T) tsm[i] = twt[i];
     twt = tsm;
   }
+  // tensor-core operands and accumulator (TC != 0)
+  __shared__ uint64_t tcbar[2];
+  __shared__ uint32_t tc_tmem;
+  unsigned char* tc_a = nullptr;      // per warpgroup: A high [, A low], 16 KB each
+  unsigned char* tc_b = nullptr;      // DFT-16 matrix, transposed: high, low (4 KB each)
+  if constexpr (TC != 0) {
+    const uintptr_t after = reinterpret_cast<uintptr_t>(scr + G::SCR + (G::TWS ? G::TWN : 0));
+    tc_a = reinterpret_cast<unsigned char*>((after + 1023) & ~uintptr_t(1023));
+    tc_b = tc_a + 2 * (TC == 3 ? 2 : 1) * 16384;
+    if (t < 32) {
+      // row n of B^T = column n of the real 32 x 32 DFT-16 matrix W:
+      // W[2j][2m] = W[2j+1][2m+1] = cos(2 pi jm/16), W[2j][2m+1] = -W[2j+1][2m] = -sin(2 pi jm/16)
+      const int m = t >> 1, im = t & 1;
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        float w[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const int kk = 4 * c + e, j = kk >> 1, kim = kk & 1;
+          const int q = (j * m) & 15;
+          const double cs = Eighths::cosv(q), sn = -Eighths::sinv(q);
+          w[e] = (float)(kim == im ? cs : (kim ? -sn : sn));
+        }
+        const float4 h = {tc::to_tf32(w[0]), tc::to_tf32(w[1]), tc::to_tf32(w[2]), tc::to_tf32(w[3])};
+        *reinterpret_cast<float4*>(tc_b + tc::sw128_off(t, c)) = h;
+        const float4 l = {tc::to_tf32(w[0] - h.x), tc::to_tf32(w[1] - h.y), tc::to_tf32(w[2] - h.z),
+                          tc::to_tf32(w[3] - h.w)};
+        *reinterpret_cast<float4*>(tc_b + 4096 + tc::sw128_off(t, c)) = l;
+      }
+    }
+    fence_proxy_async();
+    if (warp == 0) tc::tmem_alloc(&tc_tmem, 64);
+    if (t == 0) {
+      mbar_init(&tcbar[0], 1);
+      mbar_init(&tcbar[1], 1);
+      fence_mbar_init();
+    }
+    tc::fence_before_sync();
+  }
   __syncthreads();
+  if constexpr (TC != 0) tc::fence_after_sync();
+  uint32_t tc_phase = 0;
 
   const bool abft = p.abft_in || p.abft_out;
   const bool inject = p.fault.mode != 0 && p.fault.pass == p.pass_index;
@@ -412,6 +469,57 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
       asm volatile("bar.sync 1, 256;" ::: "memory");
     } else {
       asm volatile("bar.sync %0, %1;" ::"r"(2 + c0), "r"(32 * G::WPL) : "memory");
+    }
+  };
+
+  // The radix-16 DFT of this thread's 16 values: register butterflies, or
+  // this thread's row of its warpgroup's tensor-core product.
+  auto dft16 = [&](cT* v) {
+    if constexpr (TC == 0) {
+      Dft<E>::run(v);
+    } else {
+      const int wg = warp >> 2, row = t & 127;
+      unsigned char* ahi = tc_a + wg * (TC == 3 ? 2 : 1) * 16384;
+      unsigned char* alo = ahi + 16384;
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        const float4 q = {v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y};
+        const float4 h = {tc::to_tf32(q.x), tc::to_tf32(q.y), tc::to_tf32(q.z), tc::to_tf32(q.w)};
+        *reinterpret_cast<float4*>(ahi + tc::sw128_off(row, c)) = h;
+        if constexpr (TC == 3) {
+          const float4 l = {tc::to_tf32(q.x - h.x), tc::to_tf32(q.y - h.y), tc::to_tf32(q.z - h.z),
+                            tc::to_tf32(q.w - h.w)};
+          *reinterpret_cast<float4*>(alo + tc::sw128_off(row, c)) = l;
+        }
+      }
+      fence_proxy_async();
+      tc::fence_before_sync();
+      asm volatile("bar.sync %0, 128;" ::"r"(8 + wg) : "memory");
+      tc::fence_after_sync();
+      const uint32_t d_tmem = tc_tmem + 32u * wg;
+      if (row == 0) {
+        constexpr uint32_t idesc = tc::instr_desc(2, 128, 32);
+        const unsigned char* as[3] = {ahi, ahi, alo};
+        const unsigned char* bs[3] = {tc_b, tc_b + 4096, tc_b};
+#pragma unroll
+        for (int term = 0; term < (TC == 3 ? 3 : 1); term++)
+#pragma unroll
+          for (int kq = 0; kq < 4; kq++)
+            tc::mma_tf32(d_tmem, tc::smem_desc_sw128(smem_u32(as[term]) + 32u * kq),
+                         tc::smem_desc_sw128(smem_u32(bs[term]) + 32u * kq), idesc, (term | kq) != 0);
+        tc::mma_commit(&tcbar[wg]);
+      }
+      if (!mbar_wait_bounded(&tcbar[wg], tc_phase, abort_flag)) {
+        *abort_flag = 1;
+        atomicExch(p.err_flag, 1);
+      }
+      tc_phase ^= 1u;
+      tc::fence_after_sync();
+      float d[32];
+      tc::tmem_ld32(d_tmem + ((uint32_t)(32 * (warp & 3)) << 16), d);
+#pragma unroll
+      for (int m = 0; m < 16; m++) v[m] = cT{d[2 * m], d[2 * m + 1]};
+      tc::fence_before_sync();
     }
   };
 
@@ -549,14 +657,18 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
       }
       // butterfly u of stage 0 takes v[u + m BPT0] (inputs j0 + u TPL + m NSUB / R0)
       // and writes its output q to position (j0 + u TPL) R0 + q
+      if constexpr (G::R0 == E) {
+        dft16(v);
+      } else {
 #pragma unroll
-      for (int u = 0; u < G::BPT0; u++) {
-        cT w[G::R0];
+        for (int u = 0; u < G::BPT0; u++) {
+          cT w[G::R0];
 #pragma unroll
-        for (int m = 0; m < G::R0; m++) w[m] = v[u + m * G::BPT0];
-        Dft<G::R0>::run(w);
+          for (int m = 0; m < G::R0; m++) w[m] = v[u + m * G::BPT0];
+          Dft<G::R0>::run(w);
 #pragma unroll
-        for (int m = 0; m < G::R0; m++) v[u + m * G::BPT0] = w[m];
+          for (int m = 0; m < G::R0; m++) v[u + m * G::BPT0] = w[m];
+        }
       }
       if (fst == 0) {
 #pragma unroll
@@ -590,7 +702,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
 #pragma unroll
           for (int q = 1; q < E; q++) v[q] = c_mul(v[q], G::TWS ? tw[(q - 1) * Ns] : ldg_c(tw + (q - 1) * Ns));
         }
-        Dft<E>::run(v);
+        dft16(v);
         const int basei = (j0 / Ns) * Ns * E + kk;
         if (fst == st) {
 #pragma unroll
@@ -612,7 +724,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
 #pragma unroll
         for (int q = 1; q < E; q++) v[q] = c_mul(v[q], G::TWS ? tw[(q - 1) * G::TPL] : ldg_c(tw + (q - 1) * G::TPL));
       }
-      Dft<E>::run(v);
+      dft16(v);
       if (ROLE == V3_COLS && p.twiddle) {
         cT f = tw_base;
 #pragma unroll
@@ -740,6 +852,11 @@ __global__ void __launch_bounds__(256, (v3_min_blocks<real>())) fft_v3_kernel(co
     if (abft && !p.per_signal) warp_records(acc, p, cur.g, slot);
   }
   if (lane == 0) bulk_wait_0();
+  if constexpr (TC != 0) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tc_tmem, 64);
+  }
 }
 
 }  // namespace tfft

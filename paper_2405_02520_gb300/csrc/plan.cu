@@ -97,6 +97,7 @@ struct PassPlan {
   int v3 = 0, role = 0;            // v3 kernel (compile-time geometry) and its role
   int vC = 0;                      // v3 lines per tile
   int vdt = 0;                     // v3 kernel family (launch_v3 dtype code)
+  int vtc = 0;                     // v3 tensor-core variant (3 split TF32, 1 TF32), 0 none
   int64_t vLB = 0;                 // v3 line blocks per signal
   unsigned buf_bytes = 0;
   size_t tsmem = 0;
@@ -130,6 +131,7 @@ struct tfft_plan_s {
   int detect_only = 0;
   int inverse = 0, normalize = 0;
   int one_sided = 0;                 // per-signal checksums (verification groups of one)
+  int prec = TFFT_PREC_FP32;         // arithmetic of the radix-16 butterflies
   int vG = 16;                       // signals per verification group
   int64_t vgroups = 0;               // verification groups
   int cap_fix = 1, cap_rec = 1;
@@ -512,6 +514,7 @@ int plan_v3(tfft_plan_s* p) {
   const bool c64 = p->dtype == TFFT_C64;
   const int64_t u = (int64_t)p->esize / 8, es = (int64_t)p->esize;
   const int vdt = c64 ? 0 : 1;
+  const int vtc = p->prec == TFFT_PREC_TF32X3 ? 3 : (p->prec == TFFT_PREC_TF32 ? 1 : 0);
   const int64_t E = c64 ? 16 : 8, TILE = 256 * E;
   const int64_t B = p->batch;
   for (int i = 0; i < p->passes; i++) {
@@ -525,7 +528,10 @@ int plan_v3(tfft_plan_s* p) {
     // chunk indices are 32-bit in the v3 kernels (chunks <= groups x line blocks x G)
     if (p->ngroups * (q.lines_are_signals ? 1 : q.LO * q.HI / C) * (int64_t)p->G >= (int64_t(1) << 31)) continue;
     int bps = 0;
-    if (v3_attrs(vdt, role, (int)nsub, 48 * 1024, &bps) != cudaSuccess) { cudaGetLastError(); continue; }
+    auto attrs = [&](size_t sm, int* b) {
+      return vtc ? v3_attrs_tc(vtc, role, (int)nsub, sm, b) : v3_attrs(vdt, role, (int)nsub, sm, b);
+    };
+    if (attrs(48 * 1024, &bps) != cudaSuccess) { cudaGetLastError(); continue; }
     TileMap mi{}, mo{};
     MapGeom gi = q.gin, go = q.gout;
     const int64_t rows = std::min<int64_t>(nsub, 256);
@@ -602,13 +608,14 @@ int plan_v3(tfft_plan_s* p) {
     const unsigned buf = (unsigned)((C * nsub * es + 1023) / 1024 * 1024);
     // complex64: two blocks per SM, each with at most 110 KB of dynamic
     // shared memory; complex128: one block per SM
-    const size_t budget = (c64 ? 110 : 220) * 1024;
-    const size_t fixed = scr + (size_t)v3_twiddle_smem_bytes(vdt, (int)nsub) + 1024 + 1024;
+    // (tensor-core variants: one block per SM, room for the MMA operands)
+    const size_t budget = (c64 && !vtc ? 110 : 220) * 1024;
+    const size_t fixed = scr + (size_t)v3_twiddle_smem_bytes(vdt, (int)nsub) + (size_t)v3_tc_bytes(vtc) + 1024 + 1024;
     if (fixed + 2 * (size_t)buf > budget) continue;
     const int nbuf = (int)std::min<size_t>(4, (budget - fixed) / buf);
     const size_t smem = (size_t)nbuf * buf + fixed;
-    if (v3_attrs(vdt, role, (int)nsub, smem, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
-    q.v3 = 1; q.role = role; q.tma = 1; q.vdt = vdt;
+    if (attrs(smem, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
+    q.v3 = 1; q.role = role; q.tma = 1; q.vdt = vdt; q.vtc = vtc;
     q.vC = (int)C;
     q.vLB = q.lines_are_signals ? 1 : q.LO * q.HI / C;
     q.map_in = mi; q.map_out = mo; q.gin = gi; q.gout = go;
@@ -825,7 +832,8 @@ int launch_pass(tfft_plan_s* p, PassParams& a, int i, int kind, cudaStream_t s) 
   }
   cudaError_t e;
   if (v3)
-    e = launch_v3(q.vdt, q.role, q.nsub, a, grid, q.tsmem, s);
+    e = q.vtc ? launch_v3_tc(q.vtc, q.role, q.nsub, a, grid, q.tsmem, s)
+              : launch_v3(q.vdt, q.role, q.nsub, a, grid, q.tsmem, s);
   else if (tma)
     e = p->dtype == TFFT_C64 ? launch_tile_f32(a, q.E, grid, q.tsmem, s) : launch_tile_f64(a, q.E, grid, q.tsmem, s);
   else
@@ -907,7 +915,10 @@ int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
     v.n = p->n; v.batch = p->batch; v.group = p->vG; v.ngroups = p->vgroups;
     v.slots_in = p->slots_in; v.slots_out = p->slots_out;
     v.rec_in = p->rec_in; v.rec_out = p->rec_out;
-    const double u = p->dtype == TFFT_C64 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    // unit roundoff of the butterfly arithmetic: FP32, FP64, or the tensor-core forms
+    const double u = p->dtype != TFFT_C64 ? std::ldexp(1.0, -53)
+                   : p->prec == TFFT_PREC_TF32X3 ? std::ldexp(1.0, -20)
+                   : p->prec == TFFT_PREC_TF32 ? std::ldexp(1.0, -10) : std::ldexp(1.0, -24);
     // tau = kappa u (log2 N + 4) sqrt(N) sqrt(E): the log2 N term follows the
     // rounding of the stages, the constant the fixed share of the checksum
     // arithmetic itself (table rounding, FP32 accumulation), which dominates
@@ -953,6 +964,9 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   if (o->checksum_vector != TFFT_R_SIGNED_WANG && o->checksum_vector != TFFT_R_WANG) return TFFT_ERR_INVALID_ARG;
   if ((o->direction != TFFT_FORWARD && o->direction != TFFT_INVERSE) || (o->normalize != 0 && o->normalize != 1))
     return TFFT_ERR_INVALID_ARG;
+  if (o->precision != TFFT_PREC_FP32 && o->precision != TFFT_PREC_TF32X3 && o->precision != TFFT_PREC_TF32)
+    return TFFT_ERR_INVALID_ARG;
+  if (o->precision != TFFT_PREC_FP32 && o->dtype != TFFT_C64) return TFFT_ERR_UNSUPPORTED;
   int dev = 0, count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) return TFFT_ERR_NO_DEVICE;
   TFFT_CUDA(cudaGetDevice(&dev));
@@ -970,6 +984,7 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   p->rvec = o->checksum_vector == TFFT_R_WANG ? RVEC_WANG : RVEC_SIGNED_WANG;
   if (o->checksum_seed) p->rseed = (unsigned long long)o->checksum_seed;
   p->inverse = o->direction == TFFT_INVERSE;
+  p->prec = o->precision;
   p->normalize = o->normalize;
   p->device = dev;
   p->sms = prop.multiProcessorCount;
@@ -977,9 +992,9 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   if (!rc) rc = plan_tma(p);
   if (!rc) rc = plan_v3(p);
   if (!rc) plan_slots(p);
-  if (!rc && p->one_sided)
+  if (!rc && (p->one_sided || p->prec != TFFT_PREC_FP32))
     for (int i = 0; i < p->passes; i++)
-      if (!p->pp[i].v3) rc = TFFT_ERR_UNSUPPORTED;   // per-signal records live in the tile kernels
+      if (!p->pp[i].v3) rc = TFFT_ERR_UNSUPPORTED;   // per-signal records and tensor cores live in the tile kernels
   if (!rc) rc = plan_tables(p);
   if (!rc) rc = plan_workspace(p);
   if (!rc) rc = plan_wtable(p);
@@ -1126,6 +1141,7 @@ int tfft_plan_info(tfft_plan_t p, tfft_info* info) {
   info->checksum_vector = p->rvec == RVEC_WANG ? TFFT_R_WANG : TFFT_R_SIGNED_WANG;
   info->checksum_seed = p->rseed;
   info->direction = p->inverse ? TFFT_INVERSE : TFFT_FORWARD;
+  info->precision = p->prec;
   info->normalize = p->normalize;
   return TFFT_SUCCESS;
 }

@@ -194,6 +194,10 @@ cudaError_t launch_v3(int dtype, int role, int nsub, const PassParams& p, int gr
 cudaError_t v3_attrs(int dtype, int role, int nsub, size_t smem, int* blocks_per_sm);
 int v3_scratch_bytes(int dtype, int nsub);
 int v3_twiddle_smem_bytes(int dtype, int nsub);
+// Tensor-core variants (v3_tc.cu): tc = 3 split TF32, 1 plain TF32.
+cudaError_t launch_v3_tc(int tc, int role, int nsub, const PassParams& p, int grid, size_t smem, cudaStream_t s);
+cudaError_t v3_attrs_tc(int tc, int role, int nsub, size_t smem, int* blocks_per_sm);
+int v3_tc_bytes(int tc);
 
 // Keeps `e` as the value tfft_last_cuda_error() reports; returns TFFT_ERR_CUDA.
 int record_cuda_error(cudaError_t e);
