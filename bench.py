@@ -357,6 +357,7 @@ def run_ours(args):
         t.tfft_destroy(off[lg])
 
     ragged = None if args.no_ragged else ragged_measure(t, torch, stream, args, peak)
+    tensor = None if args.no_ragged else tc_measure(t, torch, stream, peak)
     ablation = None if args.no_ragged else one_sided_measure(t, torch, x, y, stream, args)
 
     # end to end through the C ABI with host buffers (pinned), copies timed
@@ -455,6 +456,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "ragged": ragged,
         "one_sided": ablation,
+        "tensor_core": tensor,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -505,6 +507,40 @@ def ragged_measure(t, torch, stream, args, peak):
     return out
 
 
+def tc_measure(t, torch, stream, peak):
+    """The radix-16 butterflies on FP32 CUDA cores and on the tensor cores
+    (split TF32, plain TF32) at N = 4096 x 65536 and 65536 x 4096 signals,
+    N(0, 0.3^2) re/im, ABFT on.  Timing only; the error of each form against
+    the oracle is measured by the tests."""
+    out = {}
+    for n, batch in ((4096, 65536), (65536, 4096)):
+        xs = torch.empty((batch, n), dtype=torch.complex64, device=stream.device)
+        g = torch.Generator(device=stream.device).manual_seed(4)
+        xs.real.normal_(0, 0.3, generator=g)
+        xs.imag.normal_(0, 0.3, generator=g)
+        ys = torch.empty_like(xs)
+        res = {}
+        for name, prec in (("fp32", t.TFFT_PREC_FP32), ("tf32x3", t.TFFT_PREC_TF32X3), ("tf32", t.TFFT_PREC_TF32)):
+            pl = t.tfft_plan_ex(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED, precision=prec)
+            passes = t.tfft_plan_info(pl)["passes"]
+            for _ in range(3):
+                t.tfft_exec(pl, xs, ys, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                t.tfft_exec(pl, xs, ys, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 5
+            res[name] = {"ms": round(ms, 4), "gflops": round(flops(n, batch) / (ms / 1e3) / 1e9, 1),
+                         "hbm_frac": round(16.0 * passes * n * batch / (ms / 1e3) / 1e9 / peak, 4),
+                         "detected": t.tfft_report(pl)[0]}
+            t.tfft_destroy(pl)
+        out[f"{n}x{batch}"] = res
+        del xs, ys
+    return out
+
+
 def one_sided_measure(t, torch, x, y, stream, args):
     """The one-sided ABFT mode (per-signal checks, recompute on detection) as
     an ablation of the two-sided scheme: N = 2^10 and 2^16, 2^28 elements."""
@@ -545,7 +581,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ragged", action="store_true",
-                    help="skip the ragged-batch and one-sided-mode measurements")
+                    help="skip the ragged-batch, one-sided-mode and tensor-core measurements")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)      # at least three untimed warm-up steps
     if args.impl == "reference":
