@@ -495,8 +495,18 @@ def ragged_measure(t, torch, stream, args, peak):
         if mode == t.TFFT_ABFT_TWO_SIDED:
             info = dict(r.info())
             st = r.report()
-            out["detected"] = st["detected"]
+            out["detected_clean"] = st["detected"]
             out["buckets"] = {str(n): p for n, p in sorted(info.items())}
+            # one fault per 1000 signals, in distinct checksum groups, one exec
+            sites = ragged_fault_sites(lengths, 1, seed=5)
+            for k, i in enumerate(sites):
+                n = int(lengths[i])
+                r.set_fault(i, mode=t.TFFT_FAULT_SCALE, pass_=info[n] - 1, stage=0, line=0,
+                            index=(7 * k + 1) % 16, factor=3.0)
+            r.exec(xr, yr, stream)
+            st2 = r.report()
+            out["faults"] = {"injected": len(sites), "detected": st2["detected"] - st["detected"],
+                             "corrected": st2["corrected"] + st2["recomputed"] - st["corrected"] - st["recomputed"]}
         r.destroy()
     fl = sum(float(flops(int(n), 1)) for n in lengths)
     passes = {int(n): p for n, p in ((int(k), v) for k, v in out["buckets"].items())}
@@ -504,6 +514,31 @@ def ragged_measure(t, torch, stream, args, peak):
     out["gflops"] = round(fl / (out["ms"] / 1e3) / 1e9, 1)
     out["hbm_frac"] = round(alg / (out["ms"] / 1e3) / 1e9 / peak, 4)
     out["abft_overhead_pct"] = round((out["ms"] - out["ms_abft_off"]) / out["ms_abft_off"] * 100, 2)
+    return out
+
+
+def ragged_fault_sites(lengths, per_1000, seed):
+    """Signals to fault: `per_1000` per 1000 signals, in distinct checksum
+    groups (16 consecutive signals of one length), at most four per length
+    (one below 256 points, where the armed sites after the first are not
+    honoured)."""
+    rng = np.random.default_rng(seed)
+    want = max(1, len(lengths) * per_1000 // 1000)
+    local, counts = {}, {}
+    for i, n in enumerate(lengths):
+        local[i] = counts.get(int(n), 0)
+        counts[int(n)] = local[i] + 1
+    used, per_len, out = set(), {}, []
+    for i in rng.permutation(len(lengths)):
+        n = int(lengths[i])
+        g = (n, local[int(i)] // 16)
+        if g in used or per_len.get(n, 0) >= (1 if n < 256 else 4):
+            continue
+        used.add(g)
+        per_len[n] = per_len.get(n, 0) + 1
+        out.append(int(i))
+        if len(out) == want:
+            break
     return out
 
 

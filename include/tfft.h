@@ -244,7 +244,12 @@ typedef struct tfft_fault {
     double factor;
 } tfft_fault;
 
+/* Arms `fault` for the next exec.  Up to TFFT_MAX_FAULT_SITES calls before
+ * one exec arm that many sites (sites after the first are honoured by the
+ * tile kernels, i.e. complex64 n >= 256, complex128 n >= 128 and every
+ * multi-pass n); mode TFFT_FAULT_NONE disarms all.  An exec consumes them. */
 int tfft_set_fault(tfft_plan_t p, const tfft_fault *fault);
+#define TFFT_MAX_FAULT_SITES 4
 
 typedef struct tfft_info {
     int64_t n, batch;

@@ -456,7 +456,11 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
   uint32_t tc_phase = 0;
 
   const bool abft = p.abft_in || p.abft_out;
-  const bool inject = p.fault.mode != 0 && p.fault.pass == p.pass_index;
+  bool inject = false;     // a fault site is armed for this pass
+  for (int q = 0; q < p.nfault && q < 4; q++) {
+    const FaultSite& f = q == 0 ? p.fault : p.fault_more[q - 1];
+    inject |= f.mode != 0 && f.pass == p.pass_index;
+  }
 
   // this thread's line and butterfly index inside the tile
   const int c0 = G::WL ? warp * G::LPW + lane / G::TPL : warp / G::WPL;
@@ -620,8 +624,17 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
       const long long b0 = (ROLE == V3_SINGLE) ? tb + c0 : tb;     // this thread's signal
       const bool valid = b0 < se;
       // the stage at which this thread plants the test fault (none: -9)
-      const int fst = (inject && valid && fault_signal(p.fault, b0) && p.fault.line == line_c) ? p.fault.stage
-                                                                                               : -9;
+      int fst = -9, fk = 0;
+      if (inject && valid) {
+        for (int q = 0; q < p.nfault && q < 4; q++) {
+          const FaultSite& f = q == 0 ? p.fault : p.fault_more[q - 1];
+          if (fst == -9 && f.mode != 0 && f.pass == p.pass_index && fault_signal(f, b0) && f.line == line_c) {
+            fst = f.stage;
+            fk = q;
+          }
+        }
+      }
+      const FaultSite& fs = fk == 0 ? p.fault : p.fault_more[fk - 1];
 
       // ---------------- stage 0: box -> registers, radix R0 -> scratch ----------------
       cT v[E];
@@ -653,7 +666,7 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
       if (fst == -1) {
 #pragma unroll
         for (int r = 0; r < E; r++)
-          if (p.fault.index == j0 + r * G::TPL) v[r] = faulted(v[r], p.fault);
+          if (fs.index == j0 + r * G::TPL) v[r] = faulted(v[r], fs);
       }
       // butterfly u of stage 0 takes v[u + m BPT0] (inputs j0 + u TPL + m NSUB / R0)
       // and writes its output q to position (j0 + u TPL) R0 + q
@@ -675,7 +688,7 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
         for (int u = 0; u < G::BPT0; u++)
 #pragma unroll
           for (int q = 0; q < G::R0; q++)
-            if (p.fault.index == (j0 + u * G::TPL) * G::R0 + q) v[u + q * G::BPT0] = faulted(v[u + q * G::BPT0], p.fault);
+            if (fs.index == (j0 + u * G::TPL) * G::R0 + q) v[u + q * G::BPT0] = faulted(v[u + q * G::BPT0], fs);
       }
       if constexpr (!G::WL) line_sync();   // the previous tile's last-stage reads are done
 #pragma unroll
@@ -707,7 +720,7 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
         if (fst == st) {
 #pragma unroll
           for (int q = 0; q < E; q++)
-            if (p.fault.index == basei + q * Ns) v[q] = faulted(v[q], p.fault);
+            if (fs.index == basei + q * Ns) v[q] = faulted(v[q], fs);
         }
         const int wb = scr_c + A::idx(basei);
 #pragma unroll
@@ -736,7 +749,7 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
       if (fst == G::S - 1) {
 #pragma unroll
         for (int q = 0; q < E; q++)
-          if (p.fault.index == j0 + q * G::TPL) v[q] = faulted(v[q], p.fault);
+          if (fs.index == j0 + q * G::TPL) v[q] = faulted(v[q], fs);
       }
       if (p.abft_out && valid) {
         // T += sum_q s_q w3^(k0 + q dl) y_q: group the outputs by q mod 3

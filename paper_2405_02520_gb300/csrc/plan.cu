@@ -157,7 +157,9 @@ struct tfft_plan_s {
   const void* enc_ptr[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
   CUtensorMap enc_map[3][2];
 
-  FaultSite pending{};
+  FaultSite pending{};                 // first armed fault site (every kernel)
+  FaultSite pending_more[3]{};          // further sites (tile kernels)
+  int npending = 0;
   int64_t execs = 0, launches = 0;
   cudaStream_t last_stream = nullptr;
   bool used = false;
@@ -893,6 +895,8 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
       if (p->passes == 1) a.slots = p->slots_in;
       a.rec_in = p->rec_in; a.rec_out = p->rec_out;
       a.fault = p->pending;
+      for (int k = 0; k < 3; k++) a.fault_more[k] = p->pending_more[k];
+      a.nfault = p->npending;
       if (i == 0 && p->abft) { a.zero_on_entry[0] = p->lists.fix; a.zero_on_entry[1] = p->lists.rec; }
     } else {
       a.list = list; a.list_identity = list_identity; a.list_cap = list_cap;
@@ -1018,7 +1022,9 @@ int tfft_exec(tfft_plan_t p, const void* in, void* out, tfft_stream_t stream) {
   std::lock_guard<std::mutex> lk(p->mu);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int rc = exec_device(p, in, out, s);
-  p->pending = FaultSite{};     // an armed fault lasts one exec
+  p->pending = FaultSite{};     // armed faults last one exec
+  for (auto& f : p->pending_more) f = FaultSite{};
+  p->npending = 0;
   p->execs++;
   p->last_stream = s;
   p->used = true;
@@ -1117,7 +1123,19 @@ int tfft_set_fault(tfft_plan_t p, const tfft_fault* f) {
   s.mode = f->mode; s.pass = f->pass; s.stage = f->stage; s.bit = f->bit;
   s.signal = f->signal; s.line = f->line; s.index = f->index; s.factor = f->factor;
   std::lock_guard<std::mutex> lk(p->mu);
-  p->pending = s;
+  if (s.mode == 0) {
+    p->pending = FaultSite{};
+    for (auto& f : p->pending_more) f = FaultSite{};
+    p->npending = 0;
+  } else if (p->npending == 0) {
+    p->pending = s;
+    p->npending = 1;
+  } else if (p->npending < TFFT_MAX_FAULT_SITES) {
+    p->pending_more[p->npending - 1] = s;
+    p->npending++;
+  } else {
+    return TFFT_ERR_INVALID_ARG;
+  }
   return TFFT_SUCCESS;
 }
 

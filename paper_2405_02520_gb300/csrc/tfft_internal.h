@@ -162,6 +162,8 @@ struct PassParams {
   int64_t list_block;     // signals per listed block
 
   int64_t nchunks;
+  FaultSite fault_more[3];   // armed sites after `fault` (tile kernels only)
+  int nfault;                // armed sites in total (0..4)
   // inverse / normalised transforms: conj on load (first pass), conj and
   // scale on store (last pass); the checksums see the forward transform
   int conj_in, conj_out;

@@ -78,3 +78,53 @@ def test_ragged_faults_in_two_buckets_corrected():
     st = r.report()
     assert st["detected"] == 2 and st["corrected"] + st["recomputed"] == 2
     r.destroy()
+
+
+def _fault_sites(lengths, per_1000, seed):
+    """Signals to fault, one per `1000 / per_1000` signals, in distinct ABFT
+    groups (16 consecutive signals of one length), at most four per length
+    and one per length below 256 points."""
+    rng = np.random.default_rng(seed)
+    want = max(1, len(lengths) * per_1000 // 1000)
+    order = rng.permutation(len(lengths))
+    local = {}
+    counts = {}
+    for i, n in enumerate(lengths):
+        local[i] = counts.get(int(n), 0)
+        counts[int(n)] = local[i] + 1
+    used, per_len, out = set(), {}, []
+    for i in order:
+        n = int(lengths[i])
+        g = (n, local[i] // 16)
+        cap = 1 if n < 256 else 4
+        if g in used or per_len.get(n, 0) >= cap:
+            continue
+        used.add(g)
+        per_len[n] = per_len.get(n, 0) + 1
+        out.append(int(i))
+        if len(out) == want:
+            break
+    return out
+
+
+def test_ragged_one_fault_per_thousand_signals():
+    """4000 signals (2^6..2^12 points), four faults in distinct groups in one
+    exec: all detected and corrected."""
+    import torch
+    lengths, x = _ragged_input(4000, seed=505, lo=6, hi=12)
+    r = t.Ragged(lengths.tolist(), autotune=False)
+    passes = dict(r.info())
+    sites = _fault_sites(lengths, 1, seed=7)
+    assert len(sites) == 4
+    for k, i in enumerate(sites):
+        n = int(lengths[i])
+        r.set_fault(i, mode=t.TFFT_FAULT_SCALE, pass_=passes[n] - 1, stage=0, line=0, index=(3 * k + 1) % n,
+                    factor=3.0)
+    xt = torch.from_numpy(x).cuda()
+    yt = torch.empty_like(xt)
+    r.exec(xt, yt)
+    torch.cuda.synchronize()
+    _check(lengths, x, yt.cpu().numpy())
+    st = r.report()
+    assert st["detected"] == 4 and st["corrected"] + st["recomputed"] == 4, st
+    r.destroy()
