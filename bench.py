@@ -544,7 +544,7 @@ def ragged_fault_sites(lengths, per_1000, seed):
 
 def tc_measure(t, torch, stream, peak):
     """The radix-16 butterflies on FP32 CUDA cores and on the tensor cores
-    (split TF32, plain TF32) at N = 4096 x 65536 and 65536 x 4096 signals,
+    (split TF32, split BF16, plain TF32) at N = 4096 x 65536 and 65536 x 4096 signals,
     N(0, 0.3^2) re/im, ABFT on.  Timing only; the error of each form against
     the oracle is measured by the tests."""
     out = {}
@@ -555,7 +555,8 @@ def tc_measure(t, torch, stream, peak):
         xs.imag.normal_(0, 0.3, generator=g)
         ys = torch.empty_like(xs)
         res = {}
-        for name, prec in (("fp32", t.TFFT_PREC_FP32), ("tf32x3", t.TFFT_PREC_TF32X3), ("tf32", t.TFFT_PREC_TF32)):
+        for name, prec in (("fp32", t.TFFT_PREC_FP32), ("tf32x3", t.TFFT_PREC_TF32X3),
+                           ("bf16x3", t.TFFT_PREC_BF16X3), ("tf32", t.TFFT_PREC_TF32)):
             pl = t.tfft_plan_ex(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED, precision=prec)
             passes = t.tfft_plan_info(pl)["passes"]
             for _ in range(3):

@@ -133,14 +133,16 @@ typedef struct tfft_plan_opts {
                              TF32 high and low parts, three products summed in
                              FP32 (about 21 significant bits);
                            TFFT_PREC_TF32 tensor cores, one TF32 product
-                             (about 11 bits).
+                             (about 11 bits);
+                           TFFT_PREC_BF16X3 tensor cores, BF16 high and low
+                             parts, three products (about 16 bits).
                            The tensor-core forms cover n = 2^8..2^12 and 2^16;
                            other n return TFFT_ERR_UNSUPPORTED.  The detection
-                           threshold uses the form's unit roundoff (2^-20 and
-                           2^-10 in place of 2^-24).                         */
+                           threshold uses the form's unit roundoff (2^-20,
+                           2^-10 and 2^-17 in place of 2^-24).               */
 } tfft_plan_opts;
 
-enum tfft_precision { TFFT_PREC_FP32 = 0, TFFT_PREC_TF32X3 = 1, TFFT_PREC_TF32 = 2 };
+enum tfft_precision { TFFT_PREC_FP32 = 0, TFFT_PREC_TF32X3 = 1, TFFT_PREC_TF32 = 2, TFFT_PREC_BF16X3 = 3 };
 
 /* The inverse runs the forward machinery on conj(x) and stores conj(.)/N:
  * the checksums of Section III check that forward transform, so detection,

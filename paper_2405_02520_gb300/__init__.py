@@ -22,7 +22,7 @@ TFFT_C64, TFFT_C128 = 0, 1
 TFFT_ABFT_OFF, TFFT_ABFT_ONE_SIDED, TFFT_ABFT_TWO_SIDED = 0, 1, 2
 TFFT_R_SIGNED_WANG, TFFT_R_WANG = 0, 1
 TFFT_FORWARD, TFFT_INVERSE = 0, 1
-TFFT_PREC_FP32, TFFT_PREC_TF32X3, TFFT_PREC_TF32 = 0, 1, 2
+TFFT_PREC_FP32, TFFT_PREC_TF32X3, TFFT_PREC_TF32, TFFT_PREC_BF16X3 = 0, 1, 2, 3
 TFFT_FAULT_NONE, TFFT_FAULT_BITFLIP, TFFT_FAULT_SCALE, TFFT_FAULT_ADD, TFFT_FAULT_ADD_PAIR = 0, 1, 2, 3, 4
 TIMING_KINDS = ("first_pass", "middle_pass", "last_pass", "single_pass", "verify", "correction")
 

@@ -340,7 +340,7 @@ __device__ __forceinline__ void copy_out(const PassParams& p, long long tb, long
 // and low for the split form) of its 128 butterflies, and the DFT-16 matrix
 // (high and low); 1024-byte aligned.
 __host__ __device__ constexpr int v3_tc_smem_bytes(int tc) {
-  return tc == 0 ? 0 : 1024 + 2 * (tc == 3 ? 2 : 1) * 16384 + 2 * 4096;
+  return tc == 0 ? 0 : 1024 + 2 * (tc == 1 ? 1 : 2) * 16384 + 2 * 4096;
 }
 
 // Blocks per SM the register budget targets: two for complex64 (at most 128
@@ -420,26 +420,39 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
   if constexpr (TC != 0) {
     const uintptr_t after = reinterpret_cast<uintptr_t>(scr + G::SCR + (G::TWS ? G::TWN : 0));
     tc_a = reinterpret_cast<unsigned char*>((after + 1023) & ~uintptr_t(1023));
-    tc_b = tc_a + 2 * (TC == 3 ? 2 : 1) * 16384;
+    tc_b = tc_a + 2 * (TC == 1 ? 1 : 2) * 16384;
     if (t < 32) {
       // row n of B^T = column n of the real 32 x 32 DFT-16 matrix W:
       // W[2j][2m] = W[2j+1][2m+1] = cos(2 pi jm/16), W[2j][2m+1] = -W[2j+1][2m] = -sin(2 pi jm/16)
       const int m = t >> 1, im = t & 1;
+      auto wval = [&](int kk) -> float {
+        const int j = kk >> 1, kim = kk & 1;
+        const int q = (j * m) & 15;
+        const double cs = Eighths::cosv(q), sn = -Eighths::sinv(q);
+        return (float)(kim == im ? cs : (kim ? -sn : sn));
+      };
+      if constexpr (TC == 2) {
+        // BF16: 32 values = 64 bytes, chunks 0..3 of the 128-byte row
 #pragma unroll
-      for (int c = 0; c < 8; c++) {
-        float w[4];
+        for (int c = 0; c < 4; c++) {
+          uint32_t h[4], l[4];
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-          const int kk = 4 * c + e, j = kk >> 1, kim = kk & 1;
-          const int q = (j * m) & 15;
-          const double cs = Eighths::cosv(q), sn = -Eighths::sinv(q);
-          w[e] = (float)(kim == im ? cs : (kim ? -sn : sn));
+          for (int e = 0; e < 4; e++) tc::split_bf16x2(wval(8 * c + 2 * e), wval(8 * c + 2 * e + 1), h[e], l[e]);
+          *reinterpret_cast<uint4*>(tc_b + tc::sw128_off(t, c)) = uint4{h[0], h[1], h[2], h[3]};
+          *reinterpret_cast<uint4*>(tc_b + 4096 + tc::sw128_off(t, c)) = uint4{l[0], l[1], l[2], l[3]};
         }
-        const float4 h = {tc::to_tf32(w[0]), tc::to_tf32(w[1]), tc::to_tf32(w[2]), tc::to_tf32(w[3])};
-        *reinterpret_cast<float4*>(tc_b + tc::sw128_off(t, c)) = h;
-        const float4 l = {tc::to_tf32(w[0] - h.x), tc::to_tf32(w[1] - h.y), tc::to_tf32(w[2] - h.z),
-                          tc::to_tf32(w[3] - h.w)};
-        *reinterpret_cast<float4*>(tc_b + 4096 + tc::sw128_off(t, c)) = l;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+          float w[4];
+#pragma unroll
+          for (int e = 0; e < 4; e++) w[e] = wval(4 * c + e);
+          const float4 h = {tc::to_tf32(w[0]), tc::to_tf32(w[1]), tc::to_tf32(w[2]), tc::to_tf32(w[3])};
+          *reinterpret_cast<float4*>(tc_b + tc::sw128_off(t, c)) = h;
+          const float4 l = {tc::to_tf32(w[0] - h.x), tc::to_tf32(w[1] - h.y), tc::to_tf32(w[2] - h.z),
+                            tc::to_tf32(w[3] - h.w)};
+          *reinterpret_cast<float4*>(tc_b + 4096 + tc::sw128_off(t, c)) = l;
+        }
       }
     }
     fence_proxy_async();
@@ -483,17 +496,31 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
       Dft<E>::run(v);
     } else {
       const int wg = warp >> 2, row = t & 127;
-      unsigned char* ahi = tc_a + wg * (TC == 3 ? 2 : 1) * 16384;
+      unsigned char* ahi = tc_a + wg * (TC == 1 ? 1 : 2) * 16384;
       unsigned char* alo = ahi + 16384;
+      if constexpr (TC == 2) {
 #pragma unroll
-      for (int c = 0; c < 8; c++) {
-        const float4 q = {v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y};
-        const float4 h = {tc::to_tf32(q.x), tc::to_tf32(q.y), tc::to_tf32(q.z), tc::to_tf32(q.w)};
-        *reinterpret_cast<float4*>(ahi + tc::sw128_off(row, c)) = h;
-        if constexpr (TC == 3) {
-          const float4 l = {tc::to_tf32(q.x - h.x), tc::to_tf32(q.y - h.y), tc::to_tf32(q.z - h.z),
-                            tc::to_tf32(q.w - h.w)};
-          *reinterpret_cast<float4*>(alo + tc::sw128_off(row, c)) = l;
+        for (int c = 0; c < 4; c++) {
+          uint32_t h[4], l[4];
+#pragma unroll
+          for (int e = 0; e < 2; e++) {
+            tc::split_bf16x2(v[4 * c + 2 * e].x, v[4 * c + 2 * e].y, h[2 * e], l[2 * e]);
+            tc::split_bf16x2(v[4 * c + 2 * e + 1].x, v[4 * c + 2 * e + 1].y, h[2 * e + 1], l[2 * e + 1]);
+          }
+          *reinterpret_cast<uint4*>(ahi + tc::sw128_off(row, c)) = uint4{h[0], h[1], h[2], h[3]};
+          *reinterpret_cast<uint4*>(alo + tc::sw128_off(row, c)) = uint4{l[0], l[1], l[2], l[3]};
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+          const float4 q = {v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y};
+          const float4 h = {tc::to_tf32(q.x), tc::to_tf32(q.y), tc::to_tf32(q.z), tc::to_tf32(q.w)};
+          *reinterpret_cast<float4*>(ahi + tc::sw128_off(row, c)) = h;
+          if constexpr (TC == 3) {
+            const float4 l = {tc::to_tf32(q.x - h.x), tc::to_tf32(q.y - h.y), tc::to_tf32(q.z - h.z),
+                              tc::to_tf32(q.w - h.w)};
+            *reinterpret_cast<float4*>(alo + tc::sw128_off(row, c)) = l;
+          }
         }
       }
       fence_proxy_async();
@@ -502,15 +529,26 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
       tc::fence_after_sync();
       const uint32_t d_tmem = tc_tmem + 32u * wg;
       if (row == 0) {
-        constexpr uint32_t idesc = tc::instr_desc(2, 128, 32);
         const unsigned char* as[3] = {ahi, ahi, alo};
         const unsigned char* bs[3] = {tc_b, tc_b + 4096, tc_b};
+        if constexpr (TC == 2) {
+          // BF16: K = 16 values (32 bytes) per product, two products per term
+          constexpr uint32_t idesc = tc::instr_desc(1, 128, 32);
 #pragma unroll
-        for (int term = 0; term < (TC == 3 ? 3 : 1); term++)
+          for (int term = 0; term < 3; term++)
 #pragma unroll
-          for (int kq = 0; kq < 4; kq++)
-            tc::mma_tf32(d_tmem, tc::smem_desc_sw128(smem_u32(as[term]) + 32u * kq),
-                         tc::smem_desc_sw128(smem_u32(bs[term]) + 32u * kq), idesc, (term | kq) != 0);
+            for (int kq = 0; kq < 2; kq++)
+              tc::mma_f16(d_tmem, tc::smem_desc_sw128(smem_u32(as[term]) + 32u * kq),
+                          tc::smem_desc_sw128(smem_u32(bs[term]) + 32u * kq), idesc, (term | kq) != 0);
+        } else {
+          constexpr uint32_t idesc = tc::instr_desc(2, 128, 32);
+#pragma unroll
+          for (int term = 0; term < (TC == 3 ? 3 : 1); term++)
+#pragma unroll
+            for (int kq = 0; kq < 4; kq++)
+              tc::mma_tf32(d_tmem, tc::smem_desc_sw128(smem_u32(as[term]) + 32u * kq),
+                           tc::smem_desc_sw128(smem_u32(bs[term]) + 32u * kq), idesc, (term | kq) != 0);
+        }
         tc::mma_commit(&tcbar[wg]);
       }
       if (!mbar_wait_bounded(&tcbar[wg], tc_phase, abort_flag)) {

@@ -516,7 +516,8 @@ int plan_v3(tfft_plan_s* p) {
   const bool c64 = p->dtype == TFFT_C64;
   const int64_t u = (int64_t)p->esize / 8, es = (int64_t)p->esize;
   const int vdt = c64 ? 0 : 1;
-  const int vtc = p->prec == TFFT_PREC_TF32X3 ? 3 : (p->prec == TFFT_PREC_TF32 ? 1 : 0);
+  const int vtc = p->prec == TFFT_PREC_TF32X3 ? 3
+                : p->prec == TFFT_PREC_BF16X3 ? 2 : (p->prec == TFFT_PREC_TF32 ? 1 : 0);
   const int64_t E = c64 ? 16 : 8, TILE = 256 * E;
   const int64_t B = p->batch;
   for (int i = 0; i < p->passes; i++) {
@@ -922,7 +923,8 @@ int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
     // unit roundoff of the butterfly arithmetic: FP32, FP64, or the tensor-core forms
     const double u = p->dtype != TFFT_C64 ? std::ldexp(1.0, -53)
                    : p->prec == TFFT_PREC_TF32X3 ? std::ldexp(1.0, -20)
-                   : p->prec == TFFT_PREC_TF32 ? std::ldexp(1.0, -10) : std::ldexp(1.0, -24);
+                   : p->prec == TFFT_PREC_TF32 ? std::ldexp(1.0, -10)
+                   : p->prec == TFFT_PREC_BF16X3 ? std::ldexp(1.0, -17) : std::ldexp(1.0, -24);
     // tau = kappa u (log2 N + 4) sqrt(N) sqrt(E): the log2 N term follows the
     // rounding of the stages, the constant the fixed share of the checksum
     // arithmetic itself (table rounding, FP32 accumulation), which dominates
@@ -968,8 +970,7 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   if (o->checksum_vector != TFFT_R_SIGNED_WANG && o->checksum_vector != TFFT_R_WANG) return TFFT_ERR_INVALID_ARG;
   if ((o->direction != TFFT_FORWARD && o->direction != TFFT_INVERSE) || (o->normalize != 0 && o->normalize != 1))
     return TFFT_ERR_INVALID_ARG;
-  if (o->precision != TFFT_PREC_FP32 && o->precision != TFFT_PREC_TF32X3 && o->precision != TFFT_PREC_TF32)
-    return TFFT_ERR_INVALID_ARG;
+  if (o->precision < TFFT_PREC_FP32 || o->precision > TFFT_PREC_BF16X3) return TFFT_ERR_INVALID_ARG;
   if (o->precision != TFFT_PREC_FP32 && o->dtype != TFFT_C64) return TFFT_ERR_UNSUPPORTED;
   int dev = 0, count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) return TFFT_ERR_NO_DEVICE;

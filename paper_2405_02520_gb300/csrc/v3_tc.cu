@@ -1,5 +1,6 @@
 // v3_tc.cu -- instantiations of the v3 pass kernel with the tensor-core
-// radix-16 DFT (complex64): TC = 3 three-term split TF32, TC = 1 plain TF32;
+// radix-16 DFT (complex64): TC = 3 three-term split TF32, TC = 2 three-term
+// split BF16, TC = 1 plain TF32;
 // single pass 256..4096 points, column and last passes of 256 points.
 #include "fft_v3.cuh"
 
@@ -25,14 +26,16 @@ const void* tc_kernel(int role, int nsub) {
 }  // namespace
 
 cudaError_t launch_v3_tc(int tc, int role, int nsub, const PassParams& p, int grid, size_t smem, cudaStream_t s) {
-  const void* f = tc == 3 ? tc_kernel<3>(role, nsub) : (tc == 1 ? tc_kernel<1>(role, nsub) : nullptr);
+  const void* f = tc == 3 ? tc_kernel<3>(role, nsub)
+                : tc == 2 ? tc_kernel<2>(role, nsub) : (tc == 1 ? tc_kernel<1>(role, nsub) : nullptr);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<PassParams*>(&p)};
   return cudaLaunchKernel(f, dim3(grid), dim3(256), args, smem, s);
 }
 
 cudaError_t v3_attrs_tc(int tc, int role, int nsub, size_t smem, int* bps) {
-  const void* f = tc == 3 ? tc_kernel<3>(role, nsub) : (tc == 1 ? tc_kernel<1>(role, nsub) : nullptr);
+  const void* f = tc == 3 ? tc_kernel<3>(role, nsub)
+                : tc == 2 ? tc_kernel<2>(role, nsub) : (tc == 1 ? tc_kernel<1>(role, nsub) : nullptr);
   if (!f) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
   if (e != cudaSuccess) return e;

@@ -12,10 +12,10 @@ from tests.gpu_util import oracle_fft, rel_err_rows, run_gpu, tol
 pytestmark = pytest.mark.gpu
 
 # relative-L2 bound per signal, in units of the complex64 tolerance
-FORM_BOUND = {t.TFFT_PREC_TF32X3: 8.0, t.TFFT_PREC_TF32: 2e3}
+FORM_BOUND = {t.TFFT_PREC_TF32X3: 8.0, t.TFFT_PREC_BF16X3: 64.0, t.TFFT_PREC_TF32: 2e3}
 
 
-@pytest.mark.parametrize("precision", [t.TFFT_PREC_TF32X3, t.TFFT_PREC_TF32])
+@pytest.mark.parametrize("precision", [t.TFFT_PREC_TF32X3, t.TFFT_PREC_BF16X3, t.TFFT_PREC_TF32])
 @pytest.mark.parametrize("log2n", [8, 9, 10, 11, 12, 16])
 def test_tc_forms_match_oracle(log2n, precision):
     n = 1 << log2n
@@ -66,15 +66,16 @@ def test_tc_split_keeps_small_tones(log2n):
     t.tfft_destroy(ptc)
 
 
-def test_tc_fault_detected_and_corrected():
+@pytest.mark.parametrize("precision", [t.TFFT_PREC_TF32X3, t.TFFT_PREC_BF16X3])
+def test_tc_fault_detected_and_corrected(precision):
     n, batch = 4096, 64
     x = uniform_batch(n, batch, seed=1600)
-    plan = t.tfft_plan_ex(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED, precision=t.TFFT_PREC_TF32X3)
+    plan = t.tfft_plan_ex(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED, precision=precision)
     info = t.tfft_plan_info(plan)
     fault = dict(mode=t.TFFT_FAULT_SCALE, pass_=0, stage=info["stages"][0] - 1, signal=37, line=0, index=100,
                  factor=1.5)
     y, _ = run_gpu(x, t.TFFT_C64, plan=plan, fault=fault)
-    assert rel_err_rows(y, oracle_fft(x)).max() <= FORM_BOUND[t.TFFT_PREC_TF32X3] * tol(n, t.TFFT_C64)
+    assert rel_err_rows(y, oracle_fft(x)).max() <= FORM_BOUND[precision] * tol(n, t.TFFT_C64)
     assert t.tfft_report(plan) == (1, 1)
     t.tfft_destroy(plan)
 
@@ -85,4 +86,7 @@ def test_tc_unsupported_lengths():
     assert e.value.code == -2
     with pytest.raises(t.TfftError) as e:
         t.tfft_plan_ex(1 << 10, 4, t.TFFT_C128, t.TFFT_ABFT_TWO_SIDED, precision=t.TFFT_PREC_TF32X3)
+    assert e.value.code == -2
+    with pytest.raises(t.TfftError) as e:
+        t.tfft_plan_ex(1 << 14, 4, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED, precision=t.TFFT_PREC_BF16X3)
     assert e.value.code == -2
