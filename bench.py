@@ -468,8 +468,10 @@ RAGGED_COUNT, RAGGED_LOG2 = 20000, (6, 16)
 def ragged_measure(t, torch, stream, args, peak):
     """A ragged batch: 20,000 signals, log2 length uniform over {6..16},
     U[-1,1) re/im, seed 5, packed back to back; autotuned plan, graph-replayed
-    execs, ABFT on and off.  Bytes counted as algorithmic: 16 B per element per
-    pass of each bucket's plan (the gather and scatter copies are overhead)."""
+    execs, ABFT on and off; beside it the staged form (gather, transform,
+    scatter) and one plan per length run one after another on the same
+    signals grouped by length beforehand (the grouping not timed).  Bytes
+    counted as algorithmic: 16 B per element per pass of each bucket's plan."""
     rng = np.random.default_rng(5)
     lengths = (1 << rng.integers(RAGGED_LOG2[0], RAGGED_LOG2[1] + 1, size=RAGGED_COUNT)).astype(np.int64)
     total = int(lengths.sum())
@@ -479,8 +481,9 @@ def ragged_measure(t, torch, stream, args, peak):
     xr.imag.uniform_(-1, 1, generator=g)
     yr = torch.empty_like(xr)
     out = {"signals": RAGGED_COUNT, "log2_lengths": list(RAGGED_LOG2), "elements": total, "seed": 5}
-    for mode, key in ((t.TFFT_ABFT_TWO_SIDED, "ms"), (t.TFFT_ABFT_OFF, "ms_abft_off")):
-        r = t.Ragged(lengths.tolist(), abft_mode=mode, autotune=True)
+    for mode, key, staged in ((t.TFFT_ABFT_TWO_SIDED, "ms", False), (t.TFFT_ABFT_OFF, "ms_abft_off", False),
+                              (t.TFFT_ABFT_TWO_SIDED, "ms_staged", True)):
+        r = t.Ragged(lengths.tolist(), abft_mode=mode, autotune=True, staged=staged)
         for _ in range(max(3, args.warmup)):
             r.exec(xr, yr, stream)
         torch.cuda.synchronize()
@@ -492,11 +495,12 @@ def ragged_measure(t, torch, stream, args, peak):
         e1.record(stream)
         torch.cuda.synchronize()
         out[key] = round(e0.elapsed_time(e1) / k, 4)
-        if mode == t.TFFT_ABFT_TWO_SIDED:
+        if key == "ms":
             info = dict(r.info())
             st = r.report()
             out["detected_clean"] = st["detected"]
             out["buckets"] = {str(n): p for n, p in sorted(info.items())}
+            out["in_place_buckets"] = sum(r.layout().values())
             # one fault per 1000 signals, in distinct checksum groups, one exec
             sites = ragged_fault_sites(lengths, 1, seed=5)
             for k, i in enumerate(sites):
@@ -508,6 +512,31 @@ def ragged_measure(t, torch, stream, args, peak):
             out["faults"] = {"injected": len(sites), "detected": st2["detected"] - st["detected"],
                              "corrected": st2["corrected"] + st2["recomputed"] - st["corrected"] - st["recomputed"]}
         r.destroy()
+    # one plan per length over the same signals grouped by length
+    off = np.concatenate([[0], np.cumsum(lengths)])
+    groups = []
+    for n in sorted(set(lengths.tolist()), reverse=True):
+        idx = np.nonzero(lengths == n)[0]
+        sel = torch.from_numpy((off[idx][:, None] + np.arange(n)[None, :]).reshape(-1)).to(stream.device)
+        xg = xr[sel].reshape(len(idx), n).contiguous()
+        groups.append((t.tfft_plan(n, len(idx), t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED), xg, torch.empty_like(xg)))
+        del sel
+    for _ in range(max(3, args.warmup)):
+        for pl, xg, yg in groups:
+            t.tfft_exec(pl, xg, yg, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k = max(5, args.steps)
+    e0.record(stream)
+    for _ in range(k):
+        for pl, xg, yg in groups:
+            t.tfft_exec(pl, xg, yg, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["ms_per_length_plans"] = round(e0.elapsed_time(e1) / k, 4)
+    for pl, _, _ in groups:
+        t.tfft_destroy(pl)
+    del groups
+    out["speedup_vs_per_length_plans"] = round(out["ms_per_length_plans"] / out["ms"], 3)
     fl = sum(float(flops(int(n), 1)) for n in lengths)
     passes = {int(n): p for n, p in ((int(k), v) for k, v in out["buckets"].items())}
     alg = sum(16.0 * passes[int(n)] * int(n) for n in lengths)

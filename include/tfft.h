@@ -318,17 +318,26 @@ int tfft_exec_noalloc(int64_t n, int64_t batch, const void *in, void *out, tfft_
  * equal lengths only; the two-sided checksums (Section III) run over groups
  * of G consecutive signals of equal length.
  *
- * tfft_ragged_plan: buckets the signals by length, plans one batched
- * transform per bucket and allocates two staging areas of the total size.
- * autotune = 1 times every pass count (one, two or three launches) a
- * bucket's length admits and keeps the fastest; 0 takes the planner's
- * choice.  The caller's `lengths` array is not kept.
+ * tfft_ragged_plan: buckets the signals by length and plans one batched
+ * transform per bucket.  A bucket's plan reads and writes its signals where
+ * they lie in `in` and `out` (per-signal offsets in the first pass's loads
+ * and the last pass's stores, no copies) when its passes allow it: each
+ * signal on a 16-byte boundary, and for a multi-pass plan each signal's
+ * offset a multiple of the first pass's column-box width (16 elements for
+ * complex64).  Other buckets are gathered into a staging area before their
+ * transform and scattered back after it.  `flags`:
+ *   TFFT_RAGGED_AUTOTUNE  time every pass count (one, two or three launches)
+ *                         a bucket's length admits and keep the fastest;
+ *   TFFT_RAGGED_STAGED    stage every bucket (the copy-based form, kept for
+ *                         comparison).
+ * The caller's `lengths` array is not kept.
  *
- * tfft_ragged_exec: asynchronous on `stream`; gathers each bucket into
- * staging, runs the bucket plans (each on its own stream, joined to
- * `stream`), scatters the results.  The sequence is captured into a CUDA
- * graph on the first exec with given (in, out) and replayed on the
- * next ones.  `in` and `out` must not overlap (TFFT_ERR_INPLACE).
+ * tfft_ragged_exec: asynchronous on `stream`; gathers the staged buckets,
+ * runs the bucket plans (each on its own stream, joined to `stream`,
+ * longest length first), scatters the staged results.  The sequence is
+ * captured into a CUDA graph on the first exec with given (in, out) and
+ * replayed on the next ones.  `in` and `out` must not overlap
+ * (TFFT_ERR_INPLACE).
  *
  * tfft_ragged_report: synchronises the device and sums the bucket plans'
  * counters (execs counts tfft_ragged_exec calls).
@@ -336,15 +345,18 @@ int tfft_exec_noalloc(int64_t n, int64_t batch, const void *in, void *out, tfft_
  * ignored) on caller signal `signal` for the next exec, which then runs
  * uncaptured.
  * tfft_ragged_info: number of buckets, and up to `capacity` of their
- * lengths and pass counts (longest first).
+ * lengths, pass counts and addressing (direct: 1 in place, 0 staged),
+ * longest first; any of the arrays may be NULL.
  */
 typedef struct tfft_ragged_s *tfft_ragged_t;
+enum { TFFT_RAGGED_AUTOTUNE = 1, TFFT_RAGGED_STAGED = 2 };
 int tfft_ragged_plan(tfft_ragged_t *out, const int64_t *lengths, int64_t count, int dtype, int abft_mode,
-                     int autotune);
+                     int flags);
 int tfft_ragged_exec(tfft_ragged_t r, const void *in, void *out, tfft_stream_t stream);
 int tfft_ragged_report(tfft_ragged_t r, tfft_stats *stats);
 int tfft_ragged_set_fault(tfft_ragged_t r, int64_t signal, const tfft_fault *fault);
-int tfft_ragged_info(tfft_ragged_t r, int64_t *buckets, int64_t *lengths, int *passes, int64_t capacity);
+int tfft_ragged_info(tfft_ragged_t r, int64_t *buckets, int64_t *lengths, int *passes, int *direct,
+                     int64_t capacity);
 int tfft_ragged_destroy(tfft_ragged_t r);
 
 /*

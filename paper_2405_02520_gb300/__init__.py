@@ -23,6 +23,7 @@ TFFT_ABFT_OFF, TFFT_ABFT_ONE_SIDED, TFFT_ABFT_TWO_SIDED = 0, 1, 2
 TFFT_R_SIGNED_WANG, TFFT_R_WANG = 0, 1
 TFFT_FORWARD, TFFT_INVERSE = 0, 1
 TFFT_PREC_FP32, TFFT_PREC_TF32X3, TFFT_PREC_TF32, TFFT_PREC_BF16X3 = 0, 1, 2, 3
+TFFT_RAGGED_AUTOTUNE, TFFT_RAGGED_STAGED = 1, 2
 TFFT_FAULT_NONE, TFFT_FAULT_BITFLIP, TFFT_FAULT_SCALE, TFFT_FAULT_ADD, TFFT_FAULT_ADD_PAIR = 0, 1, 2, 3, 4
 TIMING_KINDS = ("first_pass", "middle_pass", "last_pass", "single_pass", "verify", "correction")
 
@@ -109,7 +110,8 @@ def lib() -> ctypes.CDLL:
                 "tfft_ragged_exec": [P, P, P, P],
                 "tfft_ragged_report": [P, ctypes.POINTER(Stats)],
                 "tfft_ragged_set_fault": [P, I64, ctypes.POINTER(Fault)],
-                "tfft_ragged_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I), I64],
+                "tfft_ragged_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I),
+                                     ctypes.POINTER(I), I64],
                 "tfft_ragged_destroy": [P],
                 "tfft_tc_selftest": [P, P, P, I],
                 "tfft_error_string": [I],
@@ -241,10 +243,11 @@ class Ragged:
     to back (see include/tfft.h, tfft_ragged_*)."""
 
     def __init__(self, lengths, dtype: int = TFFT_C64, abft_mode: int = TFFT_ABFT_TWO_SIDED,
-                 autotune: bool = True):
+                 autotune: bool = True, staged: bool = False):
         arr = (ctypes.c_int64 * len(lengths))(*[int(v) for v in lengths])
         h = ctypes.c_void_p()
-        _check(lib().tfft_ragged_plan(ctypes.byref(h), arr, len(lengths), dtype, abft_mode, int(autotune)),
+        flags = (TFFT_RAGGED_AUTOTUNE if autotune else 0) | (TFFT_RAGGED_STAGED if staged else 0)
+        _check(lib().tfft_ragged_plan(ctypes.byref(h), arr, len(lengths), dtype, abft_mode, flags),
                "tfft_ragged_plan")
         self.handle = h.value
         self.lengths = [int(v) for v in lengths]
@@ -262,13 +265,22 @@ class Ragged:
         f = Fault(mode, pass_, stage, bit, 0, line, index, factor)
         _check(lib().tfft_ragged_set_fault(self.handle, signal, ctypes.byref(f)), "tfft_ragged_set_fault")
 
-    def info(self) -> list:
+    def _info(self):
         nb = ctypes.c_int64()
-        _check(lib().tfft_ragged_info(self.handle, ctypes.byref(nb), None, None, 0), "tfft_ragged_info")
+        _check(lib().tfft_ragged_info(self.handle, ctypes.byref(nb), None, None, None, 0), "tfft_ragged_info")
         ln = (ctypes.c_int64 * nb.value)()
         ps = (ctypes.c_int * nb.value)()
-        _check(lib().tfft_ragged_info(self.handle, ctypes.byref(nb), ln, ps, nb.value), "tfft_ragged_info")
-        return [(ln[k], ps[k]) for k in range(nb.value)]
+        dr = (ctypes.c_int * nb.value)()
+        _check(lib().tfft_ragged_info(self.handle, ctypes.byref(nb), ln, ps, dr, nb.value), "tfft_ragged_info")
+        return [(ln[k], ps[k], dr[k]) for k in range(nb.value)]
+
+    def info(self) -> list:
+        """[(length, passes)] per bucket, longest first."""
+        return [(n, p) for n, p, _ in self._info()]
+
+    def layout(self) -> dict:
+        """{length: True if the bucket is addressed in place, False if staged}."""
+        return {n: bool(d) for n, _, d in self._info()}
 
     def destroy(self) -> None:
         if self.handle:

@@ -182,10 +182,11 @@ __global__ void fix_gather_kernel(const FixParams f) {
     const int64_t gb = g * f.group, ge = min(f.batch, gb + (int64_t)f.group);
     acc_t sxr = 0, sxi = 0, syr = 0, syi = 0;
     for (int64_t b = gb; b < ge; b++) {
-      const cT xv = x[b * f.n + k];
+      const int64_t o = f.soff ? f.soff[b] : b * f.n;
+      const cT xv = x[o + k];
       sxr += (acc_t)xv.x; sxi += (acc_t)xv.y;
       if (b != bstar) {
-        const cT yv = y[b * f.n + k];
+        const cT yv = y[o + k];
         syr += (acc_t)yv.x; syi += (acc_t)yv.y;
       }
     }
@@ -206,7 +207,7 @@ __global__ void fix_apply_kernel(const FixParams f) {
     const int64_t e = idx / f.n, k = idx % f.n;
     const int64_t bstar = f.lists.fix_signal[e];
     const cT a = fc1[idx], b = ac[idx];
-    y[bstar * f.n + k] = cT{a.x - b.x, a.y - b.y};
+    y[(f.soff ? f.soff[bstar] : bstar * f.n) + k] = cT{a.x - b.x, a.y - b.y};
   }
 }
 

@@ -445,7 +445,8 @@ fft_pass_kernel(const __grid_constant__ PassParams p) {
         const int64_t b = p.lines_are_signals ? tb + c0 : tb;
         const int64_t lo = p.lines_are_signals ? 0 : lo0 + c0;
         const bool valid = b < se;
-        const int64_t base = b * p.n + hi * p.in_hi + lo * p.in_lo;
+        const int64_t sb = p.soff_in ? (valid ? p.soff_in[b] : 0) : b * p.n;
+        const int64_t base = sb + hi * p.in_hi + lo * p.in_lo;
 #pragma unroll
         for (int r = 0; r < E; r++) {
           const int i = j0 + r * (nsub / E);
@@ -565,7 +566,8 @@ fft_pass_kernel(const __grid_constant__ PassParams p) {
             for (int q = 0; q < RL; q++)
               if (p.fault.index == j + q * nb) w[q] = faulted(w[q], p.fault);
           }
-          const int64_t obase = b * p.n + hi * p.out_hi + lo * p.out_lo;
+          const int64_t osb = p.soff_out ? (valid ? p.soff_out[b] : 0) : b * p.n;
+          const int64_t obase = osb + hi * p.out_hi + lo * p.out_lo;
           if (valid) {
 #pragma unroll
             for (int q = 0; q < RL; q++) gout[obase + (int64_t)(j + q * nb) * p.out_es] = out_xform(w[q], p);

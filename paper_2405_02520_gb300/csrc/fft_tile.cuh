@@ -166,14 +166,37 @@ __device__ __forceinline__ void issue_load(const PassParams& p, const Cursor& cu
     const long long rows = min((long long)p.C, cur.se - cur.tb);
     const uint32_t bytes = (uint32_t)(rows * p.nsub * (long long)sizeof(cT));
     mbar_expect_tx(bar, bytes);
-    tma_load_bulk(dst, reinterpret_cast<const cT*>(p.in) + cur.tb * p.n, bytes, bar);
+    if (p.soff_in) {          // one copy per signal (lines are whole signals here)
+      const uint32_t sb = (uint32_t)(p.nsub * (long long)sizeof(cT));
+      for (long long r = 0; r < rows; r++)
+        tma_load_bulk(dst + r * p.nsub, reinterpret_cast<const cT*>(p.in) + p.soff_in[cur.tb + r], sb, bar);
+    } else {
+      tma_load_bulk(dst, reinterpret_cast<const cT*>(p.in) + cur.tb * p.n, bytes, bar);
+    }
     return;
   }
   const long long hi = cur.hi(p), lo0 = cur.lo0(p), b = cur.tb;
+  mbar_expect_tx(bar, m.bytes);
+  if (p.soff_in) {
+    // first pass, 2-D map over the whole packed buffer as rows of M = n / nsub
+    // columns: signal b starts at row off / M, column off mod M; a box of
+    // columns that runs past M continues on the next row (the plan checked
+    // that every offset is a multiple of the box width, so no box straddles)
+    const long long M = p.n / p.nsub, off = p.soff_in[b];
+    const long long q = off / M, r = off - q * M;
+    const int u = m.ax;
+    for (int kx = 0; kx < m.nbx; kx++) {
+      long long col = r + lo0 + (long long)kx * (m.bx_step / u), row = q;
+      if (col >= M) { col -= M; row += 1; }
+      for (int k = 0; k < m.nbox; k++)
+        tma_load_2d(dst + kx * m.bx_elems + k * m.box_elems, &p.tmap_in, (int)(u * col),
+                    (int)(row + (long long)k * m.box_rows), bar);
+    }
+    return;
+  }
   const int x = (int)(m.ax * lo0);
   const int y = (int)(m.ay * hi + m.by * b + m.cy * lo0);
   const int z = (int)(m.az * hi + m.bz * b + m.cz * lo0);
-  mbar_expect_tx(bar, m.bytes);
   for (int kx = 0; kx < m.nbx; kx++)
     for (int k = 0; k < m.nbox; k++) {
       cT* d = dst + kx * m.bx_elems + k * m.box_elems;
@@ -188,8 +211,14 @@ __device__ __forceinline__ void issue_store(const PassParams& p, long long tb, l
   const TileMap& m = p.map_out;
   if (m.kind == 1) {
     const long long rows = min((long long)p.C, se - tb);
-    const uint32_t bytes = (uint32_t)(rows * p.nsub * (long long)sizeof(cT));
-    tma_store_bulk(reinterpret_cast<cT*>(p.out) + tb * p.n, src, bytes);
+    if (p.soff_out) {
+      const uint32_t sb = (uint32_t)(p.nsub * (long long)sizeof(cT));
+      for (long long r = 0; r < rows; r++)
+        tma_store_bulk(reinterpret_cast<cT*>(p.out) + p.soff_out[tb + r], src + r * p.nsub, sb);
+    } else {
+      const uint32_t bytes = (uint32_t)(rows * p.nsub * (long long)sizeof(cT));
+      tma_store_bulk(reinterpret_cast<cT*>(p.out) + tb * p.n, src, bytes);
+    }
     return;
   }
   const int x = (int)(m.ax * lo0);

@@ -301,7 +301,7 @@ __device__ __forceinline__ void copy_out(const PassParams& p, long long tb, long
   if constexpr (ROLE == V3_SINGLE) {
     const long long rows = min((long long)G::C, se - tb);
     const int chunks = (int)(rows * (G::NSUBV * G::ES / 16));
-    unsigned char* dst = out + tb * p.n * G::ES;
+    unsigned char* dst = out + tb * p.n * G::ES;    // never called with signal offsets
     int i = lane;
     for (; i + 96 < chunks; i += 128) {
       const float4 a = *reinterpret_cast<const float4*>(tile + 16 * i);
@@ -323,7 +323,8 @@ __device__ __forceinline__ void copy_out(const PassParams& p, long long tb, long
     const long long row_stride = p.out_es * G::ES;
 #pragma unroll 1
     for (int gx = 0; gx < G::C / G::CS; gx++) {
-      unsigned char* dst = out + (tb * p.n + hi * p.out_hi + (lo0 + gx * G::CS) * p.out_lo) * G::ES +
+      const long long sbase = p.soff_out ? p.soff_out[tb] : tb * p.n;
+      unsigned char* dst = out + (sbase + hi * p.out_hi + (lo0 + gx * G::CS) * p.out_lo) * G::ES +
                            rr * row_stride + 16 * j;
       const uint32_t o0 = (uint32_t)((gx * G::NSUBV + rr) * G::ROWB + 16 * j);
 #pragma unroll 4

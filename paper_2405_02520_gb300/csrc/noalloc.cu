@@ -129,6 +129,7 @@ extern "C" int tfft_exec_noalloc(int64_t n, int64_t batch, const void* in, void*
     int st = 0; for (int64_t v = 1; v < nsub; v *= E) st++;
     a.nstages = st;
     a.n = n; a.batch = batch; a.LO = LO; a.HI = 1; a.pass_index = pass;
+    a.out_scale = 1.0;            // forward, unnormalised
     if (pass == 0) {
       a.in_es = N2; a.in_lo = 1; a.out_es = N2; a.out_lo = 1;
       a.in_map = a.mid_map = a.out_map = MAP_COL;

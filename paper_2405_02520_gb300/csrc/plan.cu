@@ -155,6 +155,7 @@ struct tfft_plan_s {
   void* stage_in = nullptr; void* stage_out = nullptr;
   int* err_flag = nullptr;
   const void* enc_ptr[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+  const long long* soff = nullptr;   // signal offsets of the exec's input and output (ragged)
   CUtensorMap enc_map[3][2];
 
   FaultSite pending{};                 // first armed fault site (every kernel)
@@ -877,12 +878,16 @@ int kind_of(const tfft_plan_s* p, int i) {
 // Run the passes from `in` to `out` (through tmp when there are several).
 int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool main_exec,
                const long long* list, int list_identity, int list_cap, int64_t list_block,
-               int64_t batch, int kind_override) {
+               int64_t batch, int kind_override, bool user_io = true) {
   for (int i = 0; i < p->passes; i++) {
     PassParams a = base_params(p, i);
     a.batch = batch;
     a.in = (i == 0) ? in : p->tmp;
     a.out = (i == p->passes - 1) ? out : p->tmp;
+    if (user_io) {
+      a.soff_in = i == 0 ? p->soff : nullptr;
+      a.soff_out = i == p->passes - 1 ? p->soff : nullptr;
+    }
     if (main_exec && p->pp[i].v3) {
       const PassPlan& q = p->pp[i];
       a.C = q.vC; a.nthreads = 256; a.line_blocks = q.vLB;
@@ -937,11 +942,11 @@ int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
     if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
     FixParams f{};
     f.n = p->n; f.batch = p->batch; f.group = p->vG; f.dtype = p->dtype;
-    f.in = in; f.out = out; f.ws_c1 = p->ws_c1; f.ws_acc = p->ws_acc; f.lists = p->lists;
+    f.in = in; f.out = out; f.soff = p->soff; f.ws_c1 = p->ws_c1; f.ws_acc = p->ws_acc; f.lists = p->lists;
     if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_gather(f, s); }))) return rc;
     // W X e_1 of every queued group, in place in ws_c1
     if ((rc = run_passes(p, p->ws_c1, p->ws_c1, s, false, p->lists.fix, 1, p->cap_fix, 1,
-                         p->cap_fix, 5)))
+                         p->cap_fix, 5, false)))
       return rc;
     if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_apply(f, s); }))) return rc;
     // groups that could not be located: recompute from the input
@@ -954,6 +959,43 @@ int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
 bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
 }  // namespace
+
+namespace tfft {
+
+int plan_set_signal_offsets(tfft_plan_t p, const long long* d_off, const int64_t* h_off, int64_t total) {
+  if (!p || !d_off || !h_off || total < p->n) return TFFT_ERR_INVALID_ARG;
+  const int64_t es = (int64_t)p->esize, u = es / 8;
+  for (int64_t b = 0; b < p->batch; b++)
+    if (h_off[b] < 0 || h_off[b] > total - p->n) return TFFT_ERR_INVALID_ARG;
+  // every signal on a 16-byte boundary: the bulk copies and the 16-byte
+  // stores of the last pass need it
+  for (int64_t b = 0; b < p->batch; b++)
+    if ((h_off[b] * es) % 16) return TFFT_ERR_UNSUPPORTED;
+  PassPlan& f = p->pp[0];
+  PassPlan& l = p->pp[p->passes - 1];
+  MapGeom g = f.gin;
+  if (f.tma && f.map_in.kind >= 2) {
+    // the first pass's column boxes: 2-D map over the packed buffer as rows of
+    // M columns; an offset that is a multiple of the box width keeps each box
+    // inside one row
+    if (f.map_in.kind != 2 || g.rank != 2) return TFFT_ERR_UNSUPPORTED;
+    const int64_t M = p->n / f.nsub, width = (int64_t)g.box[0] / u;
+    if (width < 1 || M % width) return TFFT_ERR_UNSUPPORTED;
+    for (int64_t b = 0; b < p->batch; b++)
+      if (h_off[b] % width) return TFFT_ERR_UNSUPPORTED;
+    g.dims[1] = (uint64_t)((total + M - 1) / M);
+    if (!geom_ok(g) || g.dims[1] >= (uint64_t(1) << 31)) return TFFT_ERR_UNSUPPORTED;   // signed coordinates
+  }
+  // the last pass writes whole signals (bulk stores) or copies its boxes out
+  // with plain stores; other store forms keep the contiguous layout
+  if (l.tma && !(l.v3 && l.role == 2) && l.map_out.kind != 1) return TFFT_ERR_UNSUPPORTED;
+  f.gin = g;
+  p->enc_ptr[0][0] = nullptr;
+  p->soff = d_off;
+  return TFFT_SUCCESS;
+}
+
+}  // namespace tfft
 
 // =================================================================== C ABI
 extern "C" {

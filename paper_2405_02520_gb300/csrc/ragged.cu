@@ -3,16 +3,19 @@
 // The signals of a ragged batch are packed back to back in the caller's
 // order.  The plan sorts them into buckets of equal length; each bucket is an
 // ordinary batched plan (with the two-sided checksums over groups of G
-// consecutive signals of the bucket).  An exec
+// consecutive signals of the bucket).  A bucket is either
 //
-//   1. gathers every bucket into a contiguous staging area ([count][n] per
-//      bucket) with one copy kernel over 16-byte chunks;
-//   2. runs the bucket plans, each on its own stream so that the short
-//      transforms of small buckets overlap;
-//   3. scatters the results back to the caller's layout.
+//   * direct: its plan carries the caller offsets of its signals, so the
+//     first pass loads each signal where it lies and the last pass stores it
+//     back there (no copies), or
+//   * staged: an exec gathers it into a contiguous staging area with one copy
+//     kernel over 16-byte chunks and scatters the results back (the fallback
+//     for offsets a pass cannot address, and the comparison form).
 //
-// The whole sequence is captured into a CUDA graph on the first exec with a
-// given (in, out) and replayed afterwards (no per-kernel launch cost;
+// An exec runs the bucket plans, longest length first, each on its own
+// stream so that the short transforms of small buckets overlap the long
+// ones.  The whole sequence is captured into a CUDA graph on the first exec
+// with a given (in, out) and replayed afterwards (no per-kernel launch cost;
 // the small buckets are launch-bound).  An exec with a test fault armed runs
 // uncaptured.  At plan time an optional autotuner times the pass counts a
 // bucket's length admits (one, two or three launches) and keeps the fastest.
@@ -52,7 +55,9 @@ __global__ void ragged_copy_kernel(const Segment* seg, long long nseg, const uns
 struct Bucket {
   int64_t n = 0;
   std::vector<int64_t> sig;   // caller indices of the bucket's signals, in order
-  int64_t base = 0;           // element offset of the bucket in the staging areas
+  int64_t first = 0;          // index of the bucket's first entry in the offset table
+  bool direct = false;        // addressed in place through the offset table
+  int64_t base = 0;           // staged: element offset of the bucket in the staging areas
   tfft_plan_t plan = nullptr;
   int passes = 0;
   cudaStream_t stream = nullptr;
@@ -69,6 +74,8 @@ struct tfft_ragged_s {
   std::vector<int64_t> local;        // index of every signal inside its bucket
   std::vector<int> bucket_of;        // bucket of every signal
   std::vector<Bucket> buckets;
+  long long* d_off = nullptr;        // caller offsets, bucket by bucket
+  int64_t staged_total = 0;          // elements of the staged buckets
   void* stage_in = nullptr;
   void* stage_out = nullptr;
   Segment* d_gather = nullptr;
@@ -98,7 +105,7 @@ void free_ragged(tfft_ragged_s* r) {
   }
   if (r->fork) cudaEventDestroy(r->fork);
   if (r->cap) cudaStreamDestroy(r->cap);
-  for (void* p : {r->stage_in, r->stage_out, (void*)r->d_gather, (void*)r->d_scatter})
+  for (void* p : {r->stage_in, r->stage_out, (void*)r->d_gather, (void*)r->d_scatter, (void*)r->d_off})
     if (p) cudaFree(p);
   delete r;
 }
@@ -131,7 +138,8 @@ int launch_copy(const tfft_ragged_s* r, const Segment* seg, const void* src, voi
   return e == cudaSuccess ? TFFT_SUCCESS : record_cuda_error(e);
 }
 
-// gather, bucket plans on their streams, scatter -- all on or joined to `s`
+// gather (staged buckets), bucket plans on their streams, scatter -- all on
+// or joined to `s`
 int enqueue(tfft_ragged_s* r, const void* in, void* out, cudaStream_t s) {
   int rc;
   if ((rc = launch_copy(r, r->d_gather, in, r->stage_in, s))) return rc;
@@ -140,25 +148,58 @@ int enqueue(tfft_ragged_s* r, const void* in, void* out, cudaStream_t s) {
   for (auto& b : r->buckets) {
     if ((e = cudaStreamWaitEvent(b.stream, r->fork, 0)) != cudaSuccess) return record_cuda_error(e);
     const size_t boff = (size_t)b.base * r->esize;
-    if ((rc = tfft_exec(b.plan, static_cast<const unsigned char*>(r->stage_in) + boff,
-                        static_cast<unsigned char*>(r->stage_out) + boff, (tfft_stream_t)b.stream)))
-      return rc;
+    const void* bin = b.direct ? in : static_cast<const unsigned char*>(r->stage_in) + boff;
+    void* bout = b.direct ? out : static_cast<unsigned char*>(r->stage_out) + boff;
+    if ((rc = tfft_exec(b.plan, bin, bout, (tfft_stream_t)b.stream))) return rc;
     if ((e = cudaEventRecord(b.done, b.stream)) != cudaSuccess) return record_cuda_error(e);
     if ((e = cudaStreamWaitEvent(s, b.done, 0)) != cudaSuccess) return record_cuda_error(e);
   }
   return launch_copy(r, r->d_scatter, r->stage_out, out, s);
 }
 
+// A scratch pair of the packed size for the autotuner's timings of direct
+// buckets (zeroed, freed after planning).
+struct Scratch {
+  void* in = nullptr;
+  void* out = nullptr;
+  ~Scratch() {
+    if (in) cudaFree(in);
+    if (out) cudaFree(out);
+  }
+};
+
+// Plans bucket `b` (force_passes = 0: the planner's choice); a direct bucket
+// gets the offset table, and a plan that cannot take it fails with
+// TFFT_ERR_UNSUPPORTED.
+int plan_bucket(tfft_ragged_s* r, const Bucket& b, const std::vector<long long>& hoff, int force_passes,
+                bool direct, tfft_plan_t* out) {
+  tfft_plan_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.n = b.n; o.batch = (int64_t)b.sig.size(); o.dtype = r->dtype; o.abft_mode = r->abft;
+  o.force_passes = force_passes;
+  int rc = tfft_plan_ex(out, &o);
+  if (rc) return rc;
+  if (direct) {
+    static_assert(sizeof(long long) == sizeof(int64_t), "offset table entries are 64-bit");
+    rc = tfft::plan_set_signal_offsets(*out, r->d_off + b.first,
+                                       reinterpret_cast<const int64_t*>(hoff.data()) + b.first, r->total);
+    if (rc) { tfft_destroy(*out); *out = nullptr; }
+  }
+  return rc;
+}
+
 }  // namespace
 
 extern "C" int tfft_ragged_plan(tfft_ragged_t* out, const int64_t* lengths, int64_t count, int dtype,
-                                int abft_mode, int autotune) {
-  if (!out || !lengths || count < 1) return TFFT_ERR_INVALID_ARG;
+                                int abft_mode, int flags) {
+  if (!out || !lengths || count < 1 || (flags & ~(TFFT_RAGGED_AUTOTUNE | TFFT_RAGGED_STAGED)))
+    return TFFT_ERR_INVALID_ARG;
   *out = nullptr;
   if (dtype != TFFT_C64 && dtype != TFFT_C128) return TFFT_ERR_UNSUPPORTED;
   const int64_t nmin = dtype == TFFT_C64 ? 2 : 1;   // every signal starts on a 16-byte boundary
   for (int64_t i = 0; i < count; i++)
     if (!pow2(lengths[i]) || lengths[i] < nmin || lengths[i] > (int64_t(1) << 26)) return TFFT_ERR_INVALID_ARG;
+  const bool autotune = flags & TFFT_RAGGED_AUTOTUNE, all_staged = flags & TFFT_RAGGED_STAGED;
   tfft_ragged_s* r = new (std::nothrow) tfft_ragged_s();
   if (!r) return TFFT_ERR_ALLOC;
   r->dtype = dtype;
@@ -183,14 +224,16 @@ extern "C" int tfft_ragged_plan(tfft_ragged_t* out, const int64_t* lengths, int6
     r->local[i] = (int64_t)b.sig.size();
     b.sig.push_back(i);
   }
-  // staging: buckets back to back, longest first (the big transforms start first)
+  // longest first: the big transforms start first
   std::sort(r->buckets.begin(), r->buckets.end(), [](const Bucket& a, const Bucket& b) { return a.n > b.n; });
   for (size_t k = 0; k < r->buckets.size(); k++)
     for (int64_t s : r->buckets[k].sig) r->bucket_of[s] = (int)k;
-  int64_t base = 0;
+  // offset table: the caller offsets of every bucket's signals, bucket by bucket
+  std::vector<long long> hoff;
+  hoff.reserve(count);
   for (auto& b : r->buckets) {
-    b.base = base;
-    base += (int64_t)b.sig.size() * b.n;
+    b.first = (int64_t)hoff.size();
+    for (int64_t s : b.sig) hoff.push_back((long long)r->off[s]);
   }
   int dev = 0;
   cudaDeviceProp prop;
@@ -199,39 +242,15 @@ extern "C" int tfft_ragged_plan(tfft_ragged_t* out, const int64_t* lengths, int6
     return TFFT_ERR_NO_DEVICE;
   }
   r->sms = prop.multiProcessorCount;
-  const size_t bytes = (size_t)r->total * r->esize;
-  if (cudaMalloc(&r->stage_in, bytes) != cudaSuccess || cudaMalloc(&r->stage_out, bytes) != cudaSuccess ||
-      cudaMemset(r->stage_in, 0, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    free_ragged(r);
-    return TFFT_ERR_ALLOC;
-  }
-  // copy segments of at most 64 KiB: caller layout <-> staging
-  std::vector<Segment> gat, sca;
-  const long long kSeg = 64 * 1024;
-  for (const auto& b : r->buckets)
-    for (size_t j = 0; j < b.sig.size(); j++) {
-      const long long src = (long long)r->off[b.sig[j]] * (long long)r->esize;
-      const long long dst = (long long)(b.base + (int64_t)j * b.n) * (long long)r->esize;
-      const long long len = (long long)b.n * (long long)r->esize;
-      for (long long o = 0; o < len; o += kSeg) {
-        const long long L = std::min(kSeg, len - o);
-        gat.push_back(Segment{src + o, dst + o, L});
-        sca.push_back(Segment{dst + o, src + o, L});
-      }
-    }
-  r->nseg = (long long)gat.size();
-  if (cudaMalloc(&r->d_gather, gat.size() * sizeof(Segment)) != cudaSuccess ||
-      cudaMalloc(&r->d_scatter, sca.size() * sizeof(Segment)) != cudaSuccess ||
-      cudaMemcpy(r->d_gather, gat.data(), gat.size() * sizeof(Segment), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(r->d_scatter, sca.data(), sca.size() * sizeof(Segment), cudaMemcpyHostToDevice) != cudaSuccess ||
+  if (cudaMalloc(&r->d_off, hoff.size() * sizeof(long long)) != cudaSuccess ||
+      cudaMemcpy(r->d_off, hoff.data(), hoff.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     free_ragged(r);
     return TFFT_ERR_ALLOC;
   }
-  // bucket plans; the autotuner times every pass count the length admits
+  // bucket plans: direct where the plan takes the offsets, else staged
   for (auto& b : r->buckets) {
     if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess) {
@@ -239,25 +258,81 @@ extern "C" int tfft_ragged_plan(tfft_ragged_t* out, const int64_t* lengths, int6
       free_ragged(r);
       return TFFT_ERR_CUDA;
     }
-    tfft_plan_opts o;
-    std::memset(&o, 0, sizeof(o));
-    o.n = b.n; o.batch = (int64_t)b.sig.size(); o.dtype = dtype; o.abft_mode = abft_mode;
-    int rc = tfft_plan_ex(&b.plan, &o);
+    int rc = TFFT_ERR_UNSUPPORTED;
+    if (!all_staged) {
+      rc = plan_bucket(r, b, hoff, 0, true, &b.plan);
+      b.direct = rc == TFFT_SUCCESS;
+    }
+    if (rc == TFFT_ERR_UNSUPPORTED) rc = plan_bucket(r, b, hoff, 0, false, &b.plan);
     if (rc) { free_ragged(r); return rc; }
     tfft_info info;
     tfft_plan_info(b.plan, &info);
     b.passes = info.passes;
-    if (autotune) {
+  }
+  // staging areas and copy segments (of at most 64 KiB) for the staged buckets
+  for (auto& b : r->buckets)
+    if (!b.direct) {
+      b.base = r->staged_total;
+      r->staged_total += (int64_t)b.sig.size() * b.n;
+    }
+  std::vector<Segment> gat, sca;
+  if (r->staged_total) {
+    const size_t bytes = (size_t)r->staged_total * r->esize;
+    if (cudaMalloc(&r->stage_in, bytes) != cudaSuccess || cudaMalloc(&r->stage_out, bytes) != cudaSuccess ||
+        cudaMemset(r->stage_in, 0, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      free_ragged(r);
+      return TFFT_ERR_ALLOC;
+    }
+    const long long kSeg = 64 * 1024;
+    for (const auto& b : r->buckets) {
+      if (b.direct) continue;
+      for (size_t j = 0; j < b.sig.size(); j++) {
+        const long long src = (long long)r->off[b.sig[j]] * (long long)r->esize;
+        const long long dst = (long long)(b.base + (int64_t)j * b.n) * (long long)r->esize;
+        const long long len = (long long)b.n * (long long)r->esize;
+        for (long long o = 0; o < len; o += kSeg) {
+          const long long L = std::min(kSeg, len - o);
+          gat.push_back(Segment{src + o, dst + o, L});
+          sca.push_back(Segment{dst + o, src + o, L});
+        }
+      }
+    }
+    r->nseg = (long long)gat.size();
+    if (cudaMalloc(&r->d_gather, gat.size() * sizeof(Segment)) != cudaSuccess ||
+        cudaMalloc(&r->d_scatter, sca.size() * sizeof(Segment)) != cudaSuccess ||
+        cudaMemcpy(r->d_gather, gat.data(), gat.size() * sizeof(Segment), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(r->d_scatter, sca.data(), sca.size() * sizeof(Segment), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      free_ragged(r);
+      return TFFT_ERR_ALLOC;
+    }
+  }
+  // the autotuner times every pass count the length admits (a direct bucket
+  // keeps only plans that take the offsets) on zeroed buffers of the packed
+  // size
+  if (autotune) {
+    Scratch sc;
+    const bool any_direct = std::any_of(r->buckets.begin(), r->buckets.end(), [](const Bucket& b) { return b.direct; });
+    if (any_direct) {
+      const size_t bytes = (size_t)r->total * r->esize;
+      if (cudaMalloc(&sc.in, bytes) != cudaSuccess || cudaMalloc(&sc.out, bytes) != cudaSuccess ||
+          cudaMemset(sc.in, 0, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        free_ragged(r);
+        return TFFT_ERR_ALLOC;
+      }
+    }
+    for (auto& b : r->buckets) {
       const size_t boff = (size_t)b.base * r->esize;
-      const void* in = static_cast<unsigned char*>(r->stage_in) + boff;
-      void* o2 = static_cast<unsigned char*>(r->stage_out) + boff;
+      const void* in = b.direct ? sc.in : static_cast<unsigned char*>(r->stage_in) + boff;
+      void* o2 = b.direct ? sc.out : static_cast<unsigned char*>(r->stage_out) + boff;
       float best = time_plan(b.plan, in, o2, b.stream);
       for (int passes = 1; passes <= 3; passes++) {
         if (passes == b.passes) continue;
-        tfft_plan_opts f = o;
-        f.force_passes = passes;
         tfft_plan_t alt = nullptr;
-        if (tfft_plan_ex(&alt, &f) != TFFT_SUCCESS) { cudaGetLastError(); continue; }
+        if (plan_bucket(r, b, hoff, passes, b.direct, &alt) != TFFT_SUCCESS) { cudaGetLastError(); continue; }
         const float ms = time_plan(alt, in, o2, b.stream);
         if (ms < best) {
           tfft_destroy(b.plan);
@@ -270,6 +345,7 @@ extern "C" int tfft_ragged_plan(tfft_ragged_t* out, const int64_t* lengths, int6
       }
       tfft_reset_counters(b.plan);
     }
+    if (cudaDeviceSynchronize() != cudaSuccess) { free_ragged(r); return TFFT_ERR_CUDA; }
   }
   if (cudaDeviceSynchronize() != cudaSuccess) { free_ragged(r); return TFFT_ERR_CUDA; }
   *out = r;
@@ -342,13 +418,14 @@ extern "C" int tfft_ragged_set_fault(tfft_ragged_t r, int64_t signal, const tfft
   return rc;
 }
 
-extern "C" int tfft_ragged_info(tfft_ragged_t r, int64_t* buckets, int64_t* lengths, int* passes,
+extern "C" int tfft_ragged_info(tfft_ragged_t r, int64_t* buckets, int64_t* lengths, int* passes, int* direct,
                                 int64_t capacity) {
   if (!r || !buckets) return TFFT_ERR_INVALID_ARG;
   *buckets = (int64_t)r->buckets.size();
   for (int64_t k = 0; k < std::min<int64_t>(capacity, *buckets); k++) {
     if (lengths) lengths[k] = r->buckets[k].n;
     if (passes) passes[k] = r->buckets[k].passes;
+    if (direct) direct[k] = r->buckets[k].direct ? 1 : 0;
   }
   return TFFT_SUCCESS;
 }

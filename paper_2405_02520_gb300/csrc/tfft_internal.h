@@ -6,6 +6,8 @@
 #include <cuda.h>            // CUtensorMap (the tensor-map type only; no driver call is linked)
 #include <cuda_runtime.h>
 
+struct tfft_plan_s;   // the plan (plan.cu); tfft_plan_t in include/tfft.h
+
 namespace tfft {
 
 // How the butterflies of one radix stage are dealt to the threads of a tile.
@@ -126,6 +128,11 @@ struct PassParams {
   int64_t out_es, out_lo, out_hi;
   const void* in;
   void* out;
+  // signal b of `in` (`out`) starts at element soff_in[b] (soff_out[b]) instead
+  // of b n: a ragged batch read and written in the caller's packing.  Set on
+  // the first pass's input and the last pass's output only.
+  const long long* soff_in;
+  const long long* soff_out;
 
   // ---- twiddles ----
   const void* tw_sub;     // omega_{tw_sub_n}^m, m < tw_sub_n (stage twiddles)
@@ -201,6 +208,13 @@ cudaError_t launch_v3_tc(int tc, int role, int nsub, const PassParams& p, int gr
 cudaError_t v3_attrs_tc(int tc, int role, int nsub, size_t smem, int* blocks_per_sm);
 int v3_tc_bytes(int tc);
 
+// Signal offsets for a plan's exec (ragged batches in the caller's packing):
+// signal b of the exec's input and output starts at element off[b] (d_off on
+// the device, h_off its host copy, `total` elements in each buffer).  Returns
+// TFFT_ERR_UNSUPPORTED when a pass cannot address the signals that way (then
+// the caller stages the signals contiguously instead).
+int plan_set_signal_offsets(::tfft_plan_s* p, const long long* d_off, const int64_t* h_off, int64_t total);
+
 // Keeps `e` as the value tfft_last_cuda_error() reports; returns TFFT_ERR_CUDA.
 int record_cuda_error(cudaError_t e);
 
@@ -228,6 +242,7 @@ struct FixParams {
   int dtype;           // 0 c64, 1 c128
   const void* in;      // user input (read)
   void* out;           // user output (patched)
+  const long long* soff;   // signal offsets in `in` and `out` (nullptr: b n)
   void* ws_c1;         // cap_fix x n : gathered sum_b x_b, transformed in place
   void* ws_acc;        // cap_fix x n : sum_{b != b*} y'_b
   Lists lists;

@@ -33,12 +33,15 @@ def _check(lengths, x, y):
     return worst
 
 
-@pytest.mark.parametrize("autotune", [False, True])
-def test_ragged_matches_oracle_and_replays(autotune):
+@pytest.mark.parametrize("autotune,staged", [(False, False), (True, False), (False, True)])
+def test_ragged_matches_oracle_and_replays(autotune, staged):
     import torch
     lengths, x = _ragged_input(400, seed=5)
-    r = t.Ragged(lengths.tolist(), autotune=autotune)
+    r = t.Ragged(lengths.tolist(), autotune=autotune, staged=staged)
     assert sorted(n for n, _ in r.info()) == sorted(set(lengths.tolist()))
+    # lengths 2^6..2^16: every offset is a multiple of 64 elements, so every
+    # bucket is addressed in place unless staging is forced
+    assert all(d != staged for d in r.layout().values()), r.layout()
     xt = torch.from_numpy(x).cuda()
     yt = torch.empty_like(xt)
     r.exec(xt, yt)                       # captured
@@ -127,4 +130,61 @@ def test_ragged_one_fault_per_thousand_signals():
     _check(lengths, x, yt.cpu().numpy())
     st = r.report()
     assert st["detected"] == 4 and st["corrected"] + st["recomputed"] == 4, st
+    r.destroy()
+
+
+def test_ragged_mixed_direct_and_staged_buckets():
+    """Lengths 2, 8, 256, 8192 and 65536: the short signals leave the
+    multi-pass buckets' offsets off the 16-element box grid, so those buckets
+    are staged while the others are addressed in place; faults in a staged and
+    in a direct bucket are both corrected."""
+    import torch
+    rng = np.random.default_rng(77)
+    lengths = rng.choice(np.array([2, 8, 256, 8192, 65536], dtype=np.int64), size=90)
+    lengths[:2] = [2, 8192]             # make sure an 8192-point offset is misaligned
+    total = int(lengths.sum())
+    x = np.empty(total, dtype=np.complex64)
+    x.real = rng.uniform(-1, 1, total).astype(np.float32)
+    x.imag = rng.uniform(-1, 1, total).astype(np.float32)
+    r = t.Ragged(lengths.tolist(), autotune=False)
+    lay = r.layout()
+    assert lay[8192] is False and lay[256] is True and lay[2] is True, lay
+    passes = dict(r.info())
+    xt = torch.from_numpy(x).cuda()
+    yt = torch.empty_like(xt)
+    r.exec(xt, yt)
+    torch.cuda.synchronize()
+    _check(lengths, x, yt.cpu().numpy())
+    s8k = int(np.nonzero(lengths == 8192)[0][1])
+    s256 = int(np.nonzero(lengths == 256)[0][2])
+    r.set_fault(s8k, mode=t.TFFT_FAULT_SCALE, pass_=passes[8192] - 1, stage=0, line=0, index=3, factor=2.0)
+    r.set_fault(s256, mode=t.TFFT_FAULT_SCALE, pass_=0, stage=0, line=0, index=5, factor=2.0)
+    r.exec(xt, yt)
+    torch.cuda.synchronize()
+    _check(lengths, x, yt.cpu().numpy())
+    st = r.report()
+    assert st["detected"] == 2 and st["corrected"] + st["recomputed"] == 2, st
+    r.destroy()
+
+
+def test_ragged_one_sided_recompute_in_place():
+    """One-sided checks on a ragged batch addressed in place: a detected
+    signal is recomputed from the caller's input and written back at its
+    caller offset."""
+    import torch
+    lengths, x = _ragged_input(120, seed=909, lo=8, hi=14)
+    r = t.Ragged(lengths.tolist(), abft_mode=t.TFFT_ABFT_ONE_SIDED, autotune=False)
+    assert all(r.layout().values())
+    passes = dict(r.info())
+    xt = torch.from_numpy(x).cuda()
+    yt = torch.empty_like(xt)
+    big = int(np.nonzero(lengths == 1 << 14)[0][1])
+    small = int(np.nonzero(lengths == 512)[0][0])
+    r.set_fault(big, mode=t.TFFT_FAULT_SCALE, pass_=passes[1 << 14] - 1, stage=0, line=2, index=7, factor=2.0)
+    r.set_fault(small, mode=t.TFFT_FAULT_SCALE, pass_=0, stage=1, line=0, index=11, factor=2.0)
+    r.exec(xt, yt)
+    torch.cuda.synchronize()
+    _check(lengths, x, yt.cpu().numpy())
+    st = r.report()
+    assert st["detected"] == 2 and st["corrected"] + st["recomputed"] == 2, st
     r.destroy()
