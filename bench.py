@@ -345,6 +345,8 @@ def run_ours(args):
     for _ in range(args.warmup):
         step(off)
     torch.cuda.synchronize()
+    for lg in sweep:                      # the same per-launch instrumentation as the ABFT-on steps
+        t.tfft_set_timing(off[lg], True)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -354,6 +356,7 @@ def run_ours(args):
     off_ms = reduce_scalar(e0.elapsed_time(e1), "max", dev)
     off_per_n = per_n_total(per_off)
     for lg in sweep:
+        t.tfft_set_timing(off[lg], False)
         t.tfft_destroy(off[lg])
 
     ragged = None if args.no_ragged else ragged_measure(t, torch, stream, args, peak)

@@ -30,119 +30,175 @@ namespace tfft {
 // of the group decides.
 // Blocks stride over the groups; the largest clean residual ratio is kept per
 // thread and folded into the counter with one atomic per block.
+// The decision for group g from its combined sums (lane 0 of the group):
+// detection against the threshold, location by the quotient, the work lists,
+// the counters and the fault log.  Clean groups update the calibration
+// maximum `clean_max` (the bits of a nonnegative double).
+struct GroupSums {
+  double s1r, s1i, s2r, s2i, en, t1r, t1i, t2r, t2i;
+  long long nfmin, nfmax;
+};
+
+__device__ void decide_group(const VerifyParams& v, int64_t g, const GroupSums& c,
+                             unsigned long long& clean_max) {
+  const int64_t gb = g * v.group;
+  const int64_t gsize = min((int64_t)v.group, v.batch - gb);
+  const double d1r = c.t1r - c.s1r, d1i = c.t1i - c.s1i;
+  const double d2r = c.t2r - c.s2r, d2i = c.t2i - c.s2i;
+  const double res = sqrt(d1r * d1r + d1i * d1i);
+  const double tau = v.kappa_u_log2n_sqrtn * sqrt(c.en);
+  const bool finite = isfinite(res) && isfinite(d2r) && isfinite(d2i);
+  const bool nonfinite = !finite || c.nfmax >= 0;
+  if (!(nonfinite || res > tau)) {
+    // calibration record: the largest clean residual relative to the threshold
+    const double ratio = tau > 0 ? res / tau : 0.0;
+    clean_max = max(clean_max, (unsigned long long)__double_as_longlong(ratio));
+    return;
+  }
+
+  atomicAdd(&v.counters->detected, 1ull);
+  // ---- locate ----
+  int64_t bstar = -1;
+  double qr = NAN, qi = NAN;
+  if (c.nfmax >= 0) {
+    if (c.nfmin == c.nfmax) bstar = c.nfmax - gb;          // the one signal whose sum overflowed
+  } else if (finite && res > 0) {
+    const double den = d1r * d1r + d1i * d1i;
+    qr = (d2r * d1r + d2i * d1i) / den;
+    qi = (d2i * d1r - d2r * d1i) / den;
+    const double m = rint(qr);
+    if (fabs(qr - m) < 0.25 && fabs(qi) < 0.25 && m >= 1.0 && m <= (double)gsize)
+      bstar = (int64_t)m - 1;
+  }
+  // ---- decide ----
+  int action = 3;
+  if (!v.detect_only) {
+    if (bstar >= 0) {
+      const long long e = (long long)atomicAdd((unsigned long long*)&v.lists.fix[0], 1ull);
+      if (e < v.lists.cap_fix) {
+        v.lists.fix[1 + e] = g;
+        v.lists.fix_signal[e] = gb + bstar;
+        action = 1;
+      }
+    } else {
+      const long long e = (long long)atomicAdd((unsigned long long*)&v.lists.rec[0], 1ull);
+      if (e < v.lists.cap_rec) {
+        v.lists.rec[1 + e] = g;
+        action = 2;
+      }
+    }
+  }
+  if (action == 1) atomicAdd(&v.counters->corrected, 1ull);
+  else if (action == 2) atomicAdd(&v.counters->recomputed, 1ull);
+  else atomicAdd(&v.counters->uncorrectable, 1ull);
+  const unsigned long long slot = atomicAdd(&v.counters->log_total, 1ull);
+  LogEvent ev;
+  ev.exec_index = v.exec_index;
+  ev.group = g;
+  ev.signal = bstar >= 0 ? gb + bstar : -1;
+  ev.action = action;
+  ev.nonfinite = nonfinite ? 1 : 0;
+  ev.residual = res;
+  ev.tau = tau;
+  ev.q_re = qr;
+  ev.q_im = qi;
+  v.log[slot % kLogRing] = ev;
+}
+
+// Each group is reduced by `lanes_per_group` threads (one thread when a group
+// holds few records -- FP64 adds are scarce on this part, so a 32-lane
+// shuffle tree over a handful of records costs more than a serial sum --,
+// one warp, or a whole block of 256 when a group holds many records); lane 0
+// of the group decides.  With v.split > 1 several blocks share a group
+// (lanes_per_group = 256) and the last of them decides.
+// Blocks stride over the groups; the largest clean residual ratio is kept per
+// thread and folded into the counter with one atomic per block.
 __global__ void verify_kernel(const VerifyParams v, int lanes_per_group) {
   __shared__ double sred[8][11];
   __shared__ unsigned long long smax[8];
+  __shared__ int s_last;
   const int lane = threadIdx.x % lanes_per_group;
-  const int64_t per_block = blockDim.x / lanes_per_group;
+  const int64_t per_block = v.split > 1 ? 1 : blockDim.x / lanes_per_group;
+  const int64_t nunits = v.ngroups * v.split;           // (group, slice) units
   unsigned long long clean_max = 0;   // bits of the largest clean ratio (a nonnegative double)
-  for (int64_t g0 = (int64_t)blockIdx.x * per_block; g0 < v.ngroups; g0 += (int64_t)gridDim.x * per_block) {
-    const int64_t g = g0 + threadIdx.x / lanes_per_group;
-    const bool active = g < v.ngroups;
-    double s1r = 0, s1i = 0, s2r = 0, s2i = 0, en = 0, t1r = 0, t1i = 0, t2r = 0, t2i = 0;
-    long long nfmin = 0x7fffffffffffffffLL, nfmax = -1;
+  for (int64_t u0 = (int64_t)blockIdx.x * per_block; u0 < nunits; u0 += (int64_t)gridDim.x * per_block) {
+    const int64_t unit = u0 + (v.split > 1 ? 0 : threadIdx.x / lanes_per_group);
+    const int64_t g = unit / v.split;
+    const int64_t slice = unit - g * v.split;
+    const bool active = unit < nunits;
+    GroupSums c{0, 0, 0, 0, 0, 0, 0, 0, 0, 0x7fffffffffffffffLL, -1};
     if (active) {
-      for (int64_t k = lane; k < v.slots_in; k += lanes_per_group) {
+      // this slice's records: [k0, k1) of the inputs and of the outputs
+      const int64_t ki0 = v.slots_in * slice / v.split, ki1 = v.slots_in * (slice + 1) / v.split;
+      const int64_t ko0 = v.slots_out * slice / v.split, ko1 = v.slots_out * (slice + 1) / v.split;
+      for (int64_t k = ki0 + lane; k < ki1; k += lanes_per_group) {
         const RecIn r = v.rec_in[g * v.slots_in + k];
-        s1r += r.s1r; s1i += r.s1i; s2r += r.s2r; s2i += r.s2i; en += r.energy;
+        c.s1r += r.s1r; c.s1i += r.s1i; c.s2r += r.s2r; c.s2i += r.s2i; c.en += r.energy;
       }
-      for (int64_t k = lane; k < v.slots_out; k += lanes_per_group) {
+      for (int64_t k = ko0 + lane; k < ko1; k += lanes_per_group) {
         const RecOut r = v.rec_out[g * v.slots_out + k];
-        t1r += r.t1r; t1i += r.t1i; t2r += r.t2r; t2i += r.t2i;
-        nfmin = min(nfmin, r.nf_min); nfmax = max(nfmax, r.nf_max);
+        c.t1r += r.t1r; c.t1i += r.t1i; c.t2r += r.t2r; c.t2i += r.t2i;
+        c.nfmin = min(c.nfmin, r.nf_min); c.nfmax = max(c.nfmax, r.nf_max);
       }
     }
     for (int off = 16; off > 0 && lanes_per_group >= 32; off >>= 1) {
-      s1r += __shfl_xor_sync(0xffffffffu, s1r, off); s1i += __shfl_xor_sync(0xffffffffu, s1i, off);
-      s2r += __shfl_xor_sync(0xffffffffu, s2r, off); s2i += __shfl_xor_sync(0xffffffffu, s2i, off);
-      en += __shfl_xor_sync(0xffffffffu, en, off);
-      t1r += __shfl_xor_sync(0xffffffffu, t1r, off); t1i += __shfl_xor_sync(0xffffffffu, t1i, off);
-      t2r += __shfl_xor_sync(0xffffffffu, t2r, off); t2i += __shfl_xor_sync(0xffffffffu, t2i, off);
-      nfmin = min(nfmin, __shfl_xor_sync(0xffffffffu, nfmin, off));
-      nfmax = max(nfmax, __shfl_xor_sync(0xffffffffu, nfmax, off));
+      c.s1r += __shfl_xor_sync(0xffffffffu, c.s1r, off); c.s1i += __shfl_xor_sync(0xffffffffu, c.s1i, off);
+      c.s2r += __shfl_xor_sync(0xffffffffu, c.s2r, off); c.s2i += __shfl_xor_sync(0xffffffffu, c.s2i, off);
+      c.en += __shfl_xor_sync(0xffffffffu, c.en, off);
+      c.t1r += __shfl_xor_sync(0xffffffffu, c.t1r, off); c.t1i += __shfl_xor_sync(0xffffffffu, c.t1i, off);
+      c.t2r += __shfl_xor_sync(0xffffffffu, c.t2r, off); c.t2i += __shfl_xor_sync(0xffffffffu, c.t2i, off);
+      c.nfmin = min(c.nfmin, __shfl_xor_sync(0xffffffffu, c.nfmin, off));
+      c.nfmax = max(c.nfmax, __shfl_xor_sync(0xffffffffu, c.nfmax, off));
     }
     if (lanes_per_group > 32) {          // combine the warps of the block
       const int w = threadIdx.x >> 5;
       if ((threadIdx.x & 31) == 0) {
-        sred[w][0] = s1r; sred[w][1] = s1i; sred[w][2] = s2r; sred[w][3] = s2i; sred[w][4] = en;
-        sred[w][5] = t1r; sred[w][6] = t1i; sred[w][7] = t2r; sred[w][8] = t2i;
-        sred[w][9] = __longlong_as_double(nfmin); sred[w][10] = __longlong_as_double(nfmax);
+        sred[w][0] = c.s1r; sred[w][1] = c.s1i; sred[w][2] = c.s2r; sred[w][3] = c.s2i; sred[w][4] = c.en;
+        sred[w][5] = c.t1r; sred[w][6] = c.t1i; sred[w][7] = c.t2r; sred[w][8] = c.t2i;
+        sred[w][9] = __longlong_as_double(c.nfmin); sred[w][10] = __longlong_as_double(c.nfmax);
       }
       __syncthreads();
       if (threadIdx.x == 0) {
         for (int q = 1; q < lanes_per_group / 32; q++) {
-          s1r += sred[q][0]; s1i += sred[q][1]; s2r += sred[q][2]; s2i += sred[q][3]; en += sred[q][4];
-          t1r += sred[q][5]; t1i += sred[q][6]; t2r += sred[q][7]; t2i += sred[q][8];
-          nfmin = min(nfmin, __double_as_longlong(sred[q][9]));
-          nfmax = max(nfmax, __double_as_longlong(sred[q][10]));
+          c.s1r += sred[q][0]; c.s1i += sred[q][1]; c.s2r += sred[q][2]; c.s2i += sred[q][3];
+          c.en += sred[q][4];
+          c.t1r += sred[q][5]; c.t1i += sred[q][6]; c.t2r += sred[q][7]; c.t2i += sred[q][8];
+          c.nfmin = min(c.nfmin, __double_as_longlong(sred[q][9]));
+          c.nfmax = max(c.nfmax, __double_as_longlong(sred[q][10]));
         }
       }
       __syncthreads();
     }
-    if (!active || lane != 0) continue;
-
-    const int64_t gb = g * v.group;
-    const int64_t gsize = min((int64_t)v.group, v.batch - gb);
-    const double d1r = t1r - s1r, d1i = t1i - s1i;
-    const double d2r = t2r - s2r, d2i = t2i - s2i;
-    const double res = sqrt(d1r * d1r + d1i * d1i);
-    const double tau = v.kappa_u_log2n_sqrtn * sqrt(en);
-    const bool finite = isfinite(res) && isfinite(d2r) && isfinite(d2i);
-    const bool nonfinite = !finite || nfmax >= 0;
-    if (!(nonfinite || res > tau)) {
-      // calibration record: the largest clean residual relative to the threshold
-      const double ratio = tau > 0 ? res / tau : 0.0;
-      clean_max = max(clean_max, (unsigned long long)__double_as_longlong(ratio));
-      continue;
-    }
-
-    atomicAdd(&v.counters->detected, 1ull);
-    // ---- locate ----
-    int64_t bstar = -1;
-    double qr = NAN, qi = NAN;
-    if (nfmax >= 0) {
-      if (nfmin == nfmax) bstar = nfmax - gb;          // the one signal whose sum overflowed
-    } else if (finite && res > 0) {
-      const double den = d1r * d1r + d1i * d1i;
-      qr = (d2r * d1r + d2i * d1i) / den;
-      qi = (d2i * d1r - d2r * d1i) / den;
-      const double m = rint(qr);
-      if (fabs(qr - m) < 0.25 && fabs(qi) < 0.25 && m >= 1.0 && m <= (double)gsize)
-        bstar = (int64_t)m - 1;
-    }
-    // ---- decide ----
-    int action = 3;
-    if (!v.detect_only) {
-      if (bstar >= 0) {
-        const long long e = (long long)atomicAdd((unsigned long long*)&v.lists.fix[0], 1ull);
-        if (e < v.lists.cap_fix) {
-          v.lists.fix[1 + e] = g;
-          v.lists.fix_signal[e] = gb + bstar;
-          action = 1;
-        }
-      } else {
-        const long long e = (long long)atomicAdd((unsigned long long*)&v.lists.rec[0], 1ull);
-        if (e < v.lists.cap_rec) {
-          v.lists.rec[1 + e] = g;
-          action = 2;
+    if (v.split > 1) {
+      // add this slice into the group's accumulators; the last slice decides
+      if (threadIdx.x == 0) {
+        double* a = v.part_acc + g * kVerifyAcc;
+        const double add[9] = {c.s1r, c.s1i, c.s2r, c.s2i, c.en, c.t1r, c.t1i, c.t2r, c.t2i};
+        for (int q = 0; q < 9; q++) atomicAdd(a + q, add[q]);
+        long long* nf = reinterpret_cast<long long*>(a + 9);
+        atomicMin(nf, c.nfmin);
+        atomicMax(nf + 1, c.nfmax);
+        __threadfence();
+        s_last = atomicAdd(v.part_cnt + g, 1u) == (unsigned)(v.split - 1);
+        if (s_last) {
+          __threadfence();
+          c.s1r = __ldcg(a + 0); c.s1i = __ldcg(a + 1); c.s2r = __ldcg(a + 2); c.s2i = __ldcg(a + 3);
+          c.en = __ldcg(a + 4);
+          c.t1r = __ldcg(a + 5); c.t1i = __ldcg(a + 6); c.t2r = __ldcg(a + 7); c.t2i = __ldcg(a + 8);
+          c.nfmin = __ldcg(nf); c.nfmax = __ldcg(nf + 1);
+          for (int q = 0; q < 9; q++) a[q] = 0.0;
+          nf[0] = 0x7fffffffffffffffLL;
+          nf[1] = -1;
+          v.part_cnt[g] = 0u;
         }
       }
+      __syncthreads();
+      if (threadIdx.x == 0 && s_last) decide_group(v, g, c, clean_max);
+      __syncthreads();
+      continue;
     }
-    if (action == 1) atomicAdd(&v.counters->corrected, 1ull);
-    else if (action == 2) atomicAdd(&v.counters->recomputed, 1ull);
-    else atomicAdd(&v.counters->uncorrectable, 1ull);
-    const unsigned long long slot = atomicAdd(&v.counters->log_total, 1ull);
-    LogEvent ev;
-    ev.exec_index = v.exec_index;
-    ev.group = g;
-    ev.signal = bstar >= 0 ? gb + bstar : -1;
-    ev.action = action;
-    ev.nonfinite = nonfinite ? 1 : 0;
-    ev.residual = res;
-    ev.tau = tau;
-    ev.q_re = qr;
-    ev.q_im = qi;
-    v.log[slot % kLogRing] = ev;
+    if (!active || lane != 0) continue;
+    decide_group(v, g, c, clean_max);
   }
   // one atomic per block for the calibration maximum
   for (int off = 16; off > 0; off >>= 1) clean_max = max(clean_max, __shfl_xor_sync(0xffffffffu, clean_max, off));
@@ -155,9 +211,24 @@ __global__ void verify_kernel(const VerifyParams v, int lanes_per_group) {
   }
 }
 
-cudaError_t launch_verify(const VerifyParams& v, cudaStream_t s) {
+int verify_split(int64_t recs, int64_t ngroups, int sms) {
+  // about 2048 records per block, and no more blocks in total than 4 per SM
+  if (recs <= 4096 || ngroups >= sms) return 1;
+  const int64_t want = (recs + 2047) / 2048;
+  const int64_t cap = std::max<int64_t>(1, (int64_t)4 * sms / ngroups);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(cap, 256)));
+}
+
+cudaError_t launch_verify(const VerifyParams& vin, cudaStream_t s) {
   const int threads = 256;
+  VerifyParams v = vin;
+  if (v.split < 1 || !v.part_acc || !v.part_cnt) v.split = 1;
   const int64_t recs = v.slots_in + v.slots_out;
+  if (v.split > 1) {
+    const int64_t blocks = std::min<int64_t>(v.ngroups * v.split, (int64_t)v.max_blocks);
+    verify_kernel<<<(unsigned)blocks, threads, 0, s>>>(v, threads);
+    return cudaGetLastError();
+  }
   const int lanes = recs > 512 ? 256 : (recs > 64 ? 32 : 1);
   const int64_t need = (v.ngroups * lanes + threads - 1) / threads;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)v.max_blocks));

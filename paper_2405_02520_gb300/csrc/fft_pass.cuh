@@ -396,7 +396,10 @@ fft_pass_kernel(const __grid_constant__ PassParams p) {
     }
   };
 
-  for (int64_t chunk = blockIdx.x; chunk < p.nchunks; chunk += gridDim.x) {
+  // a work list holds list[0] entries (often none): only their chunks are visited
+  const int64_t nchunks =
+      p.list ? min(p.nchunks, min((int64_t)p.list[0], (int64_t)p.list_cap) * p.parts * p.line_blocks) : p.nchunks;
+  for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     // ---- decode chunk -> (group, part, line block) and its signal range ----
     const int64_t lb = chunk % p.line_blocks;
     const int64_t rest = chunk / p.line_blocks;

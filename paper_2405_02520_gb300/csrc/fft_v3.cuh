@@ -691,12 +691,27 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
         if (lane == 0) red_add_release(&readers[s], 1u);
       }
       if (p.abft_in && valid) {
-        real sr = 0, si = 0, en = 0;
+        real sr, si, en;
+        if constexpr (sizeof(real) == 4) {
+          // paired FP32: P = sum (wr xr, wi xi) gives Re = P.x - P.y, and
+          // Q = sum (xr^2, xi^2) the energy; Im stays two scalar FMAs
+          float2 P = {0.f, 0.f}, Q = {0.f, 0.f};
+          float im = 0.f;
 #pragma unroll
-        for (int r = 0; r < E; r++) {
-          sr = fma(wv[r].x, v[r].x, sr); sr = fma(-wv[r].y, v[r].y, sr);
-          si = fma(wv[r].x, v[r].y, si); si = fma(wv[r].y, v[r].x, si);
-          en = fma(v[r].x, v[r].x, en); en = fma(v[r].y, v[r].y, en);
+          for (int r = 0; r < E; r++) {
+            P = __ffma2_rn(wv[r], v[r], P);
+            Q = __ffma2_rn(v[r], v[r], Q);
+            im = fmaf(wv[r].x, v[r].y, im); im = fmaf(wv[r].y, v[r].x, im);
+          }
+          sr = P.x - P.y; si = im; en = Q.x + Q.y;
+        } else {
+          sr = 0; si = 0; en = 0;
+#pragma unroll
+          for (int r = 0; r < E; r++) {
+            sr = fma(wv[r].x, v[r].x, sr); sr = fma(-wv[r].y, v[r].y, sr);
+            si = fma(wv[r].x, v[r].y, si); si = fma(wv[r].y, v[r].x, si);
+            en = fma(v[r].x, v[r].x, en); en = fma(v[r].y, v[r].y, en);
+          }
         }
         acc.s1r += sr; acc.s1i += si;
         acc.s2r = fma(wgt, sr, acc.s2r); acc.s2i = fma(wgt, si, acc.s2i);

@@ -146,6 +146,9 @@ struct tfft_plan_s {
   void* wt_lo = nullptr; void* wt_hi = nullptr; int wt_lbits = 0;
   void* tmp = nullptr;
   RecIn* rec_in = nullptr; RecOut* rec_out = nullptr;
+  int vsplit = 1;                   // verification blocks per group
+  double* part_acc = nullptr;       // split verification: per-group accumulators
+  unsigned* part_cnt = nullptr;
   int64_t slots_in = 1, slots_out = 1;
   long long* lists_mem = nullptr;
   Lists lists{};
@@ -195,7 +198,7 @@ int upload(tfft_plan_s* p, void** dst, const std::vector<double>& re, const std:
 void free_plan(tfft_plan_s* p) {
   void* bufs[] = {p->tw_sub, p->twN_lo, p->twN_hi, p->wt_lo, p->wt_hi, p->wtab, p->tmp, p->rec_in, p->rec_out,
                   p->lists_mem, p->counters, p->log, p->ws_c1, p->ws_acc, p->stage_in, p->stage_out,
-                  p->err_flag};
+                  p->err_flag, p->part_acc, p->part_cnt};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& q : p->pp)
@@ -769,6 +772,21 @@ int plan_workspace(tfft_plan_s* p) {
   if (p->abft) {
     TFFT_CUDA(cudaMalloc(&p->rec_in, sizeof(RecIn) * p->vgroups * p->slots_in));
     TFFT_CUDA(cudaMalloc(&p->rec_out, sizeof(RecOut) * p->vgroups * p->slots_out));
+    p->vsplit = verify_split(p->slots_in + p->slots_out, p->vgroups, p->sms);
+    if (p->vsplit > 1) {
+      // accumulators start as zero sums, an empty nonfinite range, zero count
+      std::vector<double> init((size_t)p->vgroups * kVerifyAcc, 0.0);
+      for (int64_t g = 0; g < p->vgroups; g++) {
+        const long long lo = 0x7fffffffffffffffLL, hi = -1;
+        std::memcpy(&init[(size_t)g * kVerifyAcc + 9], &lo, sizeof(lo));
+        std::memcpy(&init[(size_t)g * kVerifyAcc + 10], &hi, sizeof(hi));
+      }
+      TFFT_CUDA(cudaMalloc(&p->part_acc, init.size() * sizeof(double)));
+      TFFT_CUDA(cudaMemcpy(p->part_acc, init.data(), init.size() * sizeof(double), cudaMemcpyHostToDevice));
+      TFFT_CUDA(cudaMalloc(&p->part_cnt, (size_t)p->vgroups * sizeof(unsigned)));
+      TFFT_CUDA(cudaMemset(p->part_cnt, 0, (size_t)p->vgroups * sizeof(unsigned)));
+      p->workspace_bytes += (int64_t)(init.size() * sizeof(double) + (size_t)p->vgroups * sizeof(unsigned));
+    }
     TFFT_CUDA(cudaMalloc(&p->ws_c1, p->cap_fix * sig));
     TFFT_CUDA(cudaMalloc(&p->ws_acc, p->cap_fix * sig));
     p->workspace_bytes += sizeof(RecIn) * p->vgroups * p->slots_in +
@@ -939,6 +957,7 @@ int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
     v.detect_only = p->detect_only;
     v.lists = p->lists; v.counters = p->counters; v.log = p->log; v.exec_index = p->execs;
     v.max_blocks = 8 * p->sms;
+    v.split = p->vsplit; v.part_acc = p->part_acc; v.part_cnt = p->part_cnt;
     if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
     FixParams f{};
     f.n = p->n; f.batch = p->batch; f.group = p->vG; f.dtype = p->dtype;

@@ -233,7 +233,18 @@ struct VerifyParams {
   LogEvent* log;
   long long exec_index;
   int max_blocks;               // grid cap (blocks stride over the groups)
+  // groups with many records and few groups: `split` blocks per group add
+  // their slice's sums into part_acc[g] (9 sums, then the nonfinite range as
+  // integers) and count themselves in part_cnt[g]; the last one decides and
+  // restores the accumulators (zero sums, empty range, zero count)
+  int split;                    // blocks per group (1: one block strides over groups)
+  double* part_acc;             // ngroups x kVerifyAcc
+  unsigned* part_cnt;           // ngroups
 };
+constexpr int kVerifyAcc = 12;
+// blocks per group for a group of `recs` records when there are `ngroups`
+// groups on `sms` multiprocessors (1 = no split)
+int verify_split(int64_t recs, int64_t ngroups, int sms);
 cudaError_t launch_verify(const VerifyParams& v, cudaStream_t s);
 
 struct FixParams {
