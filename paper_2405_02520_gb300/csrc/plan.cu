@@ -251,10 +251,14 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
   // three passes take sub-transforms up to twice that (32-byte column runs)
   const int NSUBMAX = n > (int64_t)(TILE / CMIN) * (TILE / CMIN) * (TILE / CMIN) ? 2 * TILE / CMIN : TILE / CMIN;
 
+  // complex64 two-pass plans may end in a 1024-point last pass (line-major
+  // input rows; 32-byte output column runs), which beats three passes for
+  // N = 2^19; a 1024-point first pass (32-byte input column runs) does not
+  const int64_t LASTMAX2 = c64 ? 2 * NSUBMAX : NSUBMAX;
   int passes;
   if (o->force_passes) passes = o->force_passes;
   else if (n <= TILE) passes = 1;
-  else if (n <= (int64_t)NSUBMAX * NSUBMAX) passes = 2;
+  else if (n <= (int64_t)NSUBMAX * LASTMAX2) passes = 2;
   else passes = 3;
   const int m = ilog2(n);
   int mf[3] = {m, 0, 0};
@@ -270,7 +274,7 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
     if (mf[i] < 1) return TFFT_ERR_INVALID_ARG;
   if (passes > 1)
     for (int i = 0; i < passes; i++)
-      if ((int64_t(1) << mf[i]) > NSUBMAX) return TFFT_ERR_INVALID_ARG;
+      if ((int64_t(1) << mf[i]) > (passes == 2 && i == 1 ? LASTMAX2 : NSUBMAX)) return TFFT_ERR_INVALID_ARG;
   p->passes = passes;
 
   int G = o->group > 0 ? o->group : 16;

@@ -53,7 +53,7 @@ def _site(info, rng, passes=None):
     return p, stage, line, index
 
 
-@pytest.mark.parametrize("log2n,batch", [(10, 64), (16, 8), (20, 4)])
+@pytest.mark.parametrize("log2n,batch", [(10, 64), (16, 8), (19, 6), (20, 4)])
 def test_large_bitflips_every_pass_corrected(log2n, batch):
     """High exponent/mantissa bit flips (bits 26..30 of the real part) at
     random (pass, stage, signal, element): detected, named, corrected."""
@@ -93,7 +93,7 @@ def test_nonfinite_fault_located_and_corrected():
     t.tfft_destroy(plan)
 
 
-@pytest.mark.parametrize("log2n", [10, 16])
+@pytest.mark.parametrize("log2n", [10, 16, 19])
 def test_two_faults_in_a_group_fall_back_to_recompute(log2n):
     n = 1 << log2n
     batch = 40
