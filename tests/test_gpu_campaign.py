@@ -23,6 +23,6 @@ def test_config1_ten_thousand_clean_launches_no_false_positive():
     assert r["detected"] == 0, r
 
 
-def test_large_n_clean_launches_no_false_positive():
-    r = clean_campaign(1 << 16, 64, 1000)
+def test_large_n_ten_thousand_clean_launches_no_false_positive():
+    r = clean_campaign(1 << 16, 64, 10000)
     assert r["detected"] == 0, r
