@@ -226,11 +226,26 @@ class OraclePool:
     timing its own bounded sample of the sweep (different seeds); a sample's
     time is the wall time of the whole pool."""
 
+    THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                   "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")
+
     def __init__(self, workers: int):
         import multiprocessing as mp
         self.workers = workers
-        self.pool = mp.get_context("spawn").Pool(workers)
-        self.pool.map(_oracle_worker, [(1 << 8, 0, [8])] * workers)     # start-up and imports
+        # one thread per process: numpy's BLAS would otherwise start a thread
+        # per core in every process (the children read these at start-up)
+        saved = {k: os.environ.get(k) for k in self.THREAD_VARS}
+        for k in self.THREAD_VARS:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(workers)
+            self.pool.map(_oracle_worker, [(1 << 8, 0, [8])] * workers)     # start-up and imports
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
 
     def sample(self, elems_per_worker: int, seed0: int = 0, sweep=SWEEP):
         t0 = time.perf_counter()
@@ -454,7 +469,9 @@ def run_ours(args):
         pool = OraclePool(cores)
         f, s, desc = pool.sample(1 << 20)
         pool.close()
-        f1, s1, desc1 = oracle_sample(1 << 22)
+        one = OraclePool(1)
+        f1, s1, desc1 = one.sample(1 << 22)
+        one.close()
         cpu = {"value": round(f / s / 1e9, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                "sample": desc, "seconds": round(s, 2),
                "single_core": {"value": round(f1 / s1 / 1e9, 4), "sample": desc1, "seconds": round(s1, 2)}}

@@ -163,11 +163,17 @@ int tfft_plan_ex(tfft_plan_t *out, const tfft_plan_opts *opts);
 int tfft_exec(tfft_plan_t p, const void *in, void *out, tfft_stream_t stream);
 
 /*
- * tfft_exec_host -- the same transform on HOST buffers (pinned or pageable):
- * copies `host_in` to a plan-owned device buffer, runs tfft_exec, copies the
- * result to `host_out`, all on `stream`, and synchronises `stream` before
- * returning.  The plan allocates its two device staging buffers on the first
- * call and keeps them until tfft_destroy.
+ * tfft_exec_host -- the same transform on HOST buffers (pinned or pageable;
+ * pinned for overlap): copies `host_in` to a plan-owned device buffer, runs
+ * the transform, copies the result to `host_out`, and synchronises `stream`
+ * before returning.  The batch is cut into up to eight chunks of whole
+ * checksum groups: the input copies run back to back on a plan-owned copy
+ * stream, each chunk is transformed on `stream` once its input has landed,
+ * and its output copy (a second plan-owned stream) overlaps the later
+ * chunks' input copies and transforms.  One chunk (copy, transform, copy on
+ * `stream`) when the batch is one group or a test fault is armed.  The plan
+ * allocates its two device staging buffers, the copy streams and their
+ * events on the first call and keeps them until tfft_destroy.
  */
 int tfft_exec_host(tfft_plan_t p, const void *host_in, void *host_out, tfft_stream_t stream);
 

@@ -94,8 +94,8 @@ __device__ void decide_group(const VerifyParams& v, int64_t g, const GroupSums& 
   const unsigned long long slot = atomicAdd(&v.counters->log_total, 1ull);
   LogEvent ev;
   ev.exec_index = v.exec_index;
-  ev.group = g;
-  ev.signal = bstar >= 0 ? gb + bstar : -1;
+  ev.group = v.group_base + g;
+  ev.signal = bstar >= 0 ? v.group_base * v.group + gb + bstar : -1;
   ev.action = action;
   ev.nonfinite = nonfinite ? 1 : 0;
   ev.residual = res;

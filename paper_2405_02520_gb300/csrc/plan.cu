@@ -167,6 +167,10 @@ struct tfft_plan_s {
   int64_t execs = 0, launches = 0;
   cudaStream_t last_stream = nullptr;
   bool used = false;
+  // tfft_exec_host pipeline: copy streams and per-chunk events, made on first use
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_entry = nullptr, ev_end = nullptr;
+  cudaEvent_t ev_in[8] = {}, ev_done[8] = {};
   int timing = 0;
   std::vector<TimedLaunch> timed;
   std::vector<cudaEvent_t> event_pool;
@@ -196,6 +200,12 @@ int upload(tfft_plan_s* p, void** dst, const std::vector<double>& re, const std:
 }
 
 void free_plan(tfft_plan_s* p) {
+  for (cudaEvent_t e : p->ev_in) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_done) if (e) cudaEventDestroy(e);
+  if (p->ev_entry) cudaEventDestroy(p->ev_entry);
+  if (p->ev_end) cudaEventDestroy(p->ev_end);
+  if (p->h2d) cudaStreamDestroy(p->h2d);
+  if (p->d2h) cudaStreamDestroy(p->d2h);
   void* bufs[] = {p->tw_sub, p->twN_lo, p->twN_hi, p->wt_lo, p->wt_hi, p->wtab, p->tmp, p->rec_in, p->rec_out,
                   p->lists_mem, p->counters, p->log, p->ws_c1, p->ws_acc, p->stage_in, p->stage_out,
                   p->err_flag, p->part_acc, p->part_cnt};
@@ -900,7 +910,11 @@ int kind_of(const tfft_plan_s* p, int i) {
 // Run the passes from `in` to `out` (through tmp when there are several).
 int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool main_exec,
                const long long* list, int list_identity, int list_cap, int64_t list_block,
-               int64_t batch, int kind_override, bool user_io = true) {
+               int64_t batch, int kind_override, bool user_io = true, int64_t vgroup0 = 0) {
+  // an exec over the signals [b0, b0 + batch) of the plan (b0 = vgroup0 vG,
+  // a multiple of G): `in` and `out` already point at signal b0, the records
+  // of its verification groups start at group vgroup0
+  const int64_t ng = (batch + p->G - 1) / p->G;
   for (int i = 0; i < p->passes; i++) {
     PassParams a = base_params(p, i);
     a.batch = batch;
@@ -910,10 +924,14 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
       a.soff_in = i == 0 ? p->soff : nullptr;
       a.soff_out = i == p->passes - 1 ? p->soff : nullptr;
     }
+    if (main_exec) {
+      a.ngroups = ng;
+      a.nchunks = ng * p->pp[i].parts * p->pp[i].line_blocks;
+    }
     if (main_exec && p->pp[i].v3) {
       const PassPlan& q = p->pp[i];
       a.C = q.vC; a.nthreads = 256; a.line_blocks = q.vLB;
-      a.nchunks = p->ngroups * q.parts * q.vLB;
+      a.nchunks = ng * q.parts * q.vLB;
       a.log2C = ilog2(q.vC); a.log2LO = ilog2(q.LO); a.log2LB = ilog2(q.vLB);
     }
     if (main_exec) {
@@ -921,7 +939,10 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
       a.abft_out = p->abft && i == p->passes - 1;
       a.slots = (i == 0) ? p->slots_in : p->slots_out;
       if (p->passes == 1) a.slots = p->slots_in;
-      a.rec_in = p->rec_in; a.rec_out = p->rec_out;
+      if (p->abft) {
+        a.rec_in = p->rec_in + vgroup0 * p->slots_in;
+        a.rec_out = p->rec_out + vgroup0 * p->slots_out;
+      }
       a.fault = p->pending;
       for (int k = 0; k < 3; k++) a.fault_more[k] = p->pending_more[k];
       a.nfault = p->npending;
@@ -939,14 +960,22 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
   return 0;
 }
 
-int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
-  int rc = run_passes(p, in, out, s, true, nullptr, 0, 0, 0, p->batch, -1);
+// The exec over signals [b0, b0 + nb) (b0 a multiple of G, nb > 0): the
+// passes, the verification of their groups and the correction path, all on
+// `s`, reading in + b0 n and writing out + b0 n.
+int exec_range(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_t b0, int64_t nb) {
+  const size_t off = (size_t)b0 * (size_t)p->n * p->esize;
+  in = static_cast<const unsigned char*>(in) + off;
+  out = static_cast<unsigned char*>(out) + off;
+  const int64_t vg0 = b0 / p->vG;
+  int rc = run_passes(p, in, out, s, true, nullptr, 0, 0, 0, nb, -1, true, vg0);
   if (rc) return rc;
   if (p->abft) {
     VerifyParams v{};
-    v.n = p->n; v.batch = p->batch; v.group = p->vG; v.ngroups = p->vgroups;
+    v.n = p->n; v.batch = nb; v.group = p->vG; v.ngroups = (nb + p->vG - 1) / p->vG;
+    v.group_base = vg0;
     v.slots_in = p->slots_in; v.slots_out = p->slots_out;
-    v.rec_in = p->rec_in; v.rec_out = p->rec_out;
+    v.rec_in = p->rec_in + vg0 * p->slots_in; v.rec_out = p->rec_out + vg0 * p->slots_out;
     // unit roundoff of the butterfly arithmetic: FP32, FP64, or the tensor-core forms
     const double u = p->dtype != TFFT_C64 ? std::ldexp(1.0, -53)
                    : p->prec == TFFT_PREC_TF32X3 ? std::ldexp(1.0, -20)
@@ -964,7 +993,7 @@ int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
     v.split = p->vsplit; v.part_acc = p->part_acc; v.part_cnt = p->part_cnt;
     if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
     FixParams f{};
-    f.n = p->n; f.batch = p->batch; f.group = p->vG; f.dtype = p->dtype;
+    f.n = p->n; f.batch = nb; f.group = p->vG; f.dtype = p->dtype;
     f.in = in; f.out = out; f.soff = p->soff; f.ws_c1 = p->ws_c1; f.ws_acc = p->ws_acc; f.lists = p->lists;
     if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_gather(f, s); }))) return rc;
     // W X e_1 of every queued group, in place in ws_c1
@@ -973,10 +1002,14 @@ int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
       return rc;
     if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_apply(f, s); }))) return rc;
     // groups that could not be located: recompute from the input
-    if ((rc = run_passes(p, in, out, s, false, p->lists.rec, 0, p->cap_rec, p->vG, p->batch, 5)))
+    if ((rc = run_passes(p, in, out, s, false, p->lists.rec, 0, p->cap_rec, p->vG, nb, 5)))
       return rc;
   }
   return 0;
+}
+
+int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
+  return exec_range(p, in, out, s, 0, p->batch);
 }
 
 bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
@@ -1101,14 +1134,81 @@ int tfft_exec_host(tfft_plan_t p, const void* host_in, void* host_out, tfft_stre
   if (!p || !host_in || !host_out) return TFFT_ERR_INVALID_ARG;
   const size_t bytes = (size_t)p->batch * p->n * p->esize;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(p->mu);
   if (!p->stage_in) {
     TFFT_CUDA(cudaMalloc(&p->stage_in, bytes));
     TFFT_CUDA(cudaMalloc(&p->stage_out, bytes));
   }
-  TFFT_CUDA(cudaMemcpyAsync(p->stage_in, host_in, bytes, cudaMemcpyHostToDevice, s));
-  int rc = tfft_exec(p, p->stage_in, p->stage_out, stream);
+  // Chunks of whole checksum groups, up to eight: the host-to-device copies
+  // run back to back on one copy stream, each chunk's transform starts once
+  // its input has landed, and its device-to-host copy overlaps the next
+  // chunks' input copies and transforms (the link carries both directions at
+  // once).  One chunk when a test fault is armed (its signal index is
+  // relative to the whole batch) or the plan addresses signals by offsets.
+  const int64_t ng = (p->batch + p->G - 1) / p->G;
+  const bool armed = p->npending > 0 || p->pending.mode != 0;
+  const int nch = (armed || p->soff) ? 1 : (int)std::min<int64_t>(8, ng);
+  const size_t sig = (size_t)p->n * p->esize;
+  int rc = 0;
+  if (nch == 1) {
+    TFFT_CUDA(cudaMemcpyAsync(p->stage_in, host_in, bytes, cudaMemcpyHostToDevice, s));
+    rc = exec_range(p, p->stage_in, p->stage_out, s, 0, p->batch);
+    if (!rc) TFFT_CUDA(cudaMemcpyAsync(host_out, p->stage_out, bytes, cudaMemcpyDeviceToHost, s));
+  } else {
+    if (!p->h2d) {
+      TFFT_CUDA(cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking));
+      TFFT_CUDA(cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking));
+      TFFT_CUDA(cudaEventCreateWithFlags(&p->ev_entry, cudaEventDisableTiming));
+      TFFT_CUDA(cudaEventCreateWithFlags(&p->ev_end, cudaEventDisableTiming));
+      for (int c = 0; c < 8; c++) {
+        TFFT_CUDA(cudaEventCreateWithFlags(&p->ev_in[c], cudaEventDisableTiming));
+        TFFT_CUDA(cudaEventCreateWithFlags(&p->ev_done[c], cudaEventDisableTiming));
+      }
+    }
+    const int64_t gpc = (ng + nch - 1) / nch;   // groups per chunk
+    auto chunk = [&](int c, int64_t* b0, int64_t* nb) {
+      *b0 = std::min<int64_t>(p->batch, (int64_t)c * gpc * p->G);
+      *nb = std::min<int64_t>(p->batch, (int64_t)(c + 1) * gpc * p->G) - *b0;
+    };
+    // the copies start after whatever the caller queued on `s` before
+    TFFT_CUDA(cudaEventRecord(p->ev_entry, s));
+    TFFT_CUDA(cudaStreamWaitEvent(p->h2d, p->ev_entry, 0));
+    TFFT_CUDA(cudaStreamWaitEvent(p->d2h, p->ev_entry, 0));
+    for (int c = 0; c < nch; c++) {
+      int64_t b0, nb;
+      chunk(c, &b0, &nb);
+      if (nb <= 0) continue;
+      TFFT_CUDA(cudaMemcpyAsync(static_cast<unsigned char*>(p->stage_in) + b0 * sig,
+                                static_cast<const unsigned char*>(host_in) + b0 * sig, (size_t)nb * sig,
+                                cudaMemcpyHostToDevice, p->h2d));
+      TFFT_CUDA(cudaEventRecord(p->ev_in[c], p->h2d));
+    }
+    for (int c = 0; c < nch && !rc; c++) {
+      int64_t b0, nb;
+      chunk(c, &b0, &nb);
+      if (nb <= 0) continue;
+      TFFT_CUDA(cudaStreamWaitEvent(s, p->ev_in[c], 0));
+      rc = exec_range(p, p->stage_in, p->stage_out, s, b0, nb);
+      if (rc) break;
+      TFFT_CUDA(cudaEventRecord(p->ev_done[c], s));
+      TFFT_CUDA(cudaStreamWaitEvent(p->d2h, p->ev_done[c], 0));
+      TFFT_CUDA(cudaMemcpyAsync(static_cast<unsigned char*>(host_out) + b0 * sig,
+                                static_cast<const unsigned char*>(p->stage_out) + b0 * sig, (size_t)nb * sig,
+                                cudaMemcpyDeviceToHost, p->d2h));
+    }
+    // `s` (and so tfft_report) waits for the last copy; the copy streams for
+    // each other before the next call reuses the staging buffers
+    TFFT_CUDA(cudaEventRecord(p->ev_end, p->d2h));
+    TFFT_CUDA(cudaStreamWaitEvent(s, p->ev_end, 0));
+    TFFT_CUDA(cudaStreamWaitEvent(p->h2d, p->ev_end, 0));
+  }
+  p->pending = FaultSite{};
+  for (auto& f : p->pending_more) f = FaultSite{};
+  p->npending = 0;
+  p->execs++;
+  p->last_stream = s;
+  p->used = true;
   if (rc) return rc;
-  TFFT_CUDA(cudaMemcpyAsync(host_out, p->stage_out, bytes, cudaMemcpyDeviceToHost, s));
   TFFT_CUDA(cudaStreamSynchronize(s));
   return TFFT_SUCCESS;
 }

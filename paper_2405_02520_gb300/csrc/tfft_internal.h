@@ -223,6 +223,7 @@ struct VerifyParams {
   int64_t n, batch;
   int group;
   int64_t ngroups;
+  int64_t group_base;           // index of group 0 in the plan (fault log entries)
   int64_t slots_in, slots_out;
   const RecIn* rec_in;
   const RecOut* rec_out;
