@@ -433,6 +433,8 @@ def run_ours(args):
     ragged = None if args.no_ragged else ragged_measure(t, torch, stream, args, peak)
     tensor = None if args.no_ragged else tc_measure(t, torch, stream, peak)
     ablation = None if args.no_ragged else one_sided_measure(t, torch, x, y, stream, args)
+    small = None if args.no_ragged else config1_measure(t, torch, stream, peak)
+    c128 = None if args.no_ragged else c128_measure(t, torch, stream, peak)
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
@@ -538,6 +540,8 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "ragged": ragged,
         "one_sided": ablation,
+        "config1": small,
+        "complex128": c128,
         "tensor_core": tensor,
     }
     print(json.dumps(line), flush=True)
@@ -684,6 +688,92 @@ def tc_measure(t, torch, stream, peak):
                          "detected": t.tfft_report(pl)[0]}
             t.tfft_destroy(pl)
         out[f"{n}x{batch}"] = res
+        del xs, ys
+    return out
+
+
+def config1_measure(t, torch, stream, peak):
+    """N = 1024 x 256 signals, U[-1,1), ABFT on: 2 MiB in and out, so one pair
+    of buffers stays in L2.  Timed hot (the same pair every exec) and over 64
+    rotating pairs (128 MiB each way, more than L2) for the HBM figure."""
+    n, b, pairs, k = 1024, 256, 64, 640
+    xs = torch.empty((pairs, b, n), dtype=torch.complex64, device=stream.device)
+    g = torch.Generator(device=stream.device).manual_seed(0)
+    xs.real.uniform_(-1, 1, generator=g)
+    xs.imag.uniform_(-1, 1, generator=g)
+    ys = torch.empty_like(xs)
+    pl = t.tfft_plan(n, b, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED)
+    out = {"n": n, "batch": b}
+    for name, rot in (("hot_l2", 1), ("rotating_64_pairs", pairs)):
+        for i in range(8):
+            t.tfft_exec(pl, xs[i % rot], ys[i % rot], stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(k):
+            t.tfft_exec(pl, xs[i % rot], ys[i % rot], stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / k * 1e3
+        out[name] = {"us_per_exec": round(us, 2), "gflops": round(flops(n, b) / (us / 1e6) / 1e9, 1),
+                     "hbm_frac": round(16.0 * n * b / (us / 1e6) / 1e9 / peak, 4)}
+    # the same exec captured once into a CUDA graph and replayed (this size
+    # is launch-bound: the pass, the verification and the correction
+    # launches that find nothing to do)
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2):
+        t.tfft_exec(pl, xs[0], ys[0], torch.cuda.current_stream())
+    for _ in range(8):
+        g2.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(k):
+        g2.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) / k * 1e3
+    out["graph_replay_hot_l2"] = {"us_per_exec": round(us, 2), "gflops": round(flops(n, b) / (us / 1e6) / 1e9, 1)}
+    out["detected"] = t.tfft_report(pl)[0]
+    del g2
+    t.tfft_destroy(pl)
+    return out
+
+
+def c128_measure(t, torch, stream, peak):
+    """complex128, N(0,1) re/im: N = 2^20 x 64 and N = 2^12 x 2^14, ABFT on
+    and off.  Bytes: 32 B per element per pass; the FP64 units are the likely
+    bound on this part (GB300's FP64 rate is about 1.25 TFLOP/s nominal), so
+    the line gives both fractions."""
+    out = {"fp64_nominal_tflops": 1.25}
+    for lg, b in ((20, 64), (12, 1 << 14)):
+        n = 1 << lg
+        xs = torch.empty((b, n), dtype=torch.complex128, device=stream.device)
+        g = torch.Generator(device=stream.device).manual_seed(3)
+        xs.real.normal_(0, 1, generator=g)
+        xs.imag.normal_(0, 1, generator=g)
+        ys = torch.empty_like(xs)
+        res = {}
+        for name, mode in (("on", t.TFFT_ABFT_TWO_SIDED), ("off", t.TFFT_ABFT_OFF)):
+            pl = t.tfft_plan(n, b, t.TFFT_C128, mode)
+            passes = t.tfft_plan_info(pl)["passes"]
+            for _ in range(3):
+                t.tfft_exec(pl, xs, ys, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                t.tfft_exec(pl, xs, ys, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 5
+            res[f"ms_{name}"] = round(ms, 4)
+            if name == "on":
+                res["passes"] = passes
+                res["gflops"] = round(flops(n, b) / (ms / 1e3) / 1e9, 1)
+                res["hbm_frac"] = round(32.0 * passes * n * b / (ms / 1e3) / 1e9 / peak, 4)
+                res["detected"] = t.tfft_report(pl)[0]
+            t.tfft_destroy(pl)
+        res["abft_overhead_pct"] = round((res["ms_on"] - res["ms_off"]) / res["ms_off"] * 100, 2)
+        out[f"{n}x{b}"] = res
         del xs, ys
     return out
 

@@ -58,3 +58,27 @@ def test_exec_host_armed_fault_corrected():
     ev, total = t.tfft_fault_log(plan)
     assert total == 1 and ev[0]["signal"] == sig and ev[0]["group"] == sig // 16
     t.tfft_destroy(plan)
+
+
+@pytest.mark.parametrize("mode,dtype,precision", [(t.TFFT_ABFT_ONE_SIDED, t.TFFT_C64, t.TFFT_PREC_FP32),
+                                                  (t.TFFT_ABFT_TWO_SIDED, t.TFFT_C128, t.TFFT_PREC_FP32),
+                                                  (t.TFFT_ABFT_TWO_SIDED, t.TFFT_C64, t.TFFT_PREC_BF16X3),
+                                                  (t.TFFT_ABFT_OFF, t.TFFT_C64, t.TFFT_PREC_FP32)])
+def test_exec_host_other_modes_match_device_exec(mode, dtype, precision):
+    import torch
+    n, batch = 4096, 150
+    x = uniform_batch(n, batch, seed=4300, dtype=np.complex128 if dtype == t.TFFT_C128 else np.complex64)
+    plan = t.tfft_plan_ex(n, batch, dtype, mode, precision=precision)
+    tdt = torch.complex128 if dtype == t.TFFT_C128 else torch.complex64
+    hin = torch.empty((batch, n), dtype=tdt, pin_memory=True)
+    hin.copy_(torch.from_numpy(x))
+    hout = torch.empty_like(hin)
+    s = torch.cuda.current_stream()
+    t.tfft_exec_host(plan, hin, hout, s)
+    xd = hin.cuda()
+    yd = torch.empty_like(xd)
+    t.tfft_exec(plan, xd, yd, s)
+    torch.cuda.synchronize()
+    assert np.array_equal(hout.numpy(), yd.cpu().numpy())
+    assert t.tfft_report(plan)[0] == 0
+    t.tfft_destroy(plan)
