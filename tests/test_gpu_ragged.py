@@ -188,3 +188,33 @@ def test_ragged_one_sided_recompute_in_place():
     st = r.report()
     assert st["detected"] == 2 and st["corrected"] + st["recomputed"] == 2, st
     r.destroy()
+
+
+def test_ragged_complex128_in_place():
+    """complex128 buckets addressed in place (offsets multiples of 64
+    elements), N(0,1) re/im, a fault corrected, against the oracle at the
+    complex128 tolerance."""
+    import torch
+    rng = np.random.default_rng(1212)
+    lengths = (1 << rng.integers(6, 14, size=120)).astype(np.int64)
+    total = int(lengths.sum())
+    x = rng.standard_normal(total) + 1j * rng.standard_normal(total)
+    r = t.Ragged(lengths.tolist(), dtype=t.TFFT_C128, autotune=False)
+    assert all(r.layout().values()), r.layout()
+    passes = dict(r.info())
+    xt = torch.from_numpy(x).cuda()
+    yt = torch.empty_like(xt)
+    sig = int(np.nonzero(lengths == 4096)[0][1])
+    r.set_fault(sig, mode=t.TFFT_FAULT_SCALE, pass_=passes[4096] - 1, stage=0, line=0, index=6, factor=1.25)
+    r.exec(xt, yt)
+    torch.cuda.synchronize()
+    y = yt.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(lengths)])
+    for n in np.unique(lengths):
+        idx = np.nonzero(lengths == n)[0]
+        xs = np.stack([x[off[i]:off[i] + n] for i in idx])
+        ys = np.stack([y[off[i]:off[i] + n] for i in idx])
+        assert rel_err_rows(ys, oracle.fft(xs)).max() <= tol(int(n), t.TFFT_C128), int(n)
+    st = r.report()
+    assert st["detected"] == 1 and st["corrected"] + st["recomputed"] == 1, st
+    r.destroy()
