@@ -584,8 +584,12 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
   int k0 = 0;                   // (k of output q = 0) mod 3
   Partials<real> acc;
   bool setup_done = false;
+  // the input side of the checksum runs in the first pass (single or
+  // column role), the output side in the last (single or last role): the
+  // other side is compiled out of each role
+  constexpr bool IN_CK = ROLE != V3_LAST, OUT_CK = ROLE != V3_COLS;
   auto setup_positions = [&](long long hi, long long lo0) {
-    if (p.abft_in) {
+    if (IN_CK && p.abft_in) {
       const cT* wtab = reinterpret_cast<const cT*>(p.wtab);
       const long long lo = ROLE == V3_SINGLE ? 0 : lo0 + c0;
 #pragma unroll
@@ -598,7 +602,7 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
     }
     smask = 0;
     k0 = 0;
-    if (p.abft_out) {
+    if (OUT_CK && p.abft_out) {
       const long long lo = (ROLE == V3_SINGLE) ? 0 : lo0 + c0;
       const long long kp0 = hi * p.out_hi + lo * p.out_lo + (long long)j0 * p.out_es;
       k0 = (int)(kp0 % 3);
@@ -690,7 +694,7 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
         __syncwarp();
         if (lane == 0) red_add_release(&readers[s], 1u);
       }
-      if (p.abft_in && valid) {
+      if (IN_CK && p.abft_in && valid) {
         real sr, si, en;
         if constexpr (sizeof(real) == 4) {
           // paired FP32: P = sum (wr xr, wi xi) gives Re = P.x - P.y, and
@@ -805,7 +809,7 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
         for (int q = 0; q < E; q++)
           if (fs.index == j0 + q * G::TPL) v[q] = faulted(v[q], fs);
       }
-      if (p.abft_out && valid) {
+      if (OUT_CK && p.abft_out && valid) {
         // T += sum_q s_q w3^(k0 + q dl) y_q: group the outputs by q mod 3
         real a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
 #pragma unroll
