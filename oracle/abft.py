@@ -23,7 +23,7 @@ group b = 0..G-1.
 * Correct (Section III-B, delayed batched correction): the divergence of the
   batch checksum, delta = Y' e_1 - W (X e_1), is subtracted from column b*.
 
-Readings of points the paper leaves open (listed in the design doc as well):
+Readings of points the paper leaves open:
   - tau = kappa * u * (log2(N) + 4) * sqrt(N) * sqrt(sum_b ||x_b||^2): an
     absolute, Parseval-scaled threshold (the +4 covers the rounding of the
     checksum arithmetic itself); the paper prints no value for delta.

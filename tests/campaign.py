@@ -1,6 +1,6 @@
 """Fault-injection campaign on the GPU (TurboFFT Section II-A fault model and
 the Section V-C protocol): random signal, pass, stage, element and bit; each
-fault is run once with correction disabled, to judge it harmful or benign
+fault is run once with correction disabled, to classify it as harmful or benign
 against the FP64 oracle (harmful = the uncorrected output of the faulty signal
 misses the tolerance), and once with correction on.
 
