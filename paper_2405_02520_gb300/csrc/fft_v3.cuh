@@ -337,17 +337,27 @@ __device__ __forceinline__ void copy_out(const PassParams& p, long long tb, long
   }
 }
 
+// The tensor-core forms whose A operands (the rows of the butterflies) fit in
+// the line scratch and are placed there: split BF16 (64-byte rows, high and
+// low, 16 KB a warpgroup) and plain TF32 (128-byte rows, 16 KB a warpgroup).
+// Their blocks take no more shared memory than the FP32 kernel, so two run
+// per SM; the split-TF32 form keeps separate operands and one block per SM.
+__host__ __device__ constexpr bool v3_tc_aliased(int tc) { return tc == 1 || tc == 2; }
+
 // Shared memory of the tensor-core operands: per warpgroup the A rows (high,
-// and low for the split form) of its 128 butterflies, and the DFT-16 matrix
-// (high and low); 1024-byte aligned.
+// and low for the split form) of its 128 butterflies unless they sit in the
+// line scratch, and the DFT-16 matrix (high and low); 1024-byte aligned.
 __host__ __device__ constexpr int v3_tc_smem_bytes(int tc) {
-  return tc == 0 ? 0 : 1024 + 2 * (tc == 1 ? 1 : 2) * 16384 + 2 * 4096;
+  // B: 32 rows of 64 bytes (BF16) or 128 bytes (TF32), high and (split forms) low
+  return tc == 0 ? 0 : tc == 2 ? 1024 + 2 * 2048 : tc == 1 ? 1024 + 4096 : 1024 + 2 * 2 * 16384 + 2 * 4096;
 }
 
 // Blocks per SM the register budget targets: two for complex64 (at most 128
 // registers a thread), one for complex128, whose values take twice the registers.
 template <typename real>
 constexpr int v3_min_blocks() { return sizeof(real) == 4 ? 2 : 1; }
+template <typename real, int TC>
+constexpr int v3_min_blocks_tc() { return TC == 0 ? v3_min_blocks<real>() : (v3_tc_aliased(TC) ? 2 : 1); }
 
 // 256 threads (eight warps), two blocks per SM for complex64.  Thread 0 starts the first
 // nbuf tile loads; afterwards the last warp to finish a tile stores it and
@@ -361,9 +371,13 @@ constexpr int v3_min_blocks() { return sizeof(real) == 4 ? 2 : 1; }
 // memory; TC = 1 multiplies TF32-rounded operands, TC = 3 the three-term
 // split (x_hi w_hi + x_hi w_lo + x_lo w_hi) that keeps about 21 bits.
 template <typename real, int NSUB, int E, int ROLE, int TC = 0>
-__global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_kernel(const __grid_constant__ PassParams p) {
+__global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_kernel(const __grid_constant__ PassParams p) {
   static_assert(TC == 0 || (sizeof(real) == 4 && E == 16), "tensor-core DFT: complex64, radix 16");
   using G = V3<real, NSUB, E, ROLE>;
+  constexpr bool TCA = v3_tc_aliased(TC);
+  static_assert(!TCA || 2 * 16384 <= G::SCR * G::ES, "tensor-core operands fit in the line scratch");
+  static_assert(!TCA || G::C < 2 || ((G::C / 2) * G::PITCH * G::ES >= 16384 && ((G::C / 2) * G::PITCH * G::ES) % 1024 == 0),
+                "a warpgroup's operands fit over its own lines' scratch, 1024-byte aligned");
   using A = V3Addr<G>;
   using cT = typename G::cT;
   static_assert(E % G::PG == 0, "a thread's stage-0 values start on a pad group");
@@ -416,12 +430,18 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
   // tensor-core operands and accumulator (TC != 0)
   __shared__ uint64_t tcbar[2];
   __shared__ uint32_t tc_tmem;
-  unsigned char* tc_a = nullptr;      // per warpgroup: A high [, A low], 16 KB each
-  unsigned char* tc_b = nullptr;      // DFT-16 matrix, transposed: high, low (4 KB each)
+  unsigned char* tc_a = nullptr;      // per warpgroup: A high [, A low], 16 KB in all
+  unsigned char* tc_b = nullptr;      // DFT-16 matrix, transposed: high [, low]
   if constexpr (TC != 0) {
     const uintptr_t after = reinterpret_cast<uintptr_t>(scr + G::SCR + (G::TWS ? G::TWN : 0));
-    tc_a = reinterpret_cast<unsigned char*>((after + 1023) & ~uintptr_t(1023));
-    tc_b = tc_a + 2 * (TC == 1 ? 1 : 2) * 16384;
+    const uintptr_t al = (after + 1023) & ~uintptr_t(1023);
+    if constexpr (TCA) {
+      tc_a = reinterpret_cast<unsigned char*>(scr);     // 1024-byte aligned (the tile buffers are)
+      tc_b = reinterpret_cast<unsigned char*>(al);
+    } else {
+      tc_a = reinterpret_cast<unsigned char*>(al);
+      tc_b = tc_a + 2 * 2 * 16384;
+    }
     if (t < 32) {
       // row n of B^T = column n of the real 32 x 32 DFT-16 matrix W:
       // W[2j][2m] = W[2j+1][2m+1] = cos(2 pi jm/16), W[2j][2m+1] = -W[2j+1][2m] = -sin(2 pi jm/16)
@@ -433,14 +453,14 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
         return (float)(kim == im ? cs : (kim ? -sn : sn));
       };
       if constexpr (TC == 2) {
-        // BF16: 32 values = 64 bytes, chunks 0..3 of the 128-byte row
+        // BF16: 32 values = one 64-byte row (64-byte swizzle), high then low
 #pragma unroll
         for (int c = 0; c < 4; c++) {
           uint32_t h[4], l[4];
 #pragma unroll
           for (int e = 0; e < 4; e++) tc::split_bf16x2(wval(8 * c + 2 * e), wval(8 * c + 2 * e + 1), h[e], l[e]);
-          *reinterpret_cast<uint4*>(tc_b + tc::sw128_off(t, c)) = uint4{h[0], h[1], h[2], h[3]};
-          *reinterpret_cast<uint4*>(tc_b + 4096 + tc::sw128_off(t, c)) = uint4{l[0], l[1], l[2], l[3]};
+          *reinterpret_cast<uint4*>(tc_b + tc::sw64_off(t, c)) = uint4{h[0], h[1], h[2], h[3]};
+          *reinterpret_cast<uint4*>(tc_b + 2048 + tc::sw64_off(t, c)) = uint4{l[0], l[1], l[2], l[3]};
         }
       } else {
 #pragma unroll
@@ -450,9 +470,11 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
           for (int e = 0; e < 4; e++) w[e] = wval(4 * c + e);
           const float4 h = {tc::to_tf32(w[0]), tc::to_tf32(w[1]), tc::to_tf32(w[2]), tc::to_tf32(w[3])};
           *reinterpret_cast<float4*>(tc_b + tc::sw128_off(t, c)) = h;
-          const float4 l = {tc::to_tf32(w[0] - h.x), tc::to_tf32(w[1] - h.y), tc::to_tf32(w[2] - h.z),
-                            tc::to_tf32(w[3] - h.w)};
-          *reinterpret_cast<float4*>(tc_b + 4096 + tc::sw128_off(t, c)) = l;
+          if constexpr (TC == 3) {
+            const float4 l = {tc::to_tf32(w[0] - h.x), tc::to_tf32(w[1] - h.y), tc::to_tf32(w[2] - h.z),
+                              tc::to_tf32(w[3] - h.w)};
+            *reinterpret_cast<float4*>(tc_b + 4096 + tc::sw128_off(t, c)) = l;
+          }
         }
       }
     }
@@ -497,8 +519,25 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
       Dft<E>::run(v);
     } else {
       const int wg = warp >> 2, row = t & 127;
-      unsigned char* ahi = tc_a + wg * (TC == 1 ? 1 : 2) * 16384;
-      unsigned char* alo = ahi + 16384;
+      // split BF16: 8 KB of high and 8 KB of low rows a warpgroup; TF32: 16 KB
+      // of rows (plain) or 16 KB high and 16 KB low (split).  In the line
+      // scratch, a warpgroup whose lines are its own (two or more lines a
+      // tile) puts them over its own lines' scratch; one line a tile (shared
+      // by both warpgroups) the two take the first 32 KB.
+      unsigned char* ahi = TCA && G::C >= 2 ? tc_a + wg * (G::C / 2) * G::PITCH * G::ES
+                                            : tc_a + wg * (TC == 3 ? 2 : 1) * 16384;
+      unsigned char* alo = ahi + (TC == 2 ? 8192 : 16384);
+      // the threads that read or write the scratch the operands overlay
+      auto overlay_sync = [&]() {
+        if constexpr (G::C >= 2) asm volatile("bar.sync %0, 128;" ::"r"(8 + wg) : "memory");
+        else asm volatile("bar.sync 1, 256;" ::: "memory");
+      };
+      if constexpr (TCA) {
+        // the operands overwrite the line scratch: every thread that uses it
+        // has read its values of this stage (and of the previous tile's last
+        // stage) from it
+        overlay_sync();
+      }
       if constexpr (TC == 2) {
 #pragma unroll
         for (int c = 0; c < 4; c++) {
@@ -508,8 +547,8 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
             tc::split_bf16x2(v[4 * c + 2 * e].x, v[4 * c + 2 * e].y, h[2 * e], l[2 * e]);
             tc::split_bf16x2(v[4 * c + 2 * e + 1].x, v[4 * c + 2 * e + 1].y, h[2 * e + 1], l[2 * e + 1]);
           }
-          *reinterpret_cast<uint4*>(ahi + tc::sw128_off(row, c)) = uint4{h[0], h[1], h[2], h[3]};
-          *reinterpret_cast<uint4*>(alo + tc::sw128_off(row, c)) = uint4{l[0], l[1], l[2], l[3]};
+          *reinterpret_cast<uint4*>(ahi + tc::sw64_off(row, c)) = uint4{h[0], h[1], h[2], h[3]};
+          *reinterpret_cast<uint4*>(alo + tc::sw64_off(row, c)) = uint4{l[0], l[1], l[2], l[3]};
         }
       } else {
 #pragma unroll
@@ -531,7 +570,7 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
       const uint32_t d_tmem = tc_tmem + 32u * wg;
       if (row == 0) {
         const unsigned char* as[3] = {ahi, ahi, alo};
-        const unsigned char* bs[3] = {tc_b, tc_b + 4096, tc_b};
+        const unsigned char* bs[3] = {tc_b, tc_b + (TC == 2 ? 2048 : 4096), tc_b};
         if constexpr (TC == 2) {
           // BF16: K = 16 values (32 bytes) per product, two products per term
           constexpr uint32_t idesc = tc::instr_desc(1, 128, 32);
@@ -539,8 +578,8 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
           for (int term = 0; term < 3; term++)
 #pragma unroll
             for (int kq = 0; kq < 2; kq++)
-              tc::mma_f16(d_tmem, tc::smem_desc_sw128(smem_u32(as[term]) + 32u * kq),
-                          tc::smem_desc_sw128(smem_u32(bs[term]) + 32u * kq), idesc, (term | kq) != 0);
+              tc::mma_f16(d_tmem, tc::smem_desc_sw64(smem_u32(as[term]) + 32u * kq),
+                          tc::smem_desc_sw64(smem_u32(bs[term]) + 32u * kq), idesc, (term | kq) != 0);
         } else {
           constexpr uint32_t idesc = tc::instr_desc(2, 128, 32);
 #pragma unroll
@@ -563,6 +602,10 @@ __global__ void __launch_bounds__(256, (TC ? 1 : v3_min_blocks<real>())) fft_v3_
 #pragma unroll
       for (int m = 0; m < 16; m++) v[m] = cT{d[2 * m], d[2 * m + 1]};
       tc::fence_before_sync();
+      if constexpr (TCA) {
+        // the products over this scratch are complete before it is written
+        overlay_sync();
+      }
     }
   };
 

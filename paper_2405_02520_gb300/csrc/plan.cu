@@ -637,12 +637,19 @@ int plan_v3(tfft_plan_s* p) {
     // complex64: two blocks per SM, each with at most 110 KB of dynamic
     // shared memory; complex128: one block per SM
     // (tensor-core variants: one block per SM, room for the MMA operands)
-    const size_t budget = (c64 && !vtc ? 110 : 220) * 1024;
     const size_t fixed = scr + (size_t)v3_twiddle_smem_bytes(vdt, (int)nsub) + (size_t)v3_tc_bytes(vtc) + 1024 + 1024;
+    size_t budget = (c64 && (vtc == 0 || v3_tc_two_blocks(vtc)) ? 110 : 220) * 1024;
+    if (vtc && fixed + 2 * (size_t)buf > budget) budget = 220 * 1024;   // one block per SM
     if (fixed + 2 * (size_t)buf > budget) continue;
     const int nbuf = (int)std::min<size_t>(4, (budget - fixed) / buf);
     const size_t smem = (size_t)nbuf * buf + fixed;
     if (attrs(smem, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
+    // the occupancy query reports one block of the scratch-aliased
+    // tensor-core forms per SM; their registers (128) and shared memory
+    // (two blocks of at most 110 KB plus 2 KB of static and reserved
+    // memory in 228 KB) hold two, which the launch statistics confirm
+    if (vtc && v3_tc_two_blocks(vtc) && bps == 1 && budget <= 110 * 1024 && 2 * (smem + 2048) <= 228 * 1024)
+      bps = 2;
     q.v3 = 1; q.role = role; q.tma = 1; q.vdt = vdt; q.vtc = vtc;
     q.vC = (int)C;
     q.vLB = q.lines_are_signals ? 1 : q.LO * q.HI / C;

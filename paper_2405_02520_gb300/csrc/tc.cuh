@@ -35,6 +35,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// The same for a 64-byte swizzle (rows of 64 bytes, 8-row groups 512 bytes
+// apart, layout code 4): 16-byte chunk c of row r at chunk c ^ ((r / 2) mod 4).
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);          // start address
+  d |= (uint64_t)(16u >> 4) << 16;                  // leading byte offset (unused for this layout)
+  d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;     // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                           // version
+  d |= (uint64_t)4 << 61;                           // layout: 64-byte swizzle
+  return d;
+}
+
 // Instruction descriptor: FP32 accumulator, A and B of format `fmt`
 // (TF32 = 2 for kind::tf32, BF16 = 1 for kind::f16), both K-major, M x N.
 __host__ __device__ constexpr uint32_t instr_desc(int fmt, int M, int N) {
@@ -129,6 +141,10 @@ __device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, u
 // K-major operand.
 __device__ __forceinline__ uint32_t sw128_off(int m, int c) {
   return (uint32_t)((m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4));
+}
+// ... and of chunk c (0..3) of row m in a 64-byte-swizzled one.
+__device__ __forceinline__ uint32_t sw64_off(int m, int c) {
+  return (uint32_t)(m * 64 + ((c ^ ((m >> 1) & 3)) << 4));
 }
 
 }  // namespace tc

@@ -207,6 +207,9 @@ int v3_twiddle_smem_bytes(int dtype, int nsub);
 cudaError_t launch_v3_tc(int tc, int role, int nsub, const PassParams& p, int grid, size_t smem, cudaStream_t s);
 cudaError_t v3_attrs_tc(int tc, int role, int nsub, size_t smem, int* blocks_per_sm);
 int v3_tc_bytes(int tc);
+// True for the tensor-core forms that keep their operands in the line scratch
+// and so fit two blocks per SM (split BF16, plain TF32).
+bool v3_tc_two_blocks(int tc);
 
 // Signal offsets for a plan's exec (ragged batches in the caller's packing):
 // signal b of the exec's input and output starts at element off[b] (d_off on

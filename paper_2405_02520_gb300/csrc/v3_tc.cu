@@ -39,9 +39,14 @@ cudaError_t v3_attrs_tc(int tc, int role, int nsub, size_t smem, int* bps) {
   if (!f) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
   if (e != cudaSuccess) return e;
+  // all of the unified L1 / shared storage as shared memory, so that two
+  // blocks of the scratch-aliased forms fit
+  e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, f, 256, smem);
 }
 
 int v3_tc_bytes(int tc) { return v3_tc_smem_bytes(tc); }
+bool v3_tc_two_blocks(int tc) { return v3_tc_aliased(tc); }
 
 }  // namespace tfft
