@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
   static_assert(TC == 0 || (sizeof(real) == 4 && E == 16), "tensor-core DFT: complex64, radix 16");
   using G = V3<real, NSUB, E, ROLE>;
   constexpr bool TCA = v3_tc_aliased(TC);
+  constexpr bool BOXA = TCA && ROLE == V3_SINGLE && G::C == 1;
   static_assert(!TCA || 2 * 16384 <= G::SCR * G::ES, "tensor-core operands fit in the line scratch");
   static_assert(!TCA || G::C < 2 || ((G::C / 2) * G::PITCH * G::ES >= 16384 && ((G::C / 2) * G::PITCH * G::ES) % 1024 == 0),
                 "a warpgroup's operands fit over its own lines' scratch, 1024-byte aligned");
@@ -514,7 +515,9 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
 
   // The radix-16 DFT of this thread's 16 values: register butterflies, or
   // this thread's row of its warpgroup's tensor-core product.
-  auto dft16 = [&](cT* v) {
+  // kind: 0 the first stage, 1 a middle stage (its reads ended by a line
+  // barrier), 2 the last stage; box: the current tile's buffer
+  auto dft16 = [&](cT* v, int kind, unsigned char* box) {
     if constexpr (TC == 0) {
       Dft<E>::run(v);
     } else {
@@ -524,8 +527,13 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
       // scratch, a warpgroup whose lines are its own (two or more lines a
       // tile) puts them over its own lines' scratch; one line a tile (shared
       // by both warpgroups) the two take the first 32 KB.
+      // A single-pass tile of one line: after the first stage has read the
+      // tile's buffer, the later stages put their operands there (the
+      // output is written to it only after the last product), which spares
+      // the barriers around the line scratch.
+      const bool in_box = BOXA && kind != 0;
       unsigned char* ahi = TCA && G::C >= 2 ? tc_a + wg * (G::C / 2) * G::PITCH * G::ES
-                                            : tc_a + wg * (TC == 3 ? 2 : 1) * 16384;
+                                            : (in_box ? box : tc_a) + wg * (TC == 3 ? 2 : 1) * 16384;
       unsigned char* alo = ahi + (TC == 2 ? 8192 : 16384);
       // the threads that read or write the scratch the operands overlay
       auto overlay_sync = [&]() {
@@ -536,7 +544,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
         // the operands overwrite the line scratch: every thread that uses it
         // has read its values of this stage (and of the previous tile's last
         // stage) from it
-        overlay_sync();
+        if (!in_box) overlay_sync();
       }
       if constexpr (TC == 2) {
 #pragma unroll
@@ -603,8 +611,9 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
       for (int m = 0; m < 16; m++) v[m] = cT{d[2 * m], d[2 * m + 1]};
       tc::fence_before_sync();
       if constexpr (TCA) {
-        // the products over this scratch are complete before it is written
-        overlay_sync();
+        // the products over this scratch (or over the tile buffer, before the
+        // last stage writes the output there) are complete before it is written
+        if (!in_box || kind == 2) overlay_sync();
       }
     }
   };
@@ -772,7 +781,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
       // butterfly u of stage 0 takes v[u + m BPT0] (inputs j0 + u TPL + m NSUB / R0)
       // and writes its output q to position (j0 + u TPL) R0 + q
       if constexpr (G::R0 == E) {
-        dft16(v);
+        dft16(v, 0, tile);
       } else {
 #pragma unroll
         for (int u = 0; u < G::BPT0; u++) {
@@ -816,7 +825,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
 #pragma unroll
           for (int q = 1; q < E; q++) v[q] = c_mul(v[q], G::TWS ? tw[(q - 1) * Ns] : ldg_c(tw + (q - 1) * Ns));
         }
-        dft16(v);
+        dft16(v, 1, tile);
         const int basei = (j0 / Ns) * Ns * E + kk;
         if (fst == st) {
 #pragma unroll
@@ -838,7 +847,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
 #pragma unroll
         for (int q = 1; q < E; q++) v[q] = c_mul(v[q], G::TWS ? tw[(q - 1) * G::TPL] : ldg_c(tw + (q - 1) * G::TPL));
       }
-      dft16(v);
+      dft16(v, 2, tile);
       if (ROLE == V3_COLS && p.twiddle) {
         cT f = tw_base;
 #pragma unroll
