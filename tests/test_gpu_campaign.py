@@ -7,8 +7,10 @@ from tests.campaign import clean_campaign, run_campaign
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("log2n,batch,dtype", [(10, 64, t.TFFT_C64), (13, 32, t.TFFT_C64),
-                                               (16, 8, t.TFFT_C64), (20, 4, t.TFFT_C64),
+@pytest.mark.parametrize("log2n,batch,dtype", [(8, 64, t.TFFT_C64), (10, 64, t.TFFT_C64),
+                                               (12, 32, t.TFFT_C64), (13, 32, t.TFFT_C64),
+                                               (16, 8, t.TFFT_C64), (18, 4, t.TFFT_C64),
+                                               (19, 4, t.TFFT_C64), (20, 4, t.TFFT_C64),
                                                (12, 32, t.TFFT_C128)])
 def test_every_harmful_bitflip_detected_and_corrected(log2n, batch, dtype):
     r = run_campaign(1 << log2n, batch, dtype, faults=60, seed=log2n)
