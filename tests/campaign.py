@@ -52,6 +52,7 @@ def run_campaign(n, batch, dtype=t.TFFT_C64, faults=100, seed=0, bits=None, kapp
            "kappa": info["kappa"], "vector": "signed_wang" if vector == t.TFFT_R_SIGNED_WANG else "wang",
            "faults": 0, "harmful": 0, "harmful_detected": 0, "harmful_located": 0,
            "harmful_corrected": 0, "benign": 0, "benign_detected": 0, "benign_output_ok": 0,
+           "clear": 0, "clear_detected": 0, "clear_corrected": 0, "marginal": 0, "marginal_missed": 0,
            "missed": [], "by_stage": {}}
     tl = tol(n, dtype)
     for k in range(faults):
@@ -76,8 +77,16 @@ def run_campaign(n, batch, dtype=t.TFFT_C64, faults=100, seed=0, bits=None, kapp
             res[flag] = (yt.cpu().numpy(), det, ev[-1]["signal"] if det and ev else None)
         y_unc, det, loc = res[True]
         y_cor = res[False][0]
-        harmful = rel_rows(y_unc[sig:sig + 1], ref[sig:sig + 1])[0] > tl
+        err = rel_rows(y_unc[sig:sig + 1], ref[sig:sig + 1])[0]
+        harmful = err > tl
         ok = bool(np.all(rel_rows(y_cor, ref) <= tl))
+        if err > 2 * tl:                  # harmful by a margin
+            out["clear"] += 1
+            out["clear_detected"] += det
+            out["clear_corrected"] += ok
+        elif harmful:                     # within a factor of two of the tolerance
+            out["marginal"] += 1
+            out["marginal_missed"] += not det
         key = f"p{p}s{stage}"
         bs = out["by_stage"].setdefault(key, [0, 0])
         out["faults"] += 1
