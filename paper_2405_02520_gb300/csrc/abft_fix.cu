@@ -88,6 +88,9 @@ __device__ void decide_group(const VerifyParams& v, int64_t g, const GroupSums& 
       }
     }
   }
+  if ((action == 1 || action == 2) && v.cond_flag &&
+      atomicExch(reinterpret_cast<unsigned long long*>(v.cond_flag), 1ull) == 0ull)
+    cudaGraphSetConditional(v.cond, 1u);      // run the correction body of this exec's graph
   if (action == 1) atomicAdd(&v.counters->corrected, 1ull);
   else if (action == 2) atomicAdd(&v.counters->recomputed, 1ull);
   else atomicAdd(&v.counters->uncorrectable, 1ull);

@@ -355,6 +355,7 @@ fft_pass_kernel(const __grid_constant__ PassParams p) {
   if (blockIdx.x == 0 && t == 0) {
     if (p.zero_on_entry[0]) *p.zero_on_entry[0] = 0;
     if (p.zero_on_entry[1]) *p.zero_on_entry[1] = 0;
+    if (p.zero_on_entry[2]) *p.zero_on_entry[2] = 0;
   }
 
   // stage-0 butterfly of this thread (radix E, one per thread)

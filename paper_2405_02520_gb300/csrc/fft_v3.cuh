@@ -409,6 +409,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
     if (blockIdx.x == 0) {
       if (p.zero_on_entry[0]) *p.zero_on_entry[0] = 0;
       if (p.zero_on_entry[1]) *p.zero_on_entry[1] = 0;
+      if (p.zero_on_entry[2]) *p.zero_on_entry[2] = 0;
     }
   }
   __syncthreads();

@@ -167,6 +167,19 @@ struct tfft_plan_s {
   int64_t execs = 0, launches = 0;
   cudaStream_t last_stream = nullptr;
   bool used = false;
+  // correction graph: verification, then a conditional node whose body is the
+  // correction sequence; built for one (in, out) pair, replayed afterwards
+  long long* cond_flag = nullptr;
+  cudaStream_t gcap = nullptr;
+  cudaGraph_t cg = nullptr;
+  cudaGraphExec_t cgx = nullptr;
+  cudaGraphNode_t cg_vnode = nullptr;
+  cudaKernelNodeParams cg_kp{};
+  VerifyParams cg_v{};
+  int cg_lanes = 0;
+  const void* cg_in = nullptr;
+  void* cg_out = nullptr;
+  bool cg_off = false;              // building failed once: stream launches only
   // tfft_exec_host pipeline: copy streams and per-chunk events, made on first use
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t ev_entry = nullptr, ev_end = nullptr;
@@ -200,6 +213,9 @@ int upload(tfft_plan_s* p, void** dst, const std::vector<double>& re, const std:
 }
 
 void free_plan(tfft_plan_s* p) {
+  if (p->cgx) cudaGraphExecDestroy(p->cgx);
+  if (p->cg) cudaGraphDestroy(p->cg);
+  if (p->gcap) cudaStreamDestroy(p->gcap);
   for (cudaEvent_t e : p->ev_in) if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ev_done) if (e) cudaEventDestroy(e);
   if (p->ev_entry) cudaEventDestroy(p->ev_entry);
@@ -782,7 +798,7 @@ int plan_workspace(tfft_plan_s* p) {
     TFFT_CUDA(cudaMalloc(&p->tmp, rows * sig));
     p->workspace_bytes += rows * (int64_t)sig;
   }
-  const size_t nl = (size_t)(2 + p->cap_fix + p->cap_fix + p->cap_rec);
+  const size_t nl = (size_t)(3 + p->cap_fix + p->cap_fix + p->cap_rec);
   TFFT_CUDA(cudaMalloc(&p->lists_mem, nl * sizeof(long long)));
   TFFT_CUDA(cudaMemset(p->lists_mem, 0, nl * sizeof(long long)));
   p->lists.fix = p->lists_mem;
@@ -790,6 +806,7 @@ int plan_workspace(tfft_plan_s* p) {
   p->lists.rec = p->lists_mem + 1 + 2 * p->cap_fix;
   p->lists.cap_fix = p->cap_fix;
   p->lists.cap_rec = p->cap_rec;
+  p->cond_flag = p->lists_mem + nl - 1;
   TFFT_CUDA(cudaMalloc(&p->err_flag, sizeof(int)));
   TFFT_CUDA(cudaMemset(p->err_flag, 0, sizeof(int)));
   TFFT_CUDA(cudaMalloc(&p->counters, sizeof(Counters)));
@@ -960,7 +977,11 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
       a.fault = p->pending;
       for (int k = 0; k < 3; k++) a.fault_more[k] = p->pending_more[k];
       a.nfault = p->npending;
-      if (i == 0 && p->abft) { a.zero_on_entry[0] = p->lists.fix; a.zero_on_entry[1] = p->lists.rec; }
+      if (i == 0 && p->abft) {
+        a.zero_on_entry[0] = p->lists.fix;
+        a.zero_on_entry[1] = p->lists.rec;
+        a.zero_on_entry[2] = p->cond_flag;
+      }
     } else {
       a.list = list; a.list_identity = list_identity; a.list_cap = list_cap;
       a.list_block = list_block;
@@ -971,6 +992,99 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
     int rc = launch_pass(p, a, i, kind_override >= 0 ? kind_override : kind_of(p, i), s);
     if (rc) return rc;
   }
+  return 0;
+}
+
+// The correction sequence (Section III-B) on `s`: gather the queued groups'
+// input checksum and partial output sums, transform the checksums, apply;
+// then recompute the groups that could not be located.  Every launch returns
+// at once when its list is empty.
+int enqueue_correction(tfft_plan_s* p, const FixParams& f, const void* in, void* out, int64_t nb,
+                       cudaStream_t s) {
+  int rc;
+  if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_gather(f, s); }))) return rc;
+  // W X e_1 of every queued group, in place in ws_c1
+  if ((rc = run_passes(p, p->ws_c1, p->ws_c1, s, false, p->lists.fix, 1, p->cap_fix, 1,
+                       p->cap_fix, 5, false)))
+    return rc;
+  if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_apply(f, s); }))) return rc;
+  // groups that could not be located: recompute from the input
+  return run_passes(p, in, out, s, false, p->lists.rec, 0, p->cap_rec, p->vG, nb, 5);
+}
+
+// Builds the graph [verify] -> [if (a group was queued) { correction }] for
+// this (in, out): the verification kernel switches the conditional node on
+// (cudaGraphSetConditional) when it queues a group, so a clean exec runs one
+// graph launch after its passes instead of the five to nine launches of the
+// correction sequence.  Returns nonzero (and leaves no graph) on any failure.
+int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, const void* in, void* out) {
+  if (p->cgx) { cudaGraphExecDestroy(p->cgx); p->cgx = nullptr; }
+  if (p->cg) { cudaGraphDestroy(p->cg); p->cg = nullptr; }
+  if (!p->gcap && cudaStreamCreateWithFlags(&p->gcap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle h{};
+  cudaGraphNode_t nodes[2];
+  size_t count = 2;
+  cudaGraphNodeParams cp{};
+  cudaGraph_t body = nullptr, out_g = nullptr;
+  cudaGraphExec_t gx = nullptr;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok) {
+    v.cond_flag = p->cond_flag;
+    v.cond = h;
+    ok = cudaStreamBeginCaptureToGraph(p->gcap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+         cudaSuccess;
+    if (ok) {
+      const bool launched = launch_verify(v, p->gcap) == cudaSuccess;
+      ok = cudaStreamEndCapture(p->gcap, &out_g) == cudaSuccess && launched;
+    }
+  }
+  ok = ok && cudaGraphGetNodes(g, nodes, &count) == cudaSuccess && count == 1;
+  if (ok) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn;
+    ok = cudaGraphAddNode(&cn, g, &nodes[0], nullptr, 1, &cp) == cudaSuccess;
+  }
+  if (ok) {
+    body = cp.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(p->gcap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+         cudaSuccess;
+    if (ok) {
+      // captured, not run: keep the plan's launch count and timing records
+      const int64_t launches = p->launches;
+      const bool timing = p->timing;
+      p->timing = false;
+      const int rc = enqueue_correction(p, f, in, out, f.batch, p->gcap);
+      p->timing = timing;
+      p->launches = launches;
+      cudaGraph_t b2 = nullptr;
+      ok = cudaStreamEndCapture(p->gcap, &b2) == cudaSuccess && rc == 0;
+    }
+  }
+  cudaKernelNodeParams kp{};
+  ok = ok && cudaGraphKernelNodeGetParams(nodes[0], &kp) == cudaSuccess && kp.kernelParams;
+  ok = ok && cudaGraphInstantiate(&gx, g, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (gx) cudaGraphExecDestroy(gx);
+    if (g) cudaGraphDestroy(g);
+    return 1;
+  }
+  p->cg = g;
+  p->cgx = gx;
+  p->cg_vnode = nodes[0];
+  p->cg_kp = kp;
+  p->cg_v = v;
+  p->cg_lanes = *static_cast<int*>(kp.kernelParams[1]);
+  p->cg_in = in;
+  p->cg_out = out;
   return 0;
 }
 
@@ -1005,19 +1119,29 @@ int exec_range(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
     v.lists = p->lists; v.counters = p->counters; v.log = p->log; v.exec_index = p->execs;
     v.max_blocks = 8 * p->sms;
     v.split = p->vsplit; v.part_acc = p->part_acc; v.part_cnt = p->part_cnt;
-    if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
     FixParams f{};
     f.n = p->n; f.batch = nb; f.group = p->vG; f.dtype = p->dtype;
     f.in = in; f.out = out; f.soff = p->soff; f.ws_c1 = p->ws_c1; f.ws_acc = p->ws_acc; f.lists = p->lists;
-    if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_gather(f, s); }))) return rc;
-    // W X e_1 of every queued group, in place in ws_c1
-    if ((rc = run_passes(p, p->ws_c1, p->ws_c1, s, false, p->lists.fix, 1, p->cap_fix, 1,
-                         p->cap_fix, 5, false)))
-      return rc;
-    if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_apply(f, s); }))) return rc;
-    // groups that could not be located: recompute from the input
-    if ((rc = run_passes(p, in, out, s, false, p->lists.rec, 0, p->cap_rec, p->vG, nb, 5)))
-      return rc;
+    // a whole-batch exec on a stream that is not being captured:
+    // verification and correction from the graph (timed as one launch)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (b0 == 0 && nb == p->batch && !p->cg_off &&
+        cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      if ((!p->cgx || p->cg_in != in || p->cg_out != out) && build_correction_graph(p, v, f, in, out))
+        p->cg_off = true;
+      if (p->cgx) {
+        VerifyParams v2 = p->cg_v;
+        v2.exec_index = p->execs;
+        int lanes = p->cg_lanes;
+        void* args[2] = {&v2, &lanes};
+        cudaKernelNodeParams kp = p->cg_kp;
+        kp.kernelParams = args;
+        TFFT_CUDA(cudaGraphExecKernelNodeSetParams(p->cgx, p->cg_vnode, &kp));
+        return timed_launch(p, 4, s, [&] { return cudaGraphLaunch(p->cgx, s); });
+      }
+    }
+    if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
+    return enqueue_correction(p, f, in, out, nb, s);
   }
   return 0;
 }

@@ -160,7 +160,7 @@ struct PassParams {
   int rvec;               // RVec
   unsigned long long rseed;
   const void* wtab;       // w = W r, N entries (RVEC_SIGNED_WANG)
-  long long* zero_on_entry[2];   // list counts zeroed by block 0 (first pass of an exec)
+  long long* zero_on_entry[3];   // list counts and the correction flag, zeroed by block 0 (first pass of an exec)
 
   // ---- work list (correction path); list == nullptr for a normal exec ----
   const long long* list;  // list[0] = count, list[1 + e] = block (ignored if list_identity)
@@ -237,6 +237,11 @@ struct VerifyParams {
   LogEvent* log;
   long long exec_index;
   int max_blocks;               // grid cap (blocks stride over the groups)
+  // exec replayed from a CUDA graph: the correction work is the body of a
+  // conditional node, switched on (once, by the first thread that queues a
+  // group: *cond_flag guards the call) when a group needs it
+  long long* cond_flag;         // nullptr outside the graph
+  cudaGraphConditionalHandle cond;
   // groups with many records and few groups: `split` blocks per group add
   // their slice's sums into part_acc[g] (9 sums, then the nonfinite range as
   // integers) and count themselves in part_cnt[g]; the last one decides and
