@@ -157,7 +157,11 @@ int tfft_plan_ex(tfft_plan_t *out, const tfft_plan_opts *opts);
  * tfft_exec -- transform `batch` signals from device buffer `in` to device
  * buffer `out` (layout above, each plan->batch*n elements), asynchronously on
  * `stream`.  `in` is never written.  With ABFT on, `in` and `out` must not
- * overlap (TFFT_ERR_INPLACE).  No host synchronisation, no allocation.
+ * overlap (TFFT_ERR_INPLACE).  No host synchronisation.  When the same
+ * (in, out) pair comes back on a stream that is not being captured, the plan
+ * builds (once for that pair) a CUDA graph of the verification and the
+ * correction launches, the latter under a conditional node that runs only
+ * when a group was flagged; other execs launch them directly.
  * Returns TFFT_ERR_CUDA if a launch fails.
  */
 int tfft_exec(tfft_plan_t p, const void *in, void *out, tfft_stream_t stream);
