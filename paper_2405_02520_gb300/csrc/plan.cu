@@ -1127,8 +1127,12 @@ int exec_range(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
     // a whole-batch exec on a stream that is not being captured:
     // verification and correction from the graph (timed as one launch)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (b0 == 0 && nb == p->batch && !p->cg_off &&
-        cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+    bool capturing = true;
+    if (b0 == 0 && nb == p->batch && !p->cg_off) {
+      if (cudaStreamIsCapturing(s, &cs) == cudaSuccess) capturing = cs != cudaStreamCaptureStatusNone;
+      else cudaGetLastError();        // e.g. the legacy stream during another thread's global capture
+    }
+    if (b0 == 0 && nb == p->batch && !p->cg_off && !capturing) {
       // the graph is built when a pair of buffers comes back (an exec that
       // rotates over many buffers keeps the direct launches)
       const bool cached = p->cgx && p->cg_in == in && p->cg_out == out;
