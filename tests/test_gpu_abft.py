@@ -141,3 +141,43 @@ def test_no_false_positives_on_clean_launches(log2n, batch, launches):
         t.tfft_exec(plan, x, y, torch.cuda.current_stream())
     assert t.tfft_report(plan) == (0, 0)
     t.tfft_destroy(plan)
+
+
+@pytest.mark.parametrize("log2n,batch", [(10, 64), (16, 20)])
+def test_correction_graph_replayed_with_faults(log2n, batch):
+    """The same buffers exec'd again and again (verification and correction
+    replayed from the plan's graph): clean execs stay clean, a located fault
+    is corrected through the graph's conditional body, two faults in one
+    group are recomputed through it, and later clean execs are clean."""
+    import torch
+    n = 1 << log2n
+    x = uniform_batch(n, batch, seed=5100 + log2n)
+    ref = oracle_fft(x)
+    plan = t.tfft_plan(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED)
+    info = t.tfft_plan_info(plan)
+    xt = torch.from_numpy(x).cuda()
+    yt = torch.empty_like(xt)
+    s = torch.cuda.current_stream()
+
+    def run():
+        t.tfft_exec(plan, xt, yt, s)
+        torch.cuda.synchronize()
+        assert rel_err_rows(yt.cpu().numpy(), ref).max() <= tol(n, t.TFFT_C64)
+
+    for _ in range(3):
+        run()
+    assert t.tfft_report(plan) == (0, 0)
+    p = info["passes"] - 1
+    t.tfft_set_fault(plan, mode=t.TFFT_FAULT_SCALE, pass_=p, stage=info["stages"][p] - 1, signal=batch - 5,
+                     line=0, index=7, factor=1.5)
+    run()
+    assert t.tfft_report(plan) == (1, 1)
+    t.tfft_set_fault(plan, mode=t.TFFT_FAULT_ADD_PAIR, pass_=p, stage=info["stages"][p] - 1, signal=3, line=0,
+                     index=5, factor=3.0)
+    run()
+    st = t.tfft_report_ex(plan)
+    assert st["detected"] == 2 and st["corrected"] == 1 and st["recomputed"] == 1, st
+    for _ in range(2):
+        run()
+    assert t.tfft_report_ex(plan)["detected"] == 2
+    t.tfft_destroy(plan)
