@@ -283,39 +283,22 @@ struct V3Addr {
   }
 };
 
-// Copies a finished tile (or rows [r_begin, r_end) of an element-major box)
-// from its shared-memory box to the output, one warp, 16 bytes a lane per
-// access.  The box is laid out as the TMA would store it:
-// line-major (single pass: the tile's signals are contiguous in memory), or
-// element-major rows of ROWB bytes in column groups of CS lines with the TMA
-// swizzle (column and last passes: row i of group gx holds element i of lines
-// lo0 + gx CS .. + CS - 1, which are adjacent in memory).  Plain loads and
-// stores leave nothing in flight that still reads the box, so the buffer can be
-// refilled right after.
+// Copies rows [r_begin, r_end) of a finished last-pass tile from its
+// shared-memory box to the output, one warp, 16 bytes a lane per access.  The
+// box is laid out as the TMA would store it: element-major rows of ROWB bytes
+// in column groups of CS lines with the TMA swizzle (row i of group gx holds
+// element i of lines lo0 + gx CS .. + CS - 1, which are adjacent in memory).
+// Plain loads and stores leave nothing in flight that still reads the box, so
+// the buffer can be refilled right after.  (The single and column passes
+// store their tiles by TMA.)
 template <typename G, int ROLE>
 __device__ __forceinline__ void copy_out(const PassParams& p, long long tb, long long se, long long hi,
                                          long long lo0, const unsigned char* tile, int lane, int r_begin = 0,
                                          int r_end = G::NSUBV) {
-  using cT = typename G::cT;
+  static_assert(ROLE == V3_LAST, "the last pass copies its tiles out");
+  (void)se;
   unsigned char* out = reinterpret_cast<unsigned char*>(p.out);
-  if constexpr (ROLE == V3_SINGLE) {
-    const long long rows = min((long long)G::C, se - tb);
-    const int chunks = (int)(rows * (G::NSUBV * G::ES / 16));
-    unsigned char* dst = out + tb * p.n * G::ES;    // never called with signal offsets
-    int i = lane;
-    for (; i + 96 < chunks; i += 128) {
-      const float4 a = *reinterpret_cast<const float4*>(tile + 16 * i);
-      const float4 b = *reinterpret_cast<const float4*>(tile + 16 * (i + 32));
-      const float4 c = *reinterpret_cast<const float4*>(tile + 16 * (i + 64));
-      const float4 d = *reinterpret_cast<const float4*>(tile + 16 * (i + 96));
-      __stcs(reinterpret_cast<float4*>(dst + 16 * i), a);
-      __stcs(reinterpret_cast<float4*>(dst + 16 * (i + 32)), b);
-      __stcs(reinterpret_cast<float4*>(dst + 16 * (i + 64)), c);
-      __stcs(reinterpret_cast<float4*>(dst + 16 * (i + 96)), d);
-    }
-    for (; i < chunks; i += 32)
-      __stcs(reinterpret_cast<float4*>(dst + 16 * i), *reinterpret_cast<const float4*>(tile + 16 * i));
-  } else {
+  {
     constexpr int CPR = G::ROWB / 16;           // 16-byte chunks per box row
     constexpr int RPI = 32 / CPR;               // rows per warp access
     static_assert(G::ROWB % 16 == 0 && CPR <= 32, "box rows are whole 16-byte chunks");

@@ -652,9 +652,10 @@ int plan_v3(tfft_plan_s* p) {
     mi.bytes = mo.bytes = (unsigned)(C * nsub * es);
     const size_t scr = (size_t)v3_scratch_bytes(vdt, (int)nsub);
     const unsigned buf = (unsigned)((C * nsub * es + 1023) / 1024 * 1024);
-    // complex64: two blocks per SM, each with at most 110 KB of dynamic
-    // shared memory; complex128: one block per SM
-    // (tensor-core variants: one block per SM, room for the MMA operands)
+    // complex64 (and the tensor-core forms whose operands sit in the line
+    // scratch): two blocks per SM, each with at most 110 KB of dynamic
+    // shared memory; complex128 and the split-TF32 form (separate operands):
+    // one block per SM
     const size_t fixed = scr + (size_t)v3_twiddle_smem_bytes(vdt, (int)nsub) + (size_t)v3_tc_bytes(vtc) + 1024 + 1024;
     size_t budget = (c64 && (vtc == 0 || v3_tc_two_blocks(vtc)) ? 110 : 220) * 1024;
     if (vtc && fixed + 2 * (size_t)buf > budget) budget = 220 * 1024;   // one block per SM
