@@ -1,0 +1,54 @@
+"""Host-side helpers of bench.py on CPU: the ragged fault sites (one per 1000
+signals, distinct checksum groups, at most four per length and one below 256
+points), the one-N-per-step cycle of the reference arm, the oracle process
+pool, and the recorded DRAM traffic lookup."""
+import json
+import os
+
+import numpy as np
+
+import bench
+
+
+def test_ragged_fault_sites_distinct_groups():
+    rng = np.random.default_rng(5)
+    lengths = (1 << rng.integers(6, 17, size=20000)).astype(np.int64)
+    sites = bench.ragged_fault_sites(lengths, 1, seed=5)
+    assert len(sites) == 20
+    local, counts = {}, {}
+    for i, n in enumerate(lengths):
+        local[i] = counts.get(int(n), 0)
+        counts[int(n)] = local[i] + 1
+    groups = {(int(lengths[i]), local[i] // 16) for i in sites}
+    assert len(groups) == len(sites)                  # one fault per checksum group
+    per_len = {}
+    for i in sites:
+        per_len[int(lengths[i])] = per_len.get(int(lengths[i]), 0) + 1
+    assert all(c <= (1 if n < 256 else 4) for n, c in per_len.items())
+
+
+def test_oracle_pool_runs_one_sample_per_process():
+    pool = bench.OraclePool(2)
+    try:
+        f, s, desc = pool.sample(1 << 10, sweep=[8, 10])
+    finally:
+        pool.close()
+    # each process transforms 4 signals of 256 and 1 of 1024 points
+    assert f == 2 * (bench.flops(256, 4) + bench.flops(1024, 1))
+    assert s > 0 and "2 processes" in desc
+
+
+def test_recorded_traffic_follows_the_source_hash(tmp_path, monkeypatch):
+    rec = {"kernel_source_hash": bench.kernel_source_hash(), "bytes_per_launch": {"first_pass": 123}}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: rec["kernel_source_hash"])
+    assert bench.recorded_traffic("first_pass") == 123
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "changed")
+    assert bench.recorded_traffic("first_pass") is None
+
+
+def test_host_cores_positive():
+    assert bench.host_cores() >= 1
+    assert bench.host_cores() <= (os.cpu_count() or 1)
