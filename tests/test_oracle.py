@@ -327,3 +327,29 @@ def test_dft_bins_matches_definition_and_fft():
             assert np.max(np.abs(got - ref[ks])) <= 1e-12 * max(scale, 1e-300) * max(1, np.log2(n))
         y = oracle.fft(x[None, :])[0]
         assert np.allclose(oracle.dft_bins(x, ks), y[ks], rtol=0, atol=1e-11 * np.linalg.norm(y))
+
+
+def test_late_butterfly_fault_projection_is_rarely_small():
+    """Reading 5 (marginal faults): a fault in the last radix-16 butterfly of a
+    signal changes 16 outputs k0 + q N/16 by delta w16^(q m); the checksum sees
+    it through sum_q r_k delta w16^(q m), a sum of 16 random phases for the
+    signed e_Wang vector.  Its magnitude relative to the fault's norm
+    (4 |delta|) is Rayleigh-like: below 0.14 a few percent of the time (the
+    threshold-to-norm ratio of a fault 1.04x the tolerance at N = 2^18), so
+    such a fault can hide under the rounding noise, while below 0.01 almost
+    never."""
+    n = 1 << 14
+    r, _ = abft.vectors(n, "signed_wang", seed=20240502)
+    rng = np.random.default_rng(7)
+    q = np.arange(16)
+    ratios = []
+    for _ in range(4000):
+        k0 = int(rng.integers(n // 16))
+        m = int(rng.integers(16))
+        pattern = np.exp(-2j * np.pi * q * m / 16)
+        proj = abs(np.sum(r[k0 + q * (n // 16)] * pattern))
+        ratios.append(proj / 4.0)
+    ratios = np.array(ratios)
+    assert 0.005 < np.mean(ratios < 0.14) < 0.05
+    assert np.mean(ratios < 0.01) < 0.002
+    assert 0.8 < np.mean(ratios ** 2) < 1.2          # unit mean square: no systematic cancellation
