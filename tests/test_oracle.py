@@ -353,3 +353,24 @@ def test_late_butterfly_fault_projection_is_rarely_small():
     assert 0.005 < np.mean(ratios < 0.14) < 0.05
     assert np.mean(ratios < 0.01) < 0.002
     assert 0.8 < np.mean(ratios ** 2) < 1.2          # unit mean square: no systematic cancellation
+
+
+@pytest.mark.parametrize("n", [256, 4096])
+def test_threshold_sits_above_fp32_rounding_noise(n):
+    """Reading 4 (threshold): with kappa = 2, the residual |T1 - S1| of clean
+    groups whose outputs carry FP32 rounding (the oracle's own FP32 radix-2
+    emulation, a different operation order from any GPU kernel) stays well
+    below tau = kappa u (log2 N + 4) sqrt(N) sqrt(E), over 40 groups of 16
+    U[-1,1) signals."""
+    rng = np.random.default_rng(11)
+    r, w = abft.vectors(n, "signed_wang", seed=20240502)
+    ratios = []
+    for _ in range(40):
+        xg = (rng.uniform(-1, 1, (16, n)) + 1j * rng.uniform(-1, 1, (16, n))).astype(np.complex64)
+        yg = np.stack([oracle.fft_faulty(xg[b], 32) for b in range(16)])
+        cs = abft.group_checksums(xg.astype(np.complex128), yg, w=w, r=r)
+        v = abft.verify_group(cs, n, 16, 2.0 ** -24, 2.0)
+        assert not v.detected
+        ratios.append(v.residual / v.tau)
+    assert max(ratios) < 0.6
+    assert np.median(ratios) > 1e-3        # the residual is rounding noise, not exactly zero
