@@ -140,6 +140,13 @@ typedef struct tfft_plan_opts {
                            other n return TFFT_ERR_UNSUPPORTED.  The detection
                            threshold uses the form's unit roundoff (2^-20,
                            2^-10 and 2^-17 in place of 2^-24).               */
+    int wait_polls;     /* polls of a kernel's wait for a tile copy before it
+                           gives up (the bounded waits of the TMA pipeline):
+                           0 the default 2^20 (about a second), k > 0 that
+                           many, -1 none at all -- every such wait gives up at
+                           once, the exec's output is not valid and
+                           tfft_report returns TFFT_ERR_TIMEOUT; for testing
+                           the timeout path                                   */
 } tfft_plan_opts;
 
 enum tfft_precision { TFFT_PREC_FP32 = 0, TFFT_PREC_TF32X3 = 1, TFFT_PREC_TF32 = 2, TFFT_PREC_BF16X3 = 3 };
@@ -203,6 +210,8 @@ typedef struct tfft_stats {
 } tfft_stats;
 
 int tfft_report_ex(tfft_plan_t p, tfft_stats *stats);
+/* Zeroes the counters and the fault log count, and clears a recorded
+ * timeout (TFFT_ERR_TIMEOUT).  Synchronises the plan's last stream. */
 int tfft_reset_counters(tfft_plan_t p);
 
 /* One detection, as logged on the device (ring of 1024 entries). */
@@ -302,20 +311,25 @@ int tfft_destroy(tfft_plan_t p);
  * complex64 signals of length `n` from device buffer `in` to device buffer
  * `out` (layout above; in == out is allowed), asynchronously on `stream`,
  * without any allocation.  The paper has no counterpart: this is for callers
- * that may not allocate device memory -- code inside a CUDA-graph capture
- * that must not record allocation nodes, code under a memory manager or
+ * that may not allocate device memory -- code under a memory manager or
  * sandbox that owns every device allocation, real-time loops that may not
  * block on the allocator -- and therefore cannot create a plan.
  *
  * Limits: n a power of two with 8192 <= n <= 2^18 (the two-pass range) and
  * batch * n <= 2^23 (the 64 MiB scratch); anything else returns
  * TFFT_ERR_INVALID_ARG before any work.  The inter-pass buffer and the
- * twiddle tables are file-scope __device__ arrays that every GPU loading the
- * library holds until the process exits; no cudaMalloc, cudaFree or other
- * allocating call is made.  The first call on a device looks up the arrays'
- * device addresses (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the arrays and leave the last call's
- * contents in them; calls that overlap on the GPU race and give wrong results.
+ * twiddle tables are file-scope __device__ arrays (64 MiB + 12 KiB) that a
+ * GPU reserves when the library's module holding them is loaded on it, and
+ * holds until the process exits; no cudaMalloc, cudaFree or other allocating
+ * call is made.  With lazy module loading (the CUDA default) that load
+ * happens at the first call on a device, which also looks up the arrays'
+ * device addresses (cudaGetSymbolAddress) and the launch occupancies: make
+ * that first call early -- before memory is handed to another owner and
+ * before any stream capture.  tfft_exec_noalloc(0, 0, NULL, NULL, 0) performs
+ * only that set-up on the current device.  If the device has no memory left
+ * for the arrays the call returns TFFT_ERR_ALLOC.  All calls share the arrays
+ * and leave the last call's contents in them; calls that overlap on the GPU
+ * race and give wrong results.
  */
 int tfft_exec_noalloc(int64_t n, int64_t batch, const void *in, void *out, tfft_stream_t stream);
 

@@ -47,7 +47,7 @@ class PlanOpts(ctypes.Structure):
                 ("detect_only", ctypes.c_int), ("max_faults", ctypes.c_int),
                 ("force_passes", ctypes.c_int), ("checksum_vector", ctypes.c_int),
                 ("checksum_seed", ctypes.c_uint64), ("direction", ctypes.c_int), ("normalize", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("wait_polls", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -166,9 +166,10 @@ def tfft_plan(n: int, batch: int, dtype: int = TFFT_C64, abft_mode: int = TFFT_A
 def tfft_plan_ex(n: int, batch: int, dtype: int = TFFT_C64, abft_mode: int = TFFT_ABFT_TWO_SIDED,
                  group: int = 0, kappa: float = 0.0, detect_only: bool = False, max_faults: int = 0,
                  force_passes: int = 0, checksum_vector: int = TFFT_R_SIGNED_WANG, checksum_seed: int = 0,
-                 direction: int = TFFT_FORWARD, normalize: bool = False, precision: int = TFFT_PREC_FP32) -> int:
+                 direction: int = TFFT_FORWARD, normalize: bool = False, precision: int = TFFT_PREC_FP32,
+                 wait_polls: int = 0) -> int:
     o = PlanOpts(n, batch, dtype, abft_mode, group, kappa, int(detect_only), max_faults, force_passes,
-                 checksum_vector, checksum_seed, direction, int(normalize), precision)
+                 checksum_vector, checksum_seed, direction, int(normalize), precision, wait_polls)
     h = ctypes.c_void_p()
     _check(lib().tfft_plan_ex(ctypes.byref(h), ctypes.byref(o)), "tfft_plan_ex")
     return h.value

@@ -91,9 +91,9 @@ __device__ void decide_group(const VerifyParams& v, int64_t g, const GroupSums& 
   if ((action == 1 || action == 2) && v.cond_flag &&
       atomicExch(reinterpret_cast<unsigned long long*>(v.cond_flag), 1ull) == 0ull)
     cudaGraphSetConditional(v.cond, 1u);      // run the correction body of this exec's graph
-  if (action == 1) atomicAdd(&v.counters->corrected, 1ull);
-  else if (action == 2) atomicAdd(&v.counters->recomputed, 1ull);
-  else atomicAdd(&v.counters->uncorrectable, 1ull);
+  // corrected and recomputed groups are counted by fix_apply, after the
+  // correction has run; a group left as it is is counted here
+  if (action == 3) atomicAdd(&v.counters->uncorrectable, 1ull);
   const unsigned long long slot = atomicAdd(&v.counters->log_total, 1ull);
   LogEvent ev;
   ev.exec_index = v.exec_index;
@@ -272,6 +272,13 @@ __global__ void fix_gather_kernel(const FixParams f) {
 template <typename cT>
 __global__ void fix_apply_kernel(const FixParams f) {
   const long long count = min((long long)f.lists.fix[0], (long long)f.lists.cap_fix);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && f.counters && !(f.err_flag && *f.err_flag)) {
+    // this launch follows the transform of the checksums and the group
+    // recomputes in stream order: both are done
+    const long long nrec = min((long long)f.lists.rec[0], (long long)f.lists.cap_rec);
+    if (count > 0) atomicAdd(&f.counters->corrected, (unsigned long long)count);
+    if (nrec > 0) atomicAdd(&f.counters->recomputed, (unsigned long long)nrec);
+  }
   const int64_t total = count * f.n;
   cT* y = reinterpret_cast<cT*>(f.out);
   const cT* fc1 = reinterpret_cast<const cT*>(f.ws_c1);

@@ -267,10 +267,12 @@ fft_tile_kernel(const __grid_constant__ PassParams p) {
 
   // producer: thread 0 keeps the loads of the next tiles in flight
   TileCursor prod;
+  int nissued = 0;     // loads issued by thread 0; load j goes to buffer j % nbuf
   if (t == 0) {
     prod.start(p);
     for (int s = 0; s < nbuf - 1 && prod.valid(p); s++) {
       issue_load(p, prod, buffer(s), &full[s]);
+      nissued++;
       prod.advance(p);
     }
   }
@@ -339,11 +341,18 @@ fft_tile_kernel(const __grid_constant__ PassParams p) {
       // ---- wait for the tile (bounded) ----
       {
         bool ok = false;
-        for (long long it = 0; it < kWaitLimit && !ok; it++) ok = mbar_try_wait(&full[s], parity);
+        for (long long it = 0; it < p.wait_limit && !ok; it++) ok = mbar_try_wait(&full[s], parity);
         if (__syncthreads_or(!ok)) {
           if (t == 0) {
             atomicExch(p.err_flag, 1);
             bulk_wait_0();
+            // the loads still in flight (tiles k .. nissued-1, one per
+            // buffer) land before the block's shared memory is released
+            for (int j = k; j < nissued; j++) {
+              bool done = false;
+              for (long long it = 0; it < kWaitLimit && !done; it++)
+                done = mbar_try_wait(&full[j % nbuf], (uint32_t)((j / nbuf) & 1));
+            }
           }
           return;
         }
@@ -524,6 +533,7 @@ fft_tile_kernel(const __grid_constant__ PassParams p) {
         if (prod.valid(p)) {
           const int sp = (k + nbuf - 1) % nbuf;
           issue_load(p, prod, buffer(sp), &full[sp]);
+          nissued++;
           prod.advance(p);
         }
       }

@@ -112,12 +112,13 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* a) {
   return v;
 }
 
-// Bounded wait on an mbarrier phase; gives up early once another warp has
-// recorded a timeout in *abort.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  for (long long it = 0; it < kWaitLimit; it++) {
+// Bounded wait on an mbarrier phase (at most `limit` polls); gives up early
+// once another warp has recorded a timeout in *abort.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                                  long long limit = kWaitLimit) {
+  for (long long it = 0; it < limit; it++) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 1023) == 1023 && *abort) return false;
+    if (abort && (it & 1023) == 1023 && *abort) return false;
   }
   return false;
 }
@@ -370,6 +371,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
   __shared__ unsigned arrivals[8];   // per buffer: warps done with the tile, cumulative
   __shared__ unsigned readers[8];    // per buffer: warps done reading the input box, cumulative
   __shared__ unsigned copied[8];     // per buffer: warps done copying the tile out (last pass), cumulative
+  __shared__ unsigned issued[8];     // per buffer: tile loads issued into it, cumulative
   __shared__ int s_abort;
 
   const int t = threadIdx.x;
@@ -386,6 +388,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
       arrivals[s] = 0;
       readers[s] = 0;
       copied[s] = 0;
+      issued[s] = 0;
     }
     fence_mbar_init();
     s_abort = 0;
@@ -401,6 +404,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
     ld.start(p);
     for (int s = 0; s < nbuf && ld.valid(p); s++) {
       issue_load(p, ld, reinterpret_cast<cT*>(base + (size_t)s * p.buf_bytes), &full[s]);
+      issued[s]++;
       ld.advance(p);
     }
     for (int w = 0; w < 8; w++) ldc[w] = ld;
@@ -693,7 +697,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
 
     for (long long tb = cur.sb; tb < se; tb += BSTEP, wgt += wstep) {
       unsigned char* tile = base + (size_t)s * p.buf_bytes;
-      if (!aborted && !mbar_wait_bounded(&full[s], wrap & 1u, abort_flag)) {
+      if (!aborted && !mbar_wait_bounded(&full[s], wrap & 1u, abort_flag, p.wait_limit)) {
         aborted = true;
         *abort_flag = 1;
         atomicExch(p.err_flag, 1);
@@ -917,6 +921,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
             if (ld.valid(p)) {
               bulk_wait_read_0();               // the store has read the buffer
               issue_load(p, ld, reinterpret_cast<cT*>(tile), &full[s]);
+              issued[s]++;
             }
           }
           ld.advance(p);
@@ -949,6 +954,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
           if (old == 8u * wrap + 7u && !*abort_flag && ld.valid(p)) {
             fence_proxy_async();
             issue_load(p, ld, reinterpret_cast<cT*>(tile), &full[s]);
+            issued[s]++;
           }
           ld.advance(p);
         }
@@ -959,6 +965,16 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
     if (abft && !p.per_signal) warp_records(acc, p, cur.g, slot);
   }
   if (lane == 0) bulk_wait_0();
+  // After a timed-out wait the warps skipped waiting for tiles whose loads
+  // were already issued (no load is issued after the timeout): before the
+  // block's shared memory is released, wait (bounded) for the last load
+  // issued into every buffer.  Without a timeout every load has been waited
+  // for and each of these waits returns at once.
+  __syncthreads();
+  if (t == 0 && *abort_flag) {
+    for (int b = 0; b < nbuf; b++)
+      if (issued[b] > 0u) mbar_wait_bounded(&full[b], (issued[b] - 1u) & 1u, nullptr);
+  }
   if constexpr (TC != 0) {
     tc::fence_before_sync();
     __syncthreads();

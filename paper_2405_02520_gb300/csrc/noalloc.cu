@@ -1,19 +1,24 @@
 // noalloc.cu -- tfft_exec_noalloc: the two-pass complex64 transform without
 // any allocation, for callers that may not allocate device memory.
 //
-// Who needs this: code running where cudaMalloc is unavailable or forbidden --
-// inside a CUDA-graph capture that must not contain allocation nodes, under a
-// memory manager or sandbox that owns every device allocation, or in a
-// real-time loop that may not block on the allocator.  Such callers cannot
-// create a plan (tfft_plan allocates its workspace), so this entry point takes
-// only the caller's input and output buffers and uses, for the inter-pass
-// buffer and the twiddle tables, file-scope __device__ arrays of fixed size.
+// Who needs this: code that runs where cudaMalloc is unavailable or not
+// allowed -- under a memory manager or sandbox that owns every device
+// allocation, or in a real-time loop that may not block on the allocator.
+// Such callers cannot create a plan (tfft_plan allocates its workspace), so
+// this entry point takes only the caller's input and output buffers and uses,
+// for the inter-pass buffer and the twiddle tables, file-scope __device__
+// arrays of fixed size.
 //
-// Every GPU that loads the library holds those arrays (64 MiB + 12 KiB) until
-// the process exits.  All calls share them and they keep the last call's
-// contents; nothing needs to start at zero.  Two calls that overlap on the GPU
-// (different streams, or different host threads) race on the shared arrays
-// and produce wrong results: serialise them.
+// Those arrays (64 MiB + 12 KiB) are reserved on a GPU when this file's
+// module is loaded there and stay until the process exits.  With lazy module
+// loading (the CUDA default) that happens at the first call on the device,
+// which looks up the arrays' addresses: make that first call -- or the
+// set-up-only call tfft_exec_noalloc(0, 0, NULL, NULL, 0) -- early, before
+// memory is handed to another owner and before any stream capture.  All calls
+// share the arrays and they keep the last call's contents; nothing needs to
+// start at zero.  Two calls that overlap on the GPU (different streams, or
+// different host threads) race on the shared arrays and produce wrong
+// results: serialise them.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -24,6 +29,8 @@
 
 #include "../../include/tfft.h"
 #include "tfft_internal.h"
+
+using namespace tfft;
 
 namespace {
 
@@ -36,13 +43,16 @@ static __device__ __align__(256) float2 g_tw_sub[kTab];
 static __device__ __align__(256) float2 g_tw_lo[kTab];
 static __device__ __align__(256) float2 g_tw_hi[kTab];
 
+// Set-up state of one device: the arrays' device addresses and, per signal
+// length 2^m and pass, the resident blocks per SM of the pass kernel.
+constexpr int kMinLog2 = 13, kMaxLog2 = 18;
 struct DeviceArrays {
   void* scratch = nullptr;
   void* sub = nullptr;
   void* lo = nullptr;
   void* hi = nullptr;
   int sms = 0;
-  bool sm103 = false;
+  int bps[kMaxLog2 + 1][2] = {};
   bool ready = false;
 };
 DeviceArrays g_arrays[kMaxDevices];
@@ -67,9 +77,21 @@ __global__ void noalloc_tables_kernel(float2* sub, int T, float2* lo, int L, flo
 
 int ilog2_na(int64_t v) { int k = 0; while ((int64_t(1) << k) < v) k++; return k; }
 
-// Set-up on the current device, done by the first call on that device: the
-// device addresses of the arrays (their names in host code are host-side
-// stand-ins and must never be passed to a kernel).
+// Factor of the first pass: N1 = 2^ceil(m/2) (both factors <= 512 for N <= 2^18).
+int64_t first_factor(int m) { return int64_t(1) << ((m + 1) / 2); }
+
+int symbol_address(void** ptr, const void* symbol) {
+  const cudaError_t e = cudaGetSymbolAddress(ptr, symbol);
+  if (e == cudaSuccess) return 0;
+  cudaGetLastError();
+  // the module is loaded (and its arrays reserved) by the first lookup
+  return e == cudaErrorMemoryAllocation ? TFFT_ERR_ALLOC : record_cuda_error(e);
+}
+
+// Set-up on the current device, done once by the first call on that device:
+// the device addresses of the arrays (their names in host code are host-side
+// stand-ins and must never be passed to a kernel) and the occupancy of every
+// launch the entry point can make.
 int device_arrays(int dev, DeviceArrays** out) {
   if (dev < 0 || dev >= kMaxDevices) return TFFT_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lk(g_setup_mu);
@@ -77,13 +99,24 @@ int device_arrays(int dev, DeviceArrays** out) {
   if (!a.ready) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return TFFT_ERR_NO_DEVICE;
-    a.sm103 = prop.major == 10 && prop.minor == 3;
+    if (!(prop.major == 10 && prop.minor == 3)) return TFFT_ERR_NO_DEVICE;
     a.sms = prop.multiProcessorCount;
-    if (!a.sm103) return TFFT_ERR_NO_DEVICE;
-    if (cudaGetSymbolAddress(&a.scratch, g_scratch) != cudaSuccess) return TFFT_ERR_CUDA;
-    if (cudaGetSymbolAddress(&a.sub, g_tw_sub) != cudaSuccess) return TFFT_ERR_CUDA;
-    if (cudaGetSymbolAddress(&a.lo, g_tw_lo) != cudaSuccess) return TFFT_ERR_CUDA;
-    if (cudaGetSymbolAddress(&a.hi, g_tw_hi) != cudaSuccess) return TFFT_ERR_CUDA;
+    int rc;
+    if ((rc = symbol_address(&a.scratch, g_scratch))) return rc;
+    if ((rc = symbol_address(&a.sub, g_tw_sub))) return rc;
+    if ((rc = symbol_address(&a.lo, g_tw_lo))) return rc;
+    if ((rc = symbol_address(&a.hi, g_tw_hi))) return rc;
+    for (int m = kMinLog2; m <= kMaxLog2; m++) {
+      PassGeom g[2];
+      two_pass_geometry(int64_t(1) << m, first_factor(m), 8, g);
+      for (int pass = 0; pass < 2; pass++) {
+        int bps = 0;
+        const cudaError_t e = pass_func_attrs_f32(g[pass].E, g[pass].smem, g[pass].nthreads, &bps);
+        if (e != cudaSuccess) return record_cuda_error(e);
+        if (bps < 1) return TFFT_ERR_UNSUPPORTED;
+        a.bps[m][pass] = bps;
+      }
+    }
     a.ready = true;
   }
   *out = &a;
@@ -92,68 +125,58 @@ int device_arrays(int dev, DeviceArrays** out) {
 
 }  // namespace
 
-using namespace tfft;
-
 extern "C" int tfft_exec_noalloc(int64_t n, int64_t batch, const void* in, void* out,
                                  tfft_stream_t stream) {
-  if (!in || !out || (((uintptr_t)in | (uintptr_t)out) & 15u)) return TFFT_ERR_INVALID_ARG;
-  if (n < 8192 || n > (int64_t(1) << 18) || (n & (n - 1)) || batch < 1) return TFFT_ERR_INVALID_ARG;
-  if (batch > kScratchElems / n) return TFFT_ERR_INVALID_ARG;   // batch * n above the scratch
+  const bool setup_only = n == 0 && batch == 0;
+  if (!setup_only) {
+    if (!in || !out || (((uintptr_t)in | (uintptr_t)out) & 15u)) return TFFT_ERR_INVALID_ARG;
+    if (n < (int64_t(1) << kMinLog2) || n > (int64_t(1) << kMaxLog2) || (n & (n - 1)) || batch < 1)
+      return TFFT_ERR_INVALID_ARG;
+    if (batch > kScratchElems / n) return TFFT_ERR_INVALID_ARG;   // batch * n above the scratch
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return TFFT_ERR_NO_DEVICE;
   DeviceArrays* arr = nullptr;
   int rc = device_arrays(dev, &arr);
-  if (rc) return rc;
+  if (rc || setup_only) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
   // two passes: N1 x N2 with N1 = 2^ceil(m/2) <= 512, N2 <= 512
   const int m = ilog2_na(n);
-  const int64_t N1 = int64_t(1) << ((m + 1) / 2), N2 = n / N1;
-  const int E = 16, TILE = 4096, S = 16;
+  const int64_t N1 = first_factor(m), N2 = n / N1;
+  PassGeom g[2];
+  two_pass_geometry(n, N1, 8, g);
   const int T = (int)std::max(N1, N2);
   const int lb = (m + 1) / 2;
   const int L = 1 << lb, H = (int)((n + L - 1) / L);
   noalloc_tables_kernel<<<(kTab + 255) / 256, 256, 0, s>>>(
       reinterpret_cast<float2*>(arr->sub), T, reinterpret_cast<float2*>(arr->lo), L,
       reinterpret_cast<float2*>(arr->hi), H, (long long)n);
-  if (cudaGetLastError() != cudaSuccess) return TFFT_ERR_CUDA;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return record_cuda_error(e);
 
   for (int pass = 0; pass < 2; pass++) {
+    const PassGeom& q = g[pass];
     PassParams a;
     std::memset(&a, 0, sizeof(a));
-    const int64_t nsub = pass == 0 ? N1 : N2;
-    const int64_t LO = pass == 0 ? N2 : N1;
-    const int C = (int)std::min<int64_t>(std::min<int64_t>(TILE / nsub, LO), 64);
-    a.nsub = (int)nsub; a.log2nsub = ilog2_na(nsub); a.C = C;
-    a.nthreads = (int)(C * nsub / E);
-    int st = 0; for (int64_t v = 1; v < nsub; v *= E) st++;
-    a.nstages = st;
-    a.n = n; a.batch = batch; a.LO = LO; a.HI = 1; a.pass_index = pass;
+    a.nsub = q.nsub; a.log2nsub = ilog2_na(q.nsub); a.C = q.C; a.nthreads = q.nthreads;
+    a.nstages = q.nstages; a.pitch = q.pitch;
+    a.in_map = q.in_map; a.mid_map = q.mid_map; a.out_map = q.out_map;
+    a.n = n; a.batch = batch; a.LO = q.LO; a.HI = q.HI; a.pass_index = pass;
+    a.in_es = q.in_es; a.in_lo = q.in_lo; a.in_hi = q.in_hi;
+    a.out_es = q.out_es; a.out_lo = q.out_lo; a.out_hi = q.out_hi;
+    a.twiddle = q.twiddle; a.tw_scale = q.tw_scale;
     a.out_scale = 1.0;            // forward, unnormalised
-    if (pass == 0) {
-      a.in_es = N2; a.in_lo = 1; a.out_es = N2; a.out_lo = 1;
-      a.in_map = a.mid_map = a.out_map = MAP_COL;
-      a.pitch = (int)nsub + (C < S ? S / C : 1);
-      a.twiddle = 1; a.tw_scale = 1;
-      a.in = in; a.out = arr->scratch;
-    } else {
-      a.in_es = 1; a.in_lo = N2; a.out_es = N1; a.out_lo = 1;
-      a.in_map = MAP_ROW; a.out_map = MAP_COL;
-      a.mid_map = C >= S / 2 ? MAP_COL : MAP_ROW;
-      const int lanes = (int)std::max<int64_t>(1, nsub / E);
-      a.pitch = (int)nsub + (a.mid_map == MAP_COL ? (C < S ? S / C : 1) : (lanes < S ? lanes : 0));
-      a.in = arr->scratch; a.out = out;
-    }
-    a.tw_sub = arr->sub; a.tw_sub_stride = (int)(T / nsub);
+    a.in = pass == 0 ? in : arr->scratch;
+    a.out = pass == 0 ? arr->scratch : out;
+    a.tw_sub = arr->sub; a.tw_sub_stride = (int)(T / q.nsub);
     a.twN_lo = arr->lo; a.twN_hi = arr->hi; a.twN_lbits = lb;
     a.group = 1; a.parts = 1; a.ngroups = batch;
-    a.line_blocks = LO / C;
+    a.line_blocks = q.line_blocks;
     a.nchunks = batch * a.line_blocks;
-    const size_t smem = (size_t)C * a.pitch * sizeof(float2);
-    int bps = 0;
-    if (pass_func_attrs_f32(E, smem, a.nthreads, &bps) != cudaSuccess || bps < 1) return TFFT_ERR_CUDA;
-    const int64_t grid = std::min<int64_t>(a.nchunks, (int64_t)arr->sms * bps);
-    if (launch_pass_f32(a, E, (int)grid, smem, s) != cudaSuccess) return TFFT_ERR_CUDA;
+    const int64_t grid = std::min<int64_t>(a.nchunks, (int64_t)arr->sms * arr->bps[m][pass]);
+    e = launch_pass_f32(a, q.E, (int)grid, q.smem, s);
+    if (e != cudaSuccess) return record_cuda_error(e);
   }
   return TFFT_SUCCESS;
 }

@@ -132,6 +132,7 @@ struct tfft_plan_s {
   int inverse = 0, normalize = 0;
   int one_sided = 0;                 // per-signal checksums (verification groups of one)
   int prec = TFFT_PREC_FP32;         // arithmetic of the radix-16 butterflies
+  long long wait_limit = 1ll << 20;  // polls of a tile-arrival wait
   int vG = 16;                       // signals per verification group
   int64_t vgroups = 0;               // verification groups
   int cap_fix = 1, cap_rec = 1;
@@ -267,6 +268,59 @@ int nstages_of(int nsub, int E) {
   return std::max(s, 1);
 }
 
+}  // namespace
+
+namespace tfft {
+
+int geom_pick_E(int nsub, int E0) { return pick_E(nsub, E0); }
+int geom_nstages(int nsub, int E) { return nstages_of(nsub, E); }
+
+void two_pass_geometry(int64_t n, int64_t N1, int esize, PassGeom g[2]) {
+  const bool c64 = esize == 8;
+  const int E0 = c64 ? 16 : 8;
+  const int TILE = c64 ? 4096 : 2048;        // elements of one thread block's tile
+  const int S = c64 ? 16 : 8;                // elements per 128-byte shared-memory row
+  const int64_t M = n / N1;
+  // first pass: columns n_rest of length N1, stride M, twiddle wN^{n_rest k1}
+  PassGeom& a = g[0];
+  a = PassGeom{};
+  a.nsub = (int)N1; a.E = pick_E(a.nsub, E0);
+  a.LO = M; a.HI = 1;
+  a.C = (int)std::min<int64_t>(std::min<int64_t>(TILE / N1, M), 64);
+  a.in_es = M; a.in_lo = 1; a.out_es = M; a.out_lo = 1;
+  a.in_map = a.mid_map = a.out_map = MAP_COL;
+  a.twiddle = 1; a.tw_scale = 1;
+  a.pitch = a.nsub + col_pad(a.C, S);
+  // second pass: rows of length N2 = M, contiguous, stored transposed
+  PassGeom& b = g[1];
+  b = PassGeom{};
+  const int64_t N2 = M;
+  b.nsub = (int)N2; b.E = pick_E(b.nsub, E0);
+  b.LO = N1; b.HI = 1;
+  b.C = (int)std::min<int64_t>(std::min<int64_t>(TILE / N2, N1), 64);
+  b.in_es = 1; b.in_lo = N2; b.out_es = N1; b.out_lo = 1;
+  b.in_map = MAP_ROW; b.out_map = MAP_COL; b.mid_map = b.C >= S / 2 ? MAP_COL : MAP_ROW;
+  b.pitch = b.nsub + (b.mid_map == MAP_COL ? col_pad(b.C, S) : row_pad(b.nsub, b.E, S));
+  for (int i = 0; i < 2; i++) {
+    PassGeom& q = g[i];
+    q.nthreads = (int)((int64_t)q.C * q.nsub / q.E);
+    q.nstages = nstages_of(q.nsub, q.E);
+    q.line_blocks = q.LO * q.HI / q.C;
+    q.smem = (size_t)q.C * q.pitch * (size_t)esize;
+  }
+}
+
+}  // namespace tfft
+
+namespace {
+
+void copy_geom(PassPlan& q, const PassGeom& g) {
+  q.nsub = g.nsub; q.E = g.E; q.C = g.C; q.pitch = g.pitch;
+  q.in_map = g.in_map; q.mid_map = g.mid_map; q.out_map = g.out_map; q.twiddle = g.twiddle;
+  q.LO = g.LO; q.HI = g.HI; q.in_es = g.in_es; q.in_lo = g.in_lo; q.in_hi = g.in_hi;
+  q.out_es = g.out_es; q.out_lo = g.out_lo; q.out_hi = g.out_hi; q.tw_scale = g.tw_scale;
+}
+
 int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
   const int64_t n = o->n;
   const bool c64 = o->dtype == TFFT_C64;
@@ -330,24 +384,13 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
   } else {
     const int64_t N1 = int64_t(1) << mf[0];
     const int64_t M = n / N1;
+    PassGeom g2[2];
+    two_pass_geometry(n, N1, (int)p->esize, g2);
     // first pass: columns n_rest of length N1, stride M, twiddle wN^{n_rest k1}
     PassPlan& a = p->pp[0];
-    a.nsub = (int)N1; a.E = pick_E(a.nsub, E0);
-    a.LO = M; a.HI = 1;
-    a.C = (int)std::min<int64_t>(std::min<int64_t>(TILE / N1, M), 64);
-    a.in_es = M; a.in_lo = 1; a.out_es = M; a.out_lo = 1;
-    a.in_map = a.mid_map = a.out_map = MAP_COL;
-    a.twiddle = 1; a.tw_scale = 1;
-    a.pitch = a.nsub + col_pad(a.C, S);
+    copy_geom(a, g2[0]);
     if (passes == 2) {
-      PassPlan& b = p->pp[1];
-      const int64_t N2 = M;
-      b.nsub = (int)N2; b.E = pick_E(b.nsub, E0);
-      b.LO = N1; b.HI = 1;
-      b.C = (int)std::min<int64_t>(std::min<int64_t>(TILE / N2, N1), 64);
-      b.in_es = 1; b.in_lo = N2; b.out_es = N1; b.out_lo = 1;
-      b.in_map = MAP_ROW; b.out_map = MAP_COL; b.mid_map = b.C >= S / 2 ? MAP_COL : MAP_ROW;
-      b.pitch = b.nsub + (b.mid_map == MAP_COL ? col_pad(b.C, S) : row_pad(b.nsub, b.E, S));
+      copy_geom(p->pp[1], g2[1]);
     } else {
       const int64_t N2 = int64_t(1) << mf[1], N3 = int64_t(1) << mf[2];
       PassPlan& b = p->pp[1];           // lines (k1, n3) over n2, stride N3
@@ -877,7 +920,7 @@ int launch_pass(tfft_plan_s* p, PassParams& a, int i, int kind, cudaStream_t s) 
   const PassPlan& q = p->pp[i];
   const bool tma = q.tma && a.list == nullptr;
   if (tma) {
-    a.nbuf = q.nbuf; a.buf_bytes = q.buf_bytes; a.err_flag = p->err_flag;
+    a.nbuf = q.nbuf; a.buf_bytes = q.buf_bytes; a.err_flag = p->err_flag; a.wait_limit = p->wait_limit;
     a.map_in = q.map_in; a.map_out = q.map_out;
     const void* ptrs[2] = {a.in, a.out};
     const MapGeom* geo[2] = {&q.gin, &q.gout};
@@ -999,9 +1042,10 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
 }
 
 // The correction sequence (Section III-B) on `s`: gather the queued groups'
-// input checksum and partial output sums, transform the checksums, apply;
-// then recompute the groups that could not be located.  Every launch returns
-// at once when its list is empty.
+// input checksum and partial output sums, transform the checksums, recompute
+// the groups that could not be located (other groups: no overlap with the
+// gathered ones), then apply the located corrections, which also counts both
+// kinds as done.  Every launch returns at once when its list is empty.
 int enqueue_correction(tfft_plan_s* p, const FixParams& f, const void* in, void* out, int64_t nb,
                        cudaStream_t s) {
   int rc;
@@ -1010,9 +1054,9 @@ int enqueue_correction(tfft_plan_s* p, const FixParams& f, const void* in, void*
   if ((rc = run_passes(p, p->ws_c1, p->ws_c1, s, false, p->lists.fix, 1, p->cap_fix, 1,
                        p->cap_fix, 5, false)))
     return rc;
-  if ((rc = timed_launch(p, 5, s, [&] { return launch_fix_apply(f, s); }))) return rc;
   // groups that could not be located: recompute from the input
-  return run_passes(p, in, out, s, false, p->lists.rec, 0, p->cap_rec, p->vG, nb, 5);
+  if ((rc = run_passes(p, in, out, s, false, p->lists.rec, 0, p->cap_rec, p->vG, nb, 5))) return rc;
+  return timed_launch(p, 5, s, [&] { return launch_fix_apply(f, s); });
 }
 
 // Builds the graph [verify] -> [if (a group was queued) { correction }] for
@@ -1125,6 +1169,7 @@ int exec_range(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
     FixParams f{};
     f.n = p->n; f.batch = nb; f.group = p->vG; f.dtype = p->dtype;
     f.in = in; f.out = out; f.soff = p->soff; f.ws_c1 = p->ws_c1; f.ws_acc = p->ws_acc; f.lists = p->lists;
+    f.counters = p->counters; f.err_flag = p->err_flag;
     // a whole-batch exec on a stream that is not being captured:
     // verification and correction from the graph (timed as one launch)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -1219,6 +1264,7 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   if ((o->direction != TFFT_FORWARD && o->direction != TFFT_INVERSE) || (o->normalize != 0 && o->normalize != 1))
     return TFFT_ERR_INVALID_ARG;
   if (o->precision < TFFT_PREC_FP32 || o->precision > TFFT_PREC_BF16X3) return TFFT_ERR_INVALID_ARG;
+  if (o->wait_polls < -1) return TFFT_ERR_INVALID_ARG;
   if (o->precision != TFFT_PREC_FP32 && o->dtype != TFFT_C64) return TFFT_ERR_UNSUPPORTED;
   int dev = 0, count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) return TFFT_ERR_NO_DEVICE;
@@ -1239,6 +1285,7 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   p->inverse = o->direction == TFFT_INVERSE;
   p->prec = o->precision;
   p->normalize = o->normalize;
+  p->wait_limit = o->wait_polls == 0 ? (1ll << 20) : (o->wait_polls < 0 ? 0 : (long long)o->wait_polls);
   p->device = dev;
   p->sms = prop.multiProcessorCount;
   int rc = plan_build(p, o);
@@ -1396,6 +1443,7 @@ int tfft_reset_counters(tfft_plan_t p) {
   if (!p) return TFFT_ERR_INVALID_ARG;
   if (p->used) TFFT_CUDA(cudaStreamSynchronize(p->last_stream));
   TFFT_CUDA(cudaMemset(p->counters, 0, sizeof(Counters)));
+  TFFT_CUDA(cudaMemset(p->err_flag, 0, sizeof(int)));
   p->execs = 0;
   p->launches = 0;
   return TFFT_SUCCESS;

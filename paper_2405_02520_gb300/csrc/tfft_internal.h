@@ -183,6 +183,7 @@ struct PassParams {
   int nbuf;               // shared-memory tile buffers in the ring
   unsigned buf_bytes;     // bytes per buffer (tile rounded up to 1 KiB)
   int* err_flag;          // set when a bounded wait gives up
+  long long wait_limit;   // polls of a tile-arrival wait before it gives up
   TileMap map_in, map_out;
   CUtensorMap tmap_in;     // 64-byte aligned by its own type
   CUtensorMap tmap_out;
@@ -220,6 +221,26 @@ int plan_set_signal_offsets(::tfft_plan_s* p, const long long* d_off, const int6
 
 // Keeps `e` as the value tfft_last_cuda_error() reports; returns TFFT_ERR_CUDA.
 int record_cuda_error(cudaError_t e);
+
+// Geometry of one launch of the direct-load pass kernel (fft_pass.cuh): line
+// length, values per thread, lines per tile, butterfly maps, strides, the
+// shared-memory pitch and size.  two_pass_geometry fills both launches of the
+// two-pass factorisation N = N1 x (N / N1) (Section IV-A, "Tiled FFT"): the
+// first over columns of stride N / N1 with the inter-pass twiddle, the second
+// over contiguous rows, stored transposed into natural order.  The planner and
+// the allocation-free entry point take their two-pass geometry from here.
+struct PassGeom {
+  int nsub = 1, E = 1, C = 1, nthreads = 32, nstages = 1, pitch = 1;
+  int in_map = MAP_ROW, mid_map = MAP_ROW, out_map = MAP_ROW, twiddle = 0;
+  int64_t LO = 1, HI = 1, in_es = 1, in_lo = 0, in_hi = 0, out_es = 1, out_lo = 0, out_hi = 0;
+  int64_t tw_scale = 1, line_blocks = 1;
+  size_t smem = 0;
+};
+void two_pass_geometry(int64_t n, int64_t N1, int esize, PassGeom g[2]);
+// Elements per thread, shared-memory row padding and radix-stage count of the
+// direct-load pass kernel (see plan.cu).
+int geom_pick_E(int nsub, int E0);
+int geom_nstages(int nsub, int E);
 
 // Verify / correction kernels (abft_fix.cu).
 struct VerifyParams {
@@ -266,6 +287,11 @@ struct FixParams {
   void* ws_c1;         // cap_fix x n : gathered sum_b x_b, transformed in place
   void* ws_acc;        // cap_fix x n : sum_{b != b*} y'_b
   Lists lists;
+  // fix_apply, the last launch of the correction sequence, counts the
+  // corrected and the recomputed groups once their work has run (unless a
+  // bounded wait of the exec gave up)
+  Counters* counters;
+  const int* err_flag;
 };
 cudaError_t launch_fix_gather(const FixParams& f, cudaStream_t s);
 // r_k = s_k w3^k (SplitMix64 signs) as complex128, and a complex128 -> complex64 copy.

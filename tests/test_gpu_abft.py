@@ -181,3 +181,40 @@ def test_correction_graph_replayed_with_faults(log2n, batch):
         run()
     assert t.tfft_report_ex(plan)["detected"] == 2
     t.tfft_destroy(plan)
+
+
+@pytest.mark.parametrize("log2n,batch", [(10, 64), (14, 32)])
+def test_plain_wang_vector_parity_and_fault(log2n, batch):
+    """The paper's own left vector e_Wang (r_k = w3^k, w in closed form):
+    clean output within the tolerance with no false alarm; a scaled output
+    element and a large input-side flip are each detected, named and
+    corrected, and the oracle's scheme with kind "wang" flags and names the
+    same signal on the uncorrected output."""
+    n = 1 << log2n
+    x = uniform_batch(n, batch, seed=600 + log2n)
+    ref = oracle_fft(x)
+    plan = t.tfft_plan_ex(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED, checksum_vector=t.TFFT_R_WANG)
+    info = t.tfft_plan_info(plan)
+    assert info["checksum_vector"] == t.TFFT_R_WANG
+    y, _ = run_gpu(x, t.TFFT_C64, plan=plan)
+    assert rel_err_rows(y, ref).max() <= tol(n, t.TFFT_C64)
+    assert t.tfft_report(plan) == (0, 0)
+    last = info["passes"] - 1
+    faults = [dict(mode=t.TFFT_FAULT_SCALE, pass_=last, stage=info["stages"][last] - 1, signal=batch // 3,
+                   line=0, index=5, factor=1.0 + 1e-2),
+              dict(mode=t.TFFT_FAULT_BITFLIP, pass_=0, stage=-1, signal=batch - 2,
+                   line=min(1, info["lines_per_signal"][0] - 1), index=7, bit=29)]
+    for k, fault in enumerate(faults):
+        y, _ = run_gpu(x, t.TFFT_C64, plan=plan, fault=fault)
+        assert rel_err_rows(y, ref).max() <= tol(n, t.TFFT_C64), fault
+        assert t.tfft_report(plan) == (k + 1, k + 1)
+        ev, _ = t.tfft_fault_log(plan, 1)
+        assert ev[-1]["signal"] == fault["signal"]
+    t.tfft_destroy(plan)
+    plan = t.tfft_plan_ex(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED, checksum_vector=t.TFFT_R_WANG,
+                          detect_only=True)
+    for fault in faults:
+        yf, _ = run_gpu(x, t.TFFT_C64, plan=plan, fault=fault)
+        res = oabft.run(x, yf, group=info["group"], u=2.0 ** -24, kappa=info["kappa"], kind="wang")
+        assert res.located == {fault["signal"] // info["group"]: fault["signal"]}
+    t.tfft_destroy(plan)

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import paper_2405_02520_gb300 as t
-from tests.gpu_util import rel_err_rows, tol
+from tests.gpu_util import Guarded, rel_err_rows, tol
 
 pytestmark = pytest.mark.gpu
 
@@ -20,7 +20,9 @@ def _ragged_input(count, seed, lo=6, hi=16):
     return lengths, x
 
 
-def _check(lengths, x, y):
+def _check(lengths, x, y, *guarded):
+    for g in guarded:
+        g.check("ragged buffer")
     off = np.concatenate([[0], np.cumsum(lengths)])
     worst = 0.0
     for n in np.unique(lengths):
@@ -42,17 +44,19 @@ def test_ragged_matches_oracle_and_replays(autotune, staged):
     # lengths 2^6..2^16: every offset is a multiple of 64 elements, so every
     # bucket is addressed in place unless staging is forced
     assert all(d != staged for d in r.layout().values()), r.layout()
-    xt = torch.from_numpy(x).cuda()
-    yt = torch.empty_like(xt)
+    xg = Guarded(x.shape, None, fill=torch.from_numpy(x).cuda())
+    yg = Guarded(x.shape, xg.t.dtype)
+    xt, yt = xg.t, yg.t
     r.exec(xt, yt)                       # captured
     torch.cuda.synchronize()
     y1 = yt.cpu().numpy()
-    _check(lengths, x, y1)
+    _check(lengths, x, y1, xg, yg)
     yt.zero_()
     r.exec(xt, yt)                       # replayed
     torch.cuda.synchronize()
     assert np.array_equal(yt.cpu().numpy(), y1)
-    y2t = torch.empty_like(xt)
+    y2g = Guarded(x.shape, xg.t.dtype)
+    y2t = y2g.t
     r.exec(xt, y2t)                      # new output pointer: re-captured
     torch.cuda.synchronize()
     assert np.array_equal(y2t.cpu().numpy(), y1)
@@ -65,8 +69,9 @@ def test_ragged_faults_in_two_buckets_corrected():
     import torch
     lengths, x = _ragged_input(300, seed=55)
     r = t.Ragged(lengths.tolist(), autotune=False)
-    xt = torch.from_numpy(x).cuda()
-    yt = torch.empty_like(xt)
+    xg = Guarded(x.shape, None, fill=torch.from_numpy(x).cuda())
+    yg = Guarded(x.shape, xg.t.dtype)
+    xt, yt = xg.t, yg.t
     r.exec(xt, yt)
     torch.cuda.synchronize()
     small = int(np.nonzero(lengths == 256)[0][3])
@@ -77,7 +82,7 @@ def test_ragged_faults_in_two_buckets_corrected():
                 factor=2.0)
     r.exec(xt, yt)
     torch.cuda.synchronize()
-    _check(lengths, x, yt.cpu().numpy())
+    _check(lengths, x, yt.cpu().numpy(), xg, yg)
     st = r.report()
     assert st["detected"] == 2 and st["corrected"] + st["recomputed"] == 2
     r.destroy()
@@ -123,11 +128,12 @@ def test_ragged_one_fault_per_thousand_signals():
         n = int(lengths[i])
         r.set_fault(i, mode=t.TFFT_FAULT_SCALE, pass_=passes[n] - 1, stage=0, line=0, index=(3 * k + 1) % n,
                     factor=3.0)
-    xt = torch.from_numpy(x).cuda()
-    yt = torch.empty_like(xt)
+    xg = Guarded(x.shape, None, fill=torch.from_numpy(x).cuda())
+    yg = Guarded(x.shape, xg.t.dtype)
+    xt, yt = xg.t, yg.t
     r.exec(xt, yt)
     torch.cuda.synchronize()
-    _check(lengths, x, yt.cpu().numpy())
+    _check(lengths, x, yt.cpu().numpy(), xg, yg)
     st = r.report()
     assert st["detected"] == 4 and st["corrected"] + st["recomputed"] == 4, st
     r.destroy()
@@ -150,18 +156,19 @@ def test_ragged_mixed_direct_and_staged_buckets():
     lay = r.layout()
     assert lay[8192] is False and lay[256] is True and lay[2] is True, lay
     passes = dict(r.info())
-    xt = torch.from_numpy(x).cuda()
-    yt = torch.empty_like(xt)
+    xg = Guarded(x.shape, None, fill=torch.from_numpy(x).cuda())
+    yg = Guarded(x.shape, xg.t.dtype)
+    xt, yt = xg.t, yg.t
     r.exec(xt, yt)
     torch.cuda.synchronize()
-    _check(lengths, x, yt.cpu().numpy())
+    _check(lengths, x, yt.cpu().numpy(), xg, yg)
     s8k = int(np.nonzero(lengths == 8192)[0][1])
     s256 = int(np.nonzero(lengths == 256)[0][2])
     r.set_fault(s8k, mode=t.TFFT_FAULT_SCALE, pass_=passes[8192] - 1, stage=0, line=0, index=3, factor=2.0)
     r.set_fault(s256, mode=t.TFFT_FAULT_SCALE, pass_=0, stage=0, line=0, index=5, factor=2.0)
     r.exec(xt, yt)
     torch.cuda.synchronize()
-    _check(lengths, x, yt.cpu().numpy())
+    _check(lengths, x, yt.cpu().numpy(), xg, yg)
     st = r.report()
     assert st["detected"] == 2 and st["corrected"] + st["recomputed"] == 2, st
     r.destroy()
@@ -176,15 +183,16 @@ def test_ragged_one_sided_recompute_in_place():
     r = t.Ragged(lengths.tolist(), abft_mode=t.TFFT_ABFT_ONE_SIDED, autotune=False)
     assert all(r.layout().values())
     passes = dict(r.info())
-    xt = torch.from_numpy(x).cuda()
-    yt = torch.empty_like(xt)
+    xg = Guarded(x.shape, None, fill=torch.from_numpy(x).cuda())
+    yg = Guarded(x.shape, xg.t.dtype)
+    xt, yt = xg.t, yg.t
     big = int(np.nonzero(lengths == 1 << 14)[0][1])
     small = int(np.nonzero(lengths == 512)[0][0])
     r.set_fault(big, mode=t.TFFT_FAULT_SCALE, pass_=passes[1 << 14] - 1, stage=0, line=2, index=7, factor=2.0)
     r.set_fault(small, mode=t.TFFT_FAULT_SCALE, pass_=0, stage=1, line=0, index=11, factor=2.0)
     r.exec(xt, yt)
     torch.cuda.synchronize()
-    _check(lengths, x, yt.cpu().numpy())
+    _check(lengths, x, yt.cpu().numpy(), xg, yg)
     st = r.report()
     assert st["detected"] == 2 and st["corrected"] + st["recomputed"] == 2, st
     r.destroy()
@@ -202,8 +210,9 @@ def test_ragged_complex128_in_place():
     r = t.Ragged(lengths.tolist(), dtype=t.TFFT_C128, autotune=False)
     assert all(r.layout().values()), r.layout()
     passes = dict(r.info())
-    xt = torch.from_numpy(x).cuda()
-    yt = torch.empty_like(xt)
+    xg = Guarded(x.shape, None, fill=torch.from_numpy(x).cuda())
+    yg = Guarded(x.shape, xg.t.dtype)
+    xt, yt = xg.t, yg.t
     sig = int(np.nonzero(lengths == 4096)[0][1])
     r.set_fault(sig, mode=t.TFFT_FAULT_SCALE, pass_=passes[4096] - 1, stage=0, line=0, index=6, factor=1.25)
     r.exec(xt, yt)
@@ -215,6 +224,7 @@ def test_ragged_complex128_in_place():
         xs = np.stack([x[off[i]:off[i] + n] for i in idx])
         ys = np.stack([y[off[i]:off[i] + n] for i in idx])
         assert rel_err_rows(ys, oracle.fft(xs)).max() <= tol(int(n), t.TFFT_C128), int(n)
+    xg.check("input"); yg.check("output")
     st = r.report()
     assert st["detected"] == 1 and st["corrected"] + st["recomputed"] == 1, st
     r.destroy()

@@ -355,7 +355,7 @@ def test_late_butterfly_fault_projection_is_rarely_small():
     assert 0.8 < np.mean(ratios ** 2) < 1.2          # unit mean square: no systematic cancellation
 
 
-@pytest.mark.parametrize("n", [256, 4096])
+@pytest.mark.parametrize("n", [2, 4, 8, 256, 4096])
 def test_threshold_sits_above_fp32_rounding_noise(n):
     """Reading 4 (threshold): with kappa = 2, the residual |T1 - S1| of clean
     groups whose outputs carry FP32 rounding (the oracle's own FP32 radix-2
@@ -374,3 +374,57 @@ def test_threshold_sits_above_fp32_rounding_noise(n):
         ratios.append(v.residual / v.tau)
     assert max(ratios) < 0.6
     assert np.median(ratios) > 1e-3        # the residual is rounding noise, not exactly zero
+
+
+def _bitrev(i, bits):
+    return int(format(i, f"0{bits}b")[::-1], 2) if bits else 0
+
+
+def _flip64(v, bit):
+    u = np.array([v], dtype=np.float64).view(np.uint64)
+    u ^= np.uint64(1) << np.uint64(bit)
+    return float(u.view(np.float64)[0])
+
+
+@pytest.mark.parametrize("n,elem,comp,bit", [(16, 3, 0, 52), (256, 77, 1, 60), (1024, 1000, 0, 45)])
+def test_fault_emulation_input_flip_is_the_fft_of_the_flipped_input(n, elem, comp, bit):
+    """Stage -1 of the fault emulation flips working element `elem` after the
+    bit-reversal permutation, i.e. input x[bitrev(elem)]: the faulty
+    transform equals the oracle FFT of the input with that bit flipped."""
+    rng = np.random.default_rng(n + elem)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    pos = _bitrev(elem, int(np.log2(n)))
+    xf = x.copy()
+    if comp == 0:
+        xf[pos] = complex(_flip64(x[pos].real, bit), x[pos].imag)
+    else:
+        xf[pos] = complex(x[pos].real, _flip64(x[pos].imag, bit))
+    got = oracle.fft_faulty(x, 64, stage=-1, elem=elem, comp=comp, bit=bit)
+    want = oracle.fft(xf)
+    assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("n,stage,elem", [(64, 0, 37), (256, 2, 100), (1024, 5, 613), (1024, 9, 88)])
+def test_fault_emulation_stage_flip_spreads_over_its_residue_class(n, stage, elem):
+    """After stage s of the radix-2 decimation-in-time transform the working
+    array holds, in block i of length L = 2^(s+1), the L-point DFT Z_i of the
+    input subsequence x[c + t N/L] with c = bitrev_{log2(N/L)}(i); the output
+    is y_k = sum_i wN^(c k) Z_i[k mod L].  So a change delta of element
+    elem = i L + m0 changes exactly the outputs k = m0 (mod L), by
+    delta wN^(c k): a flip placed after the wrong stage or at the wrong
+    position would change another set of outputs or another phase."""
+    rng = np.random.default_rng(7 * n + stage)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    lg = int(np.log2(n))
+    L = 1 << (stage + 1)
+    i, m0 = divmod(elem, L)
+    c = _bitrev(i, lg - stage - 1)
+    clean = oracle.fft_faulty(x, 64)
+    bad = oracle.fft_faulty(x, 64, stage=stage, elem=elem, comp=0, bit=61)
+    diff = bad - clean
+    k = np.arange(n)
+    phase = np.exp(-2j * np.pi * ((c * k) % n) / n)
+    delta = diff[m0] / phase[m0]
+    assert abs(delta) > 1e-3                      # the flip changed the value
+    expect = np.where(k % L == m0, delta * phase, 0.0)
+    assert np.max(np.abs(diff - expect)) <= 1e-9 * abs(delta)
