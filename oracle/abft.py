@@ -191,6 +191,65 @@ def verify_group(cs: GroupChecksums, n: int, g: int, u: float, kappa: float) -> 
                         tau=float(tau), quotient=q)
 
 
+def signal_residuals(xg: np.ndarray, yg: np.ndarray, w: np.ndarray, r: np.ndarray):
+    """Left-side residual of every signal of a group, d_b = r^T y'_b - w^T x_b
+    (the one-sided check of Section III applied to each column), and its
+    input energy E_b = ||x_b||^2.  The group's two-sided residuals are their
+    right-side encodings: T1 - S1 = sum_b d_b (e_1) and T2 - S2 = sum_b (b+1)
+    d_b (e_3)."""
+    xg = np.asarray(xg, dtype=np.complex128)
+    yg = np.asarray(yg, dtype=np.complex128)
+    with np.errstate(over="ignore", invalid="ignore"):
+        d = yg @ r - xg @ w
+    return d, np.sum(np.abs(xg) ** 2, axis=1)
+
+
+@dataclass
+class SignalVerdict:
+    detected: bool
+    located: int           # b* in 0..G-1, or -1 (recompute the group)
+    flagged: list          # signals whose own test failed
+    group_residual: float  # |sum_b d_b| = |T1 - S1|
+    group_tau: float
+    quotient: complex      # sum_b (b+1) d_b / sum_b d_b
+
+
+def verify_group_signals(xg: np.ndarray, yg: np.ndarray, w: np.ndarray, r: np.ndarray, n: int,
+                         u: float, kappa: float) -> SignalVerdict:
+    """Detection and location from per-signal residuals.
+
+    Each signal b is tested on its own, |d_b| > tau(E_b) with the threshold of
+    :func:`threshold` taken over that signal's energy (or d_b not finite); the
+    group is also tested with its two-sided residual |sum_b d_b| > tau(sum_b
+    E_b).  Location: the one signal whose own test failed; with none failing
+    (a detection by the group test alone) the quotient of Section III,
+    sum_b (b+1) d_b / sum_b d_b = b* + 1; with several failing, none (the
+    group is recomputed: more than one fault)."""
+    d, e = signal_residuals(xg, yg, w, r)
+    g = d.shape[0]
+    tau_b = threshold(n, 1.0, u, kappa) * np.sqrt(e)
+    finite = np.isfinite(d)
+    with np.errstate(invalid="ignore"):
+        flagged = [b for b in range(g) if (not finite[b]) or abs(d[b]) > tau_b[b]]
+    dfin = np.where(finite, d, 0.0)
+    D1 = complex(np.sum(dfin))
+    D2 = complex(np.sum(np.arange(1, g + 1) * dfin))
+    tau_g = threshold(n, float(np.sum(np.where(finite, e, 0.0))), u, kappa)
+    res = abs(D1)
+    detected = bool(flagged) or res > tau_g
+    q = D2 / D1 if D1 != 0 else complex("nan+nanj")
+    located = -1
+    if detected:
+        if len(flagged) == 1:
+            located = flagged[0]
+        elif not flagged and D1 != 0:
+            m = int(np.rint(q.real))
+            if abs(q.real - m) < 0.25 and abs(q.imag) < 0.25 and 1 <= m <= g:
+                located = m - 1
+    return SignalVerdict(detected=detected, located=located, flagged=flagged, group_residual=float(res),
+                         group_tau=float(tau_g), quotient=q)
+
+
 def locate_nonfinite(xg: np.ndarray, yg: np.ndarray, r=None, w=None) -> int:
     """When the group residual is not finite (a value or a checksum sum
     overflowed) the quotient is undefined.  The faulty column is then the
@@ -234,10 +293,12 @@ class BatchResult:
 
 
 def run(x: np.ndarray, y_faulty: np.ndarray, group: int, u: float, kappa: float,
-        kind: str = "wang", seed: int = 0) -> BatchResult:
+        kind: str = "wang", seed: int = 0, per_signal: bool = False) -> BatchResult:
     """Apply the whole scheme to a batch: groups of ``group`` consecutive
     signals (the last one may be shorter), detect, locate, correct, with the
-    signal-side vector of ``kind`` (see :func:`vectors`)."""
+    signal-side vector of ``kind`` (see :func:`vectors`); ``per_signal``
+    detects and locates with :func:`verify_group_signals` instead of the
+    group checksums alone."""
     x = np.asarray(x, dtype=np.complex128)
     y = np.array(y_faulty, dtype=np.complex128, copy=True)
     bsz, n = x.shape
@@ -245,11 +306,22 @@ def run(x: np.ndarray, y_faulty: np.ndarray, group: int, u: float, kappa: float,
     det, loc, unc = [], {}, []
     for g0 in range(0, bsz, group):
         g1 = min(bsz, g0 + group)
+        gi = g0 // group
+        if per_signal:
+            sv = verify_group_signals(x[g0:g1], y[g0:g1], w, r, n, u, kappa)
+            if not sv.detected:
+                continue
+            det.append(gi)
+            if sv.located < 0:
+                unc.append(gi)
+                continue
+            loc[gi] = g0 + sv.located
+            y[g0:g1] = correct_group(x[g0:g1], y[g0:g1], sv.located)
+            continue
         cs = group_checksums(x[g0:g1], y[g0:g1], w=w, r=r)
         v = verify_group(cs, n, g1 - g0, u, kappa)
         if not v.detected:
             continue
-        gi = g0 // group
         det.append(gi)
         b = v.located
         if b < 0 and not (np.isfinite(cs.T1) and np.isfinite(cs.T2)):

@@ -214,6 +214,271 @@ __global__ void verify_kernel(const VerifyParams v, int lanes_per_group) {
   }
 }
 
+// ------------------------------------------------ per-signal verification
+// Per-signal records (written by the tile kernels): every signal is tested on
+// its own -- d_b = r^T y'_b - w^T x_b against tau_b = kappa u (log2 N + 4)
+// sqrt(N) ||x_b|| -- and the group's two-sided checksums of Section III are
+// formed in FP64 from the same sums: D1 = sum_b d_b = T1 - S1 (right-side
+// vector e_1) and D2 = sum_b (b+1) d_b = T2 - S2 (e_3), tested against the
+// group threshold.  A group is flagged when a signal or the group sum exceeds
+// its threshold (or is not finite).  Location: the one flagged signal; with
+// none flagged (a group-level detection) the quotient D2 / D1 = b* + 1; with
+// several flagged the group is recomputed (outside the single-event model).
+// The quotient is logged in every case.
+
+// The decision for group g (one thread): detection, location, work lists,
+// counters and the fault log.
+struct SigGroup {
+  double d1r, d1i, d2r, d2i, en;   // group sums (finite signals only)
+  int nflag, flagj, nonf;          // flagged signals, the lowest flagged index, non-finite ones
+  int flagmax;                     // highest flagged index
+  double cmax;                     // largest clean |d_b| / tau_b
+  double fres, ftau;               // residual and threshold of the lowest flagged signal
+};
+
+__device__ __forceinline__ double tau_of(const VerifyParams& v, double en) {
+  return fmax(v.kappa_u_log2n_sqrtn * sqrt(fmax(en, 0.0)), v.tau_floor);
+}
+
+__device__ void decide_sig_group(const VerifyParams& v, int64_t g, int64_t gsize, const SigGroup& c,
+                                 unsigned long long& clean_max) {
+  const double res = sqrt(c.d1r * c.d1r + c.d1i * c.d1i);
+  const double tau = tau_of(v, c.en);
+  const bool gfin = isfinite(res) && isfinite(c.d2r) && isfinite(c.d2i);
+  if (c.nflag == 0 && gfin && !(res > tau)) {
+    const double ratio = fmax(tau > 0 ? res / tau : 0.0, c.cmax);
+    clean_max = max(clean_max, (unsigned long long)__double_as_longlong(ratio));
+    return;
+  }
+  atomicAdd(&v.counters->detected, 1ull);
+  const int64_t gb = g * v.group;
+  double qr = NAN, qi = NAN;
+  if (gfin && res > 0) {
+    const double den = c.d1r * c.d1r + c.d1i * c.d1i;
+    qr = (c.d2r * c.d1r + c.d2i * c.d1i) / den;
+    qi = (c.d2i * c.d1r - c.d2r * c.d1i) / den;
+  }
+  int64_t bstar = -1;
+  if (c.nflag == 1) {
+    bstar = c.flagj;                                     // the one signal whose own test failed
+  } else if (c.nflag == 0 && gfin && res > 0) {
+    const double m = rint(qr);
+    if (fabs(qr - m) < 0.25 && fabs(qi) < 0.25 && m >= 1.0 && m <= (double)gsize) bstar = (int64_t)m - 1;
+  }
+  int action = 3;
+  if (!v.detect_only) {
+    if (bstar >= 0) {
+      const long long e = (long long)atomicAdd((unsigned long long*)&v.lists.fix[0], 1ull);
+      if (e < v.lists.cap_fix) {
+        v.lists.fix[1 + e] = g;
+        v.lists.fix_signal[e] = gb + bstar;
+        action = 1;
+      }
+    } else {
+      const long long e = (long long)atomicAdd((unsigned long long*)&v.lists.rec[0], 1ull);
+      if (e < v.lists.cap_rec) {
+        v.lists.rec[1 + e] = g;
+        action = 2;
+      }
+    }
+  }
+  if ((action == 1 || action == 2) && v.cond_flag &&
+      atomicExch(reinterpret_cast<unsigned long long*>(v.cond_flag), 1ull) == 0ull)
+    cudaGraphSetConditional(v.cond, 1u);      // run the correction body of this exec's graph
+  if (action == 3) atomicAdd(&v.counters->uncorrectable, 1ull);
+  const unsigned long long slot = atomicAdd(&v.counters->log_total, 1ull);
+  LogEvent ev;
+  ev.exec_index = v.exec_index;
+  ev.group = v.group_base + g;
+  ev.signal = bstar >= 0 ? v.group_base * v.group + gb + bstar : -1;
+  ev.action = action;
+  ev.nonfinite = (c.nonf > 0 || !gfin) ? 1 : 0;
+  // the located signal's own residual and threshold when one signal failed,
+  // else the group's
+  ev.residual = c.nflag == 1 ? c.fres : res;
+  ev.tau = c.nflag == 1 ? c.ftau : tau;
+  ev.q_re = qr;
+  ev.q_im = qi;
+  v.log[slot % kLogRing] = ev;
+}
+
+// Adds signal j's (0-based within group g) sums to the group.
+__device__ __forceinline__ void sig_accumulate(const VerifyParams& v, SigGroup& c, int j, double sr, double si,
+                                               double en, double tr, double ti) {
+  const double dr = tr - sr, di = ti - si;
+  const double d = sqrt(dr * dr + di * di);
+  const double tb = tau_of(v, en);
+  const bool fin = isfinite(d);
+  c.en += fin ? en : 0.0;
+  if (!fin || d > tb) {
+    if (c.nflag == 0 || j < c.flagj) { c.flagj = j; c.fres = d; c.ftau = tb; }
+    c.flagmax = max(c.flagmax, j);
+    c.nflag++;
+    c.nonf += fin ? 0 : 1;
+  } else {
+    c.cmax = fmax(c.cmax, tb > 0 ? d / tb : 0.0);
+  }
+  if (fin) {
+    c.d1r += dr; c.d1i += di;
+    c.d2r = fma((double)(j + 1), dr, c.d2r);
+    c.d2i = fma((double)(j + 1), di, c.d2i);
+  }
+}
+
+__device__ __forceinline__ SigGroup sig_group_zero() {
+  SigGroup c;
+  c.d1r = c.d1i = c.d2r = c.d2i = c.en = 0.0;
+  c.nflag = 0; c.flagj = 0x7fffffff; c.nonf = 0; c.flagmax = -1;
+  c.cmax = 0.0; c.fres = 0.0; c.ftau = 0.0;
+  return c;
+}
+
+// Combines two partial group states (lanes or blocks holding different signals).
+__device__ __forceinline__ void sig_group_merge(SigGroup& a, const SigGroup& b) {
+  a.d1r += b.d1r; a.d1i += b.d1i; a.d2r += b.d2r; a.d2i += b.d2i; a.en += b.en;
+  if (b.nflag > 0 && (a.nflag == 0 || b.flagj < a.flagj)) { a.flagj = b.flagj; a.fres = b.fres; a.ftau = b.ftau; }
+  a.flagmax = max(a.flagmax, b.flagmax);
+  a.nflag += b.nflag; a.nonf += b.nonf;
+  a.cmax = fmax(a.cmax, b.cmax);
+}
+
+__device__ __forceinline__ SigGroup sig_group_shfl(const SigGroup& c, int off) {
+  SigGroup o;
+  const unsigned m = 0xffffffffu;
+  o.d1r = __shfl_xor_sync(m, c.d1r, off); o.d1i = __shfl_xor_sync(m, c.d1i, off);
+  o.d2r = __shfl_xor_sync(m, c.d2r, off); o.d2i = __shfl_xor_sync(m, c.d2i, off);
+  o.en = __shfl_xor_sync(m, c.en, off);
+  o.nflag = __shfl_xor_sync(m, c.nflag, off); o.flagj = __shfl_xor_sync(m, c.flagj, off);
+  o.nonf = __shfl_xor_sync(m, c.nonf, off); o.flagmax = __shfl_xor_sync(m, c.flagmax, off);
+  o.cmax = __shfl_xor_sync(m, c.cmax, off);
+  o.fres = __shfl_xor_sync(m, c.fres, off); o.ftau = __shfl_xor_sync(m, c.ftau, off);
+  return o;
+}
+
+// One thread per signal: `lanes` (a power of two <= 32) consecutive lanes
+// take one group, lane j its signals j, j + lanes, ...; each sums its
+// records in FP64 (four independent partial sums), the lanes combine by
+// shuffles and the group's first lane decides.
+template <typename real>
+__device__ void verify_sig_serial(const VerifyParams& v, int lanes, unsigned long long& clean_max) {
+  const int lane = threadIdx.x % lanes;
+  const int64_t per_block = blockDim.x / lanes;
+  const SigIn<real>* rin = reinterpret_cast<const SigIn<real>*>(v.sig_in);
+  const SigOut<real>* rout = reinterpret_cast<const SigOut<real>*>(v.sig_out);
+  for (int64_t g0 = (int64_t)blockIdx.x * per_block; g0 < v.ngroups; g0 += (int64_t)gridDim.x * per_block) {
+    const int64_t g = g0 + threadIdx.x / lanes;
+    SigGroup c = sig_group_zero();
+    int64_t gsize = 0;
+    if (g < v.ngroups) {
+      const int64_t gb = g * v.group;
+      gsize = min((int64_t)v.group, v.batch - gb);
+      for (int64_t j = lane; j < gsize; j += lanes) {
+        const int64_t b = gb + j;
+        double sr = 0, si = 0, en = 0, tr = 0, ti = 0;
+        const SigIn<real>* pi = rin + b * v.sig_slots_in;
+        for (int64_t k = 0; k < v.sig_slots_in; k++) {
+          const SigIn<real> r = pi[k];
+          sr += (double)r.sr; si += (double)r.si; en += (double)r.en;
+        }
+        const SigOut<real>* po = rout + b * v.sig_slots_out;
+        for (int64_t k = 0; k < v.sig_slots_out; k++) {
+          const SigOut<real> r = po[k];
+          tr += (double)r.tr; ti += (double)r.ti;
+        }
+        sig_accumulate(v, c, (int)j, sr, si, en, tr, ti);
+      }
+    }
+    for (int off = lanes >> 1; off > 0; off >>= 1) sig_group_merge(c, sig_group_shfl(c, off));
+    if (g < v.ngroups && lane == 0) decide_sig_group(v, g, gsize, c, clean_max);
+  }
+}
+
+// Many records per signal: block u takes slice u % sig_split of signal
+// u / sig_split, adds its FP64 sums into sig_acc[b] and counts itself in
+// part_cnt[g]; the block that completes group g decides it (no block waits
+// on another) and restores sig_acc and the count for the next exec.
+template <typename real>
+__device__ void verify_sig_split(const VerifyParams& v, unsigned long long& clean_max) {
+  __shared__ double sred[8][5];
+  __shared__ int s_last;
+  const SigIn<real>* rin = reinterpret_cast<const SigIn<real>*>(v.sig_in);
+  const SigOut<real>* rout = reinterpret_cast<const SigOut<real>*>(v.sig_out);
+  const int64_t split = v.sig_split;
+  const int64_t nunits = v.batch * split;
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int64_t b = u / split, sl = u - b * split;
+    const int64_t i0 = v.sig_slots_in * sl / split, i1 = v.sig_slots_in * (sl + 1) / split;
+    const int64_t o0 = v.sig_slots_out * sl / split, o1 = v.sig_slots_out * (sl + 1) / split;
+    double a[5] = {0, 0, 0, 0, 0};
+    for (int64_t k = i0 + threadIdx.x; k < i1; k += blockDim.x) {
+      const SigIn<real> r = rin[b * v.sig_slots_in + k];
+      a[0] += (double)r.sr; a[1] += (double)r.si; a[2] += (double)r.en;
+    }
+    for (int64_t k = o0 + threadIdx.x; k < o1; k += blockDim.x) {
+      const SigOut<real> r = rout[b * v.sig_slots_out + k];
+      a[3] += (double)r.tr; a[4] += (double)r.ti;
+    }
+#pragma unroll
+    for (int q = 0; q < 5; q++)
+      for (int off = 16; off > 0; off >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], off);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+      for (int q = 0; q < 5; q++) sred[w][q] = a[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < 5; q++) {
+        double t = 0.0;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ww++) t += sred[ww][q];
+        a[q] = t;
+      }
+      double* acc = v.sig_acc + b * kSigAcc;
+      for (int q = 0; q < 5; q++) atomicAdd(acc + q, a[q]);
+      __threadfence();
+      const int64_t g = b / v.group;
+      const int64_t gsize = min((int64_t)v.group, v.batch - g * v.group);
+      s_last = atomicAdd(v.part_cnt + g, 1u) == (unsigned)(gsize * split - 1);
+      if (s_last) {
+        __threadfence();
+        SigGroup c = sig_group_zero();
+        for (int64_t j = 0; j < gsize; j++) {
+          double* aj = v.sig_acc + (g * v.group + j) * kSigAcc;
+          sig_accumulate(v, c, (int)j, __ldcg(aj + 0), __ldcg(aj + 1), __ldcg(aj + 2), __ldcg(aj + 3),
+                         __ldcg(aj + 4));
+          for (int q = 0; q < 5; q++) aj[q] = 0.0;
+        }
+        v.part_cnt[g] = 0u;
+        decide_sig_group(v, g, gsize, c, clean_max);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename real>
+__global__ void verify_sig_kernel(const VerifyParams v, int lanes) {
+  __shared__ unsigned long long smax[8];
+  unsigned long long clean_max = 0;   // bits of the largest clean ratio (a nonnegative double)
+  if (v.sig_split > 1) verify_sig_split<real>(v, clean_max);
+  else verify_sig_serial<real>(v, lanes, clean_max);
+  for (int off = 16; off > 0; off >>= 1) clean_max = max(clean_max, __shfl_xor_sync(0xffffffffu, clean_max, off));
+  if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = clean_max;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = max(m, smax[w]);
+    if (m) atomicMax(&v.counters->max_clean_ratio_bits, m);
+  }
+}
+
+int sig_split_of(int64_t recs, int64_t batch, int sms) {
+  if (recs <= kSigSerialMax) return 1;
+  // about 2048 records a block, and enough blocks to cover the SMs twice
+  int64_t want = (recs + 2047) / 2048;
+  const int64_t cover = (2 * (int64_t)sms + batch - 1) / batch;
+  want = std::max(want, std::min(cover, (recs + 255) / 256));
+  return (int)std::max<int64_t>(2, std::min<int64_t>(want, 4096));
+}
+
 int verify_split(int64_t recs, int64_t ngroups, int sms) {
   // about 2048 records per block, and no more blocks in total than 4 per SM
   if (recs <= 4096 || ngroups >= sms) return 1;
@@ -225,6 +490,17 @@ int verify_split(int64_t recs, int64_t ngroups, int sms) {
 cudaError_t launch_verify(const VerifyParams& vin, cudaStream_t s) {
   const int threads = 256;
   VerifyParams v = vin;
+  if (v.sigrec) {
+    int lanes = 1;
+    while (lanes < v.group && lanes < 32) lanes <<= 1;
+    int64_t blocks;
+    if (v.sig_split > 1) blocks = v.batch * v.sig_split;
+    else blocks = (v.ngroups * lanes + threads - 1) / threads;
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)v.max_blocks));
+    if (v.dtype == 0) verify_sig_kernel<float><<<(unsigned)blocks, threads, 0, s>>>(v, lanes);
+    else verify_sig_kernel<double><<<(unsigned)blocks, threads, 0, s>>>(v, lanes);
+    return cudaGetLastError();
+  }
   if (v.split < 1 || !v.part_acc || !v.part_cnt) v.split = 1;
   const int64_t recs = v.slots_in + v.slots_out;
   if (v.split > 1) {

@@ -180,34 +180,65 @@ __device__ __forceinline__ void warp_records(const Partials<real>& a, const Pass
   }
 }
 
-// One-sided mode: the records of one signal from the threads that hold it --
-// `width` consecutive lanes (a whole warp, or the TPL lanes of a warp-local
-// line) -- reduced by shuffles within those lanes and written by the first.
-template <typename real>
-__device__ __forceinline__ void line_records(const Partials<real>& a, const PassParams& p, long long sig,
-                                             long long slot, int width) {
-  const unsigned full = 0xffffffffu;
-  real v[9] = {a.s1r, a.s1i, a.s2r, a.s2i, a.en, a.t1r, a.t1i, a.t2r, a.t2i};
-  long long mn = a.nf_min, mx = a.nf_max;
-  for (int off = width >> 1; off > 0; off >>= 1) {
+// Recursive halving over the lanes of a shuffle group: with V values held
+// and the next exchange at lane distance OFF, a lane keeps the half of its
+// values selected by its bit OFF and adds its partner's copy of that half;
+// once one value is left the remaining distances complete its sum.  Every
+// lane ends with the group total of value `idx`.
+template <typename real, int V, int OFF>
+struct Halve {
+  __device__ __forceinline__ static void run(real* v, int lane, int& idx) {
+    if constexpr (OFF >= 1) {
+      if constexpr (V > 1) {
+        constexpr int H = V / 2;
+        const bool up = lane & OFF;
 #pragma unroll
-    for (int q = 0; q < 9; q++) v[q] += __shfl_xor_sync(full, v[q], off);
-    mn = min(mn, __shfl_xor_sync(full, mn, off));
-    mx = max(mx, __shfl_xor_sync(full, mx, off));
+        for (int i = 0; i < H; i++) {
+          const real keep = up ? v[i + H] : v[i];
+          const real send = up ? v[i] : v[i + H];
+          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+        }
+        if (up) idx += H;
+        Halve<real, H, OFF / 2>::run(v, lane, idx);
+      } else {
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], OFF);
+        Halve<real, 1, OFF / 2>::run(v, lane, idx);
+      }
+    }
   }
-  if ((threadIdx.x & (width - 1)) == 0 && sig >= 0) {
-    if (p.abft_in) {
-      RecIn r;
-      r.s1r = v[0]; r.s1i = v[1]; r.s2r = v[2]; r.s2i = v[3]; r.energy = v[4];
-      r.pad0 = r.pad1 = r.pad2 = 0.0;
-      p.rec_in[sig * p.slots + slot] = r;
-    }
-    if (p.abft_out) {
-      RecOut r;
-      r.t1r = v[5]; r.t1i = v[6]; r.t2r = v[7]; r.t2i = v[8];
-      r.nf_min = mn; r.nf_max = mx; r.pad0 = r.pad1 = 0.0;
-      p.rec_out[sig * p.slots + slot] = r;
-    }
+};
+
+// Per-signal records of one tile: the W consecutive lanes that hold one
+// signal's values in this tile (W = the lanes of a line in the single pass,
+// the whole warp otherwise) reduce their partial sums -- w^T x and ||x||^2 on
+// the input side, r^T y on the output side -- and write them as the record of
+// (signal `sig`, slot `slot`).  Every lane of the warp calls this; only lanes
+// of a valid signal write.
+template <typename real, int W, bool IN, bool OUT>
+__device__ __forceinline__ void sig_flush(const Partials<real>& a, const PassParams& p, long long sig,
+                                          long long slot, bool valid) {
+  constexpr int V = (IN && OUT) ? 8 : (IN ? 4 : 2);
+  static_assert(V <= W, "a record's values fit the lanes that reduce them");
+  real v[V];
+  if constexpr (IN && OUT) {
+    v[0] = a.s1r; v[1] = a.s1i; v[2] = a.en; v[3] = (real)0;
+    v[4] = a.t1r; v[5] = a.t1i; v[6] = (real)0; v[7] = (real)0;
+  } else if constexpr (IN) {
+    v[0] = a.s1r; v[1] = a.s1i; v[2] = a.en; v[3] = (real)0;
+  } else {
+    v[0] = a.t1r; v[1] = a.t1i;
+  }
+  const int lane = threadIdx.x & 31;
+  int idx = 0;
+  Halve<real, V, W / 2>::run(v, lane, idx);
+  if (!valid || (lane & (W / V - 1))) return;
+  if constexpr (IN) {
+    if (idx < 3) reinterpret_cast<real*>(reinterpret_cast<SigIn<real>*>(p.sig_in) + sig * p.sig_slots + slot)[idx] = v[0];
+  }
+  if constexpr (OUT) {
+    constexpr int O = IN ? 4 : 0;
+    if (idx >= O && idx < O + 2)
+      reinterpret_cast<real*>(reinterpret_cast<SigOut<real>*>(p.sig_out) + sig * p.sig_slots + slot)[idx - O] = v[0];
   }
 }
 
@@ -667,7 +698,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
     // one checksum record per warp and chunk
     const long long slot = (long long)(cur.part * p.line_blocks + cur.lb) * 8 + warp;
     if (!nonempty) {
-      if (abft && !p.list && !p.per_signal) {
+      if (abft && !p.list && !p.sigrec) {
         acc.zero();
         warp_records(acc, p, cur.g, slot);
       }
@@ -691,9 +722,10 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
     }
     // checksum weight (b - first signal of the group + 1) of this thread's signal
     // (one-sided mode: every signal is its own group, weight 1)
-    real wgt = p.per_signal ? (real)1 : (real)(int)(cur.sb - cur.gb + (ROLE == V3_SINGLE ? c0 : 0) + 1);
+    // (per-signal records: the group weights are applied by the verification)
+    real wgt = (real)(int)(cur.sb - cur.gb + (ROLE == V3_SINGLE ? c0 : 0) + 1);
     constexpr int BSTEP = ROLE == V3_SINGLE ? G::C : 1;
-    const real wstep = p.per_signal ? (real)0 : (real)BSTEP;
+    const real wstep = (real)BSTEP;
 
     for (long long tb = cur.sb; tb < se; tb += BSTEP, wgt += wstep) {
       unsigned char* tile = base + (size_t)s * p.buf_bytes;
@@ -758,7 +790,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
           }
         }
         acc.s1r += sr; acc.s1i += si;
-        acc.s2r = fma(wgt, sr, acc.s2r); acc.s2i = fma(wgt, si, acc.s2i);
+        if (!p.sigrec) { acc.s2r = fma(wgt, sr, acc.s2r); acc.s2i = fma(wgt, si, acc.s2i); }
         acc.en += en;
       }
       if (fst == -1) {
@@ -867,21 +899,24 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
         if (k0 == 1) { real x = hr * tr + hs * ti; ti = hr * ti - hs * tr; tr = x; }
         else if (k0 == 2) { real x = hr * tr - hs * ti; ti = hr * ti + hs * tr; tr = x; }
         acc.t1r += tr; acc.t1i += ti;
-        acc.t2r = fma(wgt, tr, acc.t2r); acc.t2i = fma(wgt, ti, acc.t2i);
-        if (!(isfinite(tr) && isfinite(ti))) {
-          acc.nf_min = min(acc.nf_min, (long long)b0);
-          acc.nf_max = max(acc.nf_max, (long long)b0);
+        if (!p.sigrec) {
+          acc.t2r = fma(wgt, tr, acc.t2r); acc.t2i = fma(wgt, ti, acc.t2i);
+          if (!(isfinite(tr) && isfinite(ti))) {
+            acc.nf_min = min(acc.nf_min, (long long)b0);
+            acc.nf_max = max(acc.nf_max, (long long)b0);
+          }
         }
       }
-      if (abft && p.per_signal) {
-        // one-sided mode: this tile's records, per signal
+      if (abft && p.sigrec) {
+        // this tile's records, one per (signal, slot); a non-finite output
+        // makes its signal's r^T y partial non-finite
         if constexpr (ROLE == V3_SINGLE) {
-          if constexpr (G::WL) line_records(acc, p, valid ? b0 : -1, 0, G::TPL);
-          else line_records(acc, p, valid ? b0 : -1, warp % G::WPL, 32);
+          if constexpr (G::WL) sig_flush<real, G::TPL, IN_CK, OUT_CK>(acc, p, b0, 0, valid);
+          else sig_flush<real, 32, IN_CK, OUT_CK>(acc, p, b0, warp % G::WPL, valid);
         } else {
-          line_records(acc, p, tb, (long long)cur.lb * 8 + warp, 32);
+          sig_flush<real, 32, IN_CK, OUT_CK>(acc, p, tb, (long long)cur.lb * 8 + warp, true);
         }
-        acc.zero();
+        acc.s1r = acc.s1i = acc.en = acc.t1r = acc.t1i = (real)0;
       }
       if constexpr (G::LM_IN != G::LM_OUT) {
         // every warp has read its input from the box before any output lands there
@@ -962,7 +997,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
       }
       if (++s == nbuf) { s = 0; wrap++; }
     }
-    if (abft && !p.per_signal) warp_records(acc, p, cur.g, slot);
+    if (abft && !p.sigrec) warp_records(acc, p, cur.g, slot);
   }
   if (lane == 0) bulk_wait_0();
   // After a timed-out wait the warps skipped waiting for tiles whose loads

@@ -147,6 +147,12 @@ struct tfft_plan_s {
   void* wt_lo = nullptr; void* wt_hi = nullptr; int wt_lbits = 0;
   void* tmp = nullptr;
   RecIn* rec_in = nullptr; RecOut* rec_out = nullptr;
+  // per-signal records (every encoding pass on the tile kernels)
+  int sigrec = 0;
+  void* sig_in = nullptr; void* sig_out = nullptr;
+  int64_t sslots_in = 1, sslots_out = 1;
+  int sig_split = 1;
+  double* sig_acc = nullptr;
   int vsplit = 1;                   // verification blocks per group
   double* part_acc = nullptr;       // split verification: per-group accumulators
   unsigned* part_cnt = nullptr;
@@ -227,7 +233,7 @@ void free_plan(tfft_plan_s* p) {
   if (p->d2h) cudaStreamDestroy(p->d2h);
   void* bufs[] = {p->tw_sub, p->twN_lo, p->twN_hi, p->wt_lo, p->wt_hi, p->wtab, p->tmp, p->rec_in, p->rec_out,
                   p->lists_mem, p->counters, p->log, p->ws_c1, p->ws_acc, p->stage_in, p->stage_out,
-                  p->err_flag, p->part_acc, p->part_cnt};
+                  p->err_flag, p->part_acc, p->part_cnt, p->sig_in, p->sig_out, p->sig_acc};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& q : p->pp)
@@ -448,17 +454,22 @@ void plan_slots(tfft_plan_s* p) {
   p->slots_out = (int64_t)l.parts * (l.v3 ? l.vLB * 8 : l.line_blocks);
   p->vG = p->G;
   p->vgroups = p->ngroups;
-  if (p->one_sided) {
-    // records per signal: the single pass writes one per warp holding a part
-    // of the line, the column and last passes one per warp and line block
+  // per-signal records when the passes that encode (the first and the last)
+  // run on the tile kernels: the single pass writes one per line, or per warp
+  // holding a part of a longer line; the column and last passes one per warp
+  // and line block
+  p->sigrec = p->abft && f.v3 && l.v3;
+  if (p->sigrec) {
     auto per_signal = [&](const PassPlan& q) -> int64_t {
       if (q.role != 0) return q.vLB * 8;
       const int E = p->dtype == TFFT_C64 ? 16 : 8;
       const int64_t tpl = q.nsub / E;
       return tpl > 32 ? tpl / 32 : 1;
     };
-    p->slots_in = per_signal(f);
-    p->slots_out = per_signal(l);
+    p->sslots_in = per_signal(f);
+    p->sslots_out = per_signal(l);
+  }
+  if (p->one_sided) {          // every signal is its own verification group
     p->vG = 1;
     p->vgroups = p->batch;
   }
@@ -860,7 +871,25 @@ int plan_workspace(tfft_plan_s* p) {
   TFFT_CUDA(cudaMalloc(&p->log, sizeof(LogEvent) * kLogRing));
   TFFT_CUDA(cudaMemset(p->log, 0, sizeof(LogEvent) * kLogRing));
   p->workspace_bytes += nl * sizeof(long long) + sizeof(Counters) + sizeof(LogEvent) * kLogRing;
-  if (p->abft) {
+  if (p->abft && p->sigrec) {
+    const size_t rin = p->dtype == TFFT_C64 ? sizeof(SigIn<float>) : sizeof(SigIn<double>);
+    const size_t rout = p->dtype == TFFT_C64 ? sizeof(SigOut<float>) : sizeof(SigOut<double>);
+    TFFT_CUDA(cudaMalloc(&p->sig_in, rin * (size_t)p->batch * (size_t)p->sslots_in));
+    TFFT_CUDA(cudaMalloc(&p->sig_out, rout * (size_t)p->batch * (size_t)p->sslots_out));
+    p->workspace_bytes += (int64_t)(rin * p->batch * p->sslots_in + rout * p->batch * p->sslots_out);
+    p->sig_split = sig_split_of(p->sslots_in + p->sslots_out, p->batch, p->sms);
+    if (p->sig_split > 1) {
+      const size_t acc = (size_t)p->batch * kSigAcc * sizeof(double);
+      TFFT_CUDA(cudaMalloc(&p->sig_acc, acc));
+      TFFT_CUDA(cudaMemset(p->sig_acc, 0, acc));
+      TFFT_CUDA(cudaMalloc(&p->part_cnt, (size_t)p->vgroups * sizeof(unsigned)));
+      TFFT_CUDA(cudaMemset(p->part_cnt, 0, (size_t)p->vgroups * sizeof(unsigned)));
+      p->workspace_bytes += (int64_t)(acc + (size_t)p->vgroups * sizeof(unsigned));
+    }
+    TFFT_CUDA(cudaMalloc(&p->ws_c1, p->cap_fix * sig));
+    TFFT_CUDA(cudaMalloc(&p->ws_acc, p->cap_fix * sig));
+    p->workspace_bytes += 2 * p->cap_fix * (int64_t)sig;
+  } else if (p->abft) {
     TFFT_CUDA(cudaMalloc(&p->rec_in, sizeof(RecIn) * p->vgroups * p->slots_in));
     TFFT_CUDA(cudaMalloc(&p->rec_out, sizeof(RecOut) * p->vgroups * p->slots_out));
     p->vsplit = verify_split(p->slots_in + p->slots_out, p->vgroups, p->sms);
@@ -908,7 +937,7 @@ PassParams base_params(const tfft_plan_s* p, int i) {
   a.wk_im = nmod3 == 1 ? 0.86602540378443864676 : (nmod3 == 2 ? -0.86602540378443864676 : 0.0);
   if (nmod3 == 0) a.wk_re = 0.0;
   a.rvec = p->rvec; a.rseed = p->rseed; a.wtab = p->wtab;
-  a.per_signal = p->one_sided;
+  a.sigrec = p->sigrec;
   a.conj_in = p->inverse && i == 0;
   a.conj_out = p->inverse && i == p->passes - 1;
   a.out_scale = (p->normalize && i == p->passes - 1) ? 1.0 / (double)p->n : 1.0;
@@ -1016,7 +1045,15 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
       a.abft_out = p->abft && i == p->passes - 1;
       a.slots = (i == 0) ? p->slots_in : p->slots_out;
       if (p->passes == 1) a.slots = p->slots_in;
-      if (p->abft) {
+      if (p->abft && p->sigrec) {
+        // records of signal b0 = vgroup0 vG onwards
+        const int64_t b0 = vgroup0 * p->vG;
+        const size_t rin = p->dtype == TFFT_C64 ? sizeof(SigIn<float>) : sizeof(SigIn<double>);
+        const size_t rout = p->dtype == TFFT_C64 ? sizeof(SigOut<float>) : sizeof(SigOut<double>);
+        a.sig_in = static_cast<unsigned char*>(p->sig_in) + (size_t)b0 * p->sslots_in * rin;
+        a.sig_out = static_cast<unsigned char*>(p->sig_out) + (size_t)b0 * p->sslots_out * rout;
+        a.sig_slots = (i == 0) ? p->sslots_in : p->sslots_out;
+      } else if (p->abft) {
         a.rec_in = p->rec_in + vgroup0 * p->slots_in;
         a.rec_out = p->rec_out + vgroup0 * p->slots_out;
       }
@@ -1166,6 +1203,23 @@ int exec_range(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
     v.lists = p->lists; v.counters = p->counters; v.log = p->log; v.exec_index = p->execs;
     v.max_blocks = 8 * p->sms;
     v.split = p->vsplit; v.part_acc = p->part_acc; v.part_cnt = p->part_cnt;
+    if (p->sigrec) {
+      const int64_t b0s = vg0 * p->vG;
+      const size_t rin = p->dtype == TFFT_C64 ? sizeof(SigIn<float>) : sizeof(SigIn<double>);
+      const size_t rout = p->dtype == TFFT_C64 ? sizeof(SigOut<float>) : sizeof(SigOut<double>);
+      v.sigrec = 1;
+      v.dtype = p->dtype == TFFT_C64 ? 0 : 1;
+      v.sig_in = static_cast<const unsigned char*>(p->sig_in) + (size_t)b0s * p->sslots_in * rin;
+      v.sig_out = static_cast<const unsigned char*>(p->sig_out) + (size_t)b0s * p->sslots_out * rout;
+      v.sig_slots_in = p->sslots_in; v.sig_slots_out = p->sslots_out;
+      v.sig_split = p->sig_split;
+      v.sig_acc = p->sig_acc ? p->sig_acc + b0s * kSigAcc : nullptr;
+      v.part_cnt = p->part_cnt ? p->part_cnt + vg0 : nullptr;
+      // a threshold never below that of signals whose every value is the
+      // smallest normal number of the element type
+      const double tiny = p->dtype == TFFT_C64 ? 1.1754943508222875e-38 : 2.2250738585072014e-308;
+      v.tau_floor = v.kappa_u_log2n_sqrtn * std::sqrt((double)p->n) * tiny;
+    }
     FixParams f{};
     f.n = p->n; f.batch = nb; f.group = p->vG; f.dtype = p->dtype;
     f.in = in; f.out = out; f.soff = p->soff; f.ws_c1 = p->ws_c1; f.ws_acc = p->ws_acc; f.lists = p->lists;

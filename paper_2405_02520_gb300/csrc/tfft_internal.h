@@ -46,6 +46,16 @@ struct RecOut {
   double pad0, pad1;
 };
 
+// Per-signal checksum records (the tile kernels, when every pass that
+// encodes runs on them): the partial sums of one (signal, slot) -- a warp's
+// share of one tile of that signal -- in the element type's precision.
+//   input side (first pass):  w^T x_b and ||x_b||^2 over the share;
+//   output side (last pass):  r^T y_b over the share.
+// The verification adds a signal's slots in FP64, tests every signal on its
+// own, and forms the group checksums X e_1, X e_3 (Section III) from them.
+template <typename real> struct SigIn { real sr, si, en, pad; };
+template <typename real> struct SigOut { real tr, ti; };
+
 struct Counters {
   unsigned long long detected, corrected, recomputed, uncorrectable;
   unsigned long long log_total, execs;
@@ -174,7 +184,12 @@ struct PassParams {
   // inverse / normalised transforms: conj on load (first pass), conj and
   // scale on store (last pass); the checksums see the forward transform
   int conj_in, conj_out;
-  int per_signal;         // one-sided ABFT: one checksum record set per signal (group = 1)
+  // per-signal records (sigrec = 1, tile kernels): this pass's records of
+  // signal b at slot k are sig_in / sig_out[b sig_slots + k]
+  int sigrec;
+  void* sig_in;           // SigIn<real>
+  void* sig_out;          // SigOut<real>
+  int64_t sig_slots;
   double out_scale;       // 1 unless normalising on the last pass
   int log2C, log2LO, log2LB;   // log2 of C, LO and line_blocks (all powers of two; v3 kernels)
   FaultSite fault;
@@ -270,8 +285,25 @@ struct VerifyParams {
   int split;                    // blocks per group (1: one block strides over groups)
   double* part_acc;             // ngroups x kVerifyAcc
   unsigned* part_cnt;           // ngroups
+  // per-signal records (sigrec = 1): signal b's records are sig_in[b sig_slots_in + k]
+  // and sig_out[b sig_slots_out + k]; dtype 0 float, 1 double
+  int sigrec;
+  int dtype;
+  const void* sig_in;
+  const void* sig_out;
+  int64_t sig_slots_in, sig_slots_out;
+  // signals with many records: `sig_split` blocks per signal add their slice
+  // into sig_acc[b] (kSigAcc sums) and count themselves in part_cnt[g]; the
+  // last block of a group decides it and restores the sums and the count
+  int sig_split;
+  double* sig_acc;              // batch x kSigAcc
+  double tau_floor;             // smallest threshold (the element type's tiny values)
 };
 constexpr int kVerifyAcc = 12;
+constexpr int kSigAcc = 6;
+// records a signal may hold for the one-thread-per-signal verification
+constexpr int64_t kSigSerialMax = 256;
+int sig_split_of(int64_t recs, int64_t batch, int sms);
 // blocks per group for a group of `recs` records when there are `ngroups`
 // groups on `sms` multiprocessors (1 = no split)
 int verify_split(int64_t recs, int64_t ngroups, int sms);

@@ -28,21 +28,28 @@ def tol(n, dtype):
     return (2e-6 if dtype == t.TFFT_C64 else 1e-14) * max(1, int(np.log2(n)))
 
 
-def rel_rows(y, ref):
-    with np.errstate(all="ignore"):
-        e = np.linalg.norm(y.astype(np.complex128) - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
-    return np.where(np.isfinite(e), e, np.inf)
-
-
 def run_campaign(n, batch, dtype=t.TFFT_C64, faults=100, seed=0, bits=None, kappa=0.0,
                  vector=t.TFFT_R_SIGNED_WANG, mode=t.TFFT_FAULT_BITFLIP):
+    """`faults` single-fault execs at random sites.  Each fault runs twice:
+    with correction off (detect only), to classify it against the oracle, and
+    with correction on.  The oracle's FP64 transform of the batch is computed
+    once on the host and kept on the device, where each exec's per-signal
+    relative L2 error against it is formed (only those numbers come back)."""
     import torch
     w = 32 if dtype == t.TFFT_C64 else 64
     x = (uniform_batch(n, batch, seed=seed) if dtype == t.TFFT_C64
          else normal_batch(n, batch, seed=seed))
-    ref = oracle.fft(x.astype(np.complex128))
+    ref = torch.from_numpy(oracle.fft(x.astype(np.complex128))).cuda()
+    ref_norm = torch.linalg.vector_norm(ref, dim=1)
     xt = torch.from_numpy(x).cuda()
     yt = torch.empty_like(xt)
+
+    def row_errors():
+        with torch.no_grad():
+            e = torch.linalg.vector_norm(yt.to(torch.complex128) - ref, dim=1) / ref_norm
+        e = e.cpu().numpy()
+        return np.where(np.isfinite(e), e, np.inf)
+
     plans = {flag: t.tfft_plan_ex(n, batch, dtype, t.TFFT_ABFT_TWO_SIDED, kappa=kappa,
                                   detect_only=flag, checksum_vector=vector)
              for flag in (True, False)}
@@ -53,7 +60,7 @@ def run_campaign(n, batch, dtype=t.TFFT_C64, faults=100, seed=0, bits=None, kapp
            "faults": 0, "harmful": 0, "harmful_detected": 0, "harmful_located": 0,
            "harmful_corrected": 0, "benign": 0, "benign_detected": 0, "benign_output_ok": 0,
            "clear": 0, "clear_detected": 0, "clear_corrected": 0, "marginal": 0, "marginal_missed": 0,
-           "missed": [], "by_stage": {}}
+           "marginal_detected": 0, "missed": [], "by_stage": {}, "max_corrected_err": 0.0}
     tl = tol(n, dtype)
     for k in range(faults):
         p = int(rng.integers(info["passes"]))
@@ -74,18 +81,20 @@ def run_campaign(n, batch, dtype=t.TFFT_C64, faults=100, seed=0, bits=None, kapp
             after = t.tfft_report_ex(plan)
             ev, _ = t.tfft_fault_log(plan, 1)
             det = after["detected"] > before["detected"]
-            res[flag] = (yt.cpu().numpy(), det, ev[-1]["signal"] if det and ev else None)
-        y_unc, det, loc = res[True]
-        y_cor = res[False][0]
-        err = rel_rows(y_unc[sig:sig + 1], ref[sig:sig + 1])[0]
+            res[flag] = (row_errors(), det, ev[-1]["signal"] if det and ev else None)
+        err_unc, det, loc = res[True]
+        err_cor = res[False][0]
+        err = err_unc[sig]
         harmful = err > tl
-        ok = bool(np.all(rel_rows(y_cor, ref) <= tl))
+        ok = bool(np.all(err_cor <= tl))
+        out["max_corrected_err"] = max(out["max_corrected_err"], float(np.max(err_cor)))
         if err > 2 * tl:                  # harmful by a margin
             out["clear"] += 1
             out["clear_detected"] += det
             out["clear_corrected"] += ok
         elif harmful:                     # within a factor of two of the tolerance
             out["marginal"] += 1
+            out["marginal_detected"] += det
             out["marginal_missed"] += not det
         key = f"p{p}s{stage}"
         bs = out["by_stage"].setdefault(key, [0, 0])
@@ -96,9 +105,9 @@ def run_campaign(n, batch, dtype=t.TFFT_C64, faults=100, seed=0, bits=None, kapp
             out["harmful_detected"] += det
             out["harmful_located"] += (loc == sig)
             out["harmful_corrected"] += ok
-            if not (det and ok):
+            if not (det and ok and loc == sig):
                 bs[1] += 1
-                out["missed"].append(site)
+                out["missed"].append(dict(site, err=float(err)))
         else:
             out["benign"] += 1
             out["benign_detected"] += det

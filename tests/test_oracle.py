@@ -428,3 +428,110 @@ def test_fault_emulation_stage_flip_spreads_over_its_residue_class(n, stage, ele
     assert abs(delta) > 1e-3                      # the flip changed the value
     expect = np.where(k % L == m0, delta * phase, 0.0)
     assert np.max(np.abs(diff - expect)) <= 1e-9 * abs(delta)
+
+
+# ------------------------------------------------ per-signal residuals
+def _group(n, g, seed, dtype=np.complex128):
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(-1, 1, (g, n)) + 1j * rng.uniform(-1, 1, (g, n))).astype(dtype)
+
+
+@pytest.mark.parametrize("n,g", [(64, 16), (1024, 16), (4096, 7)])
+def test_signal_residuals_encode_to_the_group_checksums(n, g):
+    """The right-side encodings of the per-signal residuals are the group
+    residuals computed the other way round (right side first, then the left
+    dot products): sum_b d_b = T1 - S1 and sum_b (b+1) d_b = T2 - S2."""
+    r, w = abft.vectors(n, "signed_wang", seed=20240502)
+    xg = _group(n, g, n + g)
+    yg = oracle.fft(xg)
+    yg[g // 2, 3] += 0.25 - 0.5j                  # any output, faulty or not
+    d, e = abft.signal_residuals(xg, yg, w, r)
+    cs = abft.group_checksums(xg, yg, w=w, r=r)
+    scale = np.abs(cs.T1) + np.abs(cs.S1) + 1.0
+    assert abs(np.sum(d) - (cs.T1 - cs.S1)) <= 1e-12 * scale
+    assert abs(np.sum(np.arange(1, g + 1) * d) - (cs.T2 - cs.S2)) <= 1e-12 * g * scale
+    assert np.allclose(e, np.sum(np.abs(xg) ** 2, axis=1))
+
+
+@pytest.mark.parametrize("n,g", [(8, 1), (16, 4), (64, 8)])
+def test_per_signal_every_site_detected_located_corrected(n, g):
+    """Brute force over every (signal, output element) site: an exact-arithmetic
+    fault of size 1e-3 of the signal's norm is detected by its own signal's
+    test, named, and the correction restores the clean output."""
+    r, w = abft.vectors(n, "signed_wang", seed=20240502)
+    xg = _group(n, g, 3 * n + g)
+    yc = oracle.fft(xg)
+    for b in range(g):
+        for k in range(n):
+            yf = yc.copy()
+            yf[b, k] += 1e-3 * np.linalg.norm(yc[b])
+            v = abft.verify_group_signals(xg, yf, w, r, n, 2.0 ** -52, 2.0)
+            assert v.detected and v.flagged == [b] and v.located == b, (b, k)
+            fixed = abft.correct_group(xg, yf, b)
+            assert np.linalg.norm(fixed - yc) <= 1e-10 * np.linalg.norm(yc)
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 256, 4096])
+def test_per_signal_threshold_sits_above_fp32_rounding_noise(n):
+    """Clean groups whose outputs carry FP32 rounding (the oracle's FP32
+    radix-2 emulation): no signal and no group is flagged with kappa = 2 and
+    the largest per-signal ratio |d_b| / tau_b stays well below one."""
+    rng = np.random.default_rng(12)
+    r, w = abft.vectors(n, "signed_wang", seed=20240502)
+    worst = 0.0
+    for _ in range(20):
+        xg = (rng.uniform(-1, 1, (16, n)) + 1j * rng.uniform(-1, 1, (16, n))).astype(np.complex64)
+        yg = np.stack([oracle.fft_faulty(xg[b], 32) for b in range(16)])
+        x64 = xg.astype(np.complex128)
+        v = abft.verify_group_signals(x64, yg, w, r, n, 2.0 ** -24, 2.0)
+        assert not v.detected
+        d, e = abft.signal_residuals(x64, yg, w, r)
+        worst = max(worst, float(np.max(np.abs(d) / (abft.threshold(n, 1.0, 2.0 ** -24, 2.0) * np.sqrt(e)))))
+    assert worst < 0.6
+
+
+def test_per_signal_test_catches_a_spread_fault_the_group_test_misses():
+    """A fault spread over two outputs of one signal with a small projection on
+    r (|r^T e| = 0.1 |delta|) and 1.5 times the tolerance in size: the group
+    residual stays below the group threshold (it carries the rounding of all
+    sixteen signals), the faulty signal's own residual exceeds its threshold
+    (four times lower), so the per-signal scheme names and corrects it."""
+    n, g = 256, 16
+    u, kappa = 2.0 ** -24, 2.0
+    r, w = abft.vectors(n, "signed_wang", seed=20240502)
+    rng = np.random.default_rng(5)
+    xg = (rng.uniform(-1, 1, (g, n)) + 1j * rng.uniform(-1, 1, (g, n))).astype(np.complex64)
+    x64 = xg.astype(np.complex128)
+    yg = np.stack([oracle.fft_faulty(xg[b], 32) for b in range(g)])
+    ref = oracle.fft(x64)
+    b, k1, k2, eps = 9, 17, 140, 0.1
+    tol = 2e-6 * np.log2(n)
+    delta = 1.5 * tol * np.linalg.norm(ref[b]) / np.sqrt(2.0)
+    e = np.zeros(n, dtype=np.complex128)
+    e[k1] = delta
+    e[k2] = -delta * (r[k1] / r[k2]) * (1.0 - eps)
+    yf = yg.copy()
+    yf[b] += e
+    err = np.linalg.norm(yf[b] - ref[b]) / np.linalg.norm(ref[b])
+    assert err > tol                                       # harmful
+    assert abs(r @ e) < 0.11 * abs(delta)                  # small projection
+    grp = abft.verify_group(abft.group_checksums(x64, yf, w=w, r=r), n, g, u, kappa)
+    assert not grp.detected                                # the group test alone misses it
+    v = abft.verify_group_signals(x64, yf, w, r, n, u, kappa)
+    assert v.detected and v.flagged == [b] and v.located == b
+    res = abft.run(x64, yf, group=g, u=u, kappa=kappa, kind="signed_wang", seed=20240502, per_signal=True)
+    assert res.located == {0: b}
+    assert np.linalg.norm(res.y[b] - ref[b]) / np.linalg.norm(ref[b]) <= tol
+
+
+def test_per_signal_two_faulty_signals_are_not_located():
+    """Two signals whose own tests fail (outside the single-event model): the
+    group is detected but not located, so it is recomputed."""
+    n, g = 64, 8
+    r, w = abft.vectors(n, "signed_wang", seed=20240502)
+    xg = _group(n, g, 77)
+    yf = oracle.fft(xg)
+    yf[2, 5] += 1.0
+    yf[6, 40] -= 0.5j
+    v = abft.verify_group_signals(xg, yf, w, r, n, 2.0 ** -52, 2.0)
+    assert v.detected and v.flagged == [2, 6] and v.located == -1
