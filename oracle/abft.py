@@ -250,6 +250,18 @@ def verify_group_signals(xg: np.ndarray, yg: np.ndarray, w: np.ndarray, r: np.nd
                          group_tau=float(tau_g), quotient=q)
 
 
+def last_pass_vector(n: int, n_last: int, seed: int) -> tuple:
+    """(r2, u2) of the second check across the last pass of a multi-pass
+    transform.  The last pass takes the line of output class L (outputs
+    L + M k, M = N / n_last) from its input z[L] by an n_last-point DFT, so
+    r2^T y = sum_L u2[L] . z[L] with u2[L][m] = sum_k r2[L + M k] w^(m k)
+    (w = e^{-2 pi i / n_last}).  r2 is the signed e_Wang vector of `seed`."""
+    r2 = random_left_vector(n, seed) * left_vector(n)
+    m_cls = n // n_last
+    rows = r2.reshape(n_last, m_cls).T            # rows[L][k] = r2[L + M k]
+    return r2, _fft(rows)
+
+
 def locate_nonfinite(xg: np.ndarray, yg: np.ndarray, r=None, w=None) -> int:
     """When the group residual is not finite (a value or a checksum sum
     overflowed) the quotient is undefined.  The faulty column is then the

@@ -302,23 +302,37 @@ __device__ void decide_sig_group(const VerifyParams& v, int64_t g, int64_t gsize
   v.log[slot % kLogRing] = ev;
 }
 
-// Adds signal j's (0-based within group g) sums to the group.
-__device__ __forceinline__ void sig_accumulate(const VerifyParams& v, SigGroup& c, int j, double sr, double si,
-                                               double en, double tr, double ti) {
+// Adds signal j's (0-based within group g) sums to the group: q[0..4] =
+// w^T x, ||x||^2, r^T y; q[5..8] = r2^T y, u2^T z of the second check when
+// the plan has it.
+__device__ __forceinline__ void sig_accumulate(const VerifyParams& v, SigGroup& c, int j, const double* q) {
+  const double sr = q[0], si = q[1], en = q[2], tr = q[3], ti = q[4];
   const double dr = tr - sr, di = ti - si;
   const double d = sqrt(dr * dr + di * di);
   const double tb = tau_of(v, en);
-  const bool fin = isfinite(d);
-  c.en += fin ? en : 0.0;
-  if (!fin || d > tb) {
-    if (c.nflag == 0 || j < c.flagj) { c.flagj = j; c.fres = d; c.ftau = tb; }
+  bool fin = isfinite(d);
+  bool fail = !fin || d > tb;
+  double fres = d, ftau = tb;
+  if (v.chk2) {
+    // the last pass on its own, against the second left vector
+    const double er = q[5] - q[7], ei = q[6] - q[8];
+    const double d2 = sqrt(er * er + ei * ei);
+    const double t2 = fmax(v.kappa_u_chk2 * sqrt(fmax(en, 0.0)), v.tau_floor);
+    const bool fin2 = isfinite(d2);
+    if (!fail && (!fin2 || d2 > t2)) { fail = true; fres = d2; ftau = t2; }
+    fin = fin && fin2;
+    if (!fail) c.cmax = fmax(c.cmax, t2 > 0 ? d2 / t2 : 0.0);
+  }
+  c.en += isfinite(d) ? en : 0.0;
+  if (fail) {
+    if (c.nflag == 0 || j < c.flagj) { c.flagj = j; c.fres = fres; c.ftau = ftau; }
     c.flagmax = max(c.flagmax, j);
     c.nflag++;
     c.nonf += fin ? 0 : 1;
   } else {
     c.cmax = fmax(c.cmax, tb > 0 ? d / tb : 0.0);
   }
-  if (fin) {
+  if (isfinite(d)) {
     c.d1r += dr; c.d1i += di;
     c.d2r = fma((double)(j + 1), dr, c.d2r);
     c.d2i = fma((double)(j + 1), di, c.d2i);
@@ -365,6 +379,7 @@ __device__ void verify_sig_serial(const VerifyParams& v, int lanes, unsigned lon
   const int64_t per_block = blockDim.x / lanes;
   const SigIn<real>* rin = reinterpret_cast<const SigIn<real>*>(v.sig_in);
   const SigOut<real>* rout = reinterpret_cast<const SigOut<real>*>(v.sig_out);
+  const SigChk<real>* rchk = reinterpret_cast<const SigChk<real>*>(v.sig_chk);
   for (int64_t g0 = (int64_t)blockIdx.x * per_block; g0 < v.ngroups; g0 += (int64_t)gridDim.x * per_block) {
     const int64_t g = g0 + threadIdx.x / lanes;
     SigGroup c = sig_group_zero();
@@ -374,18 +389,25 @@ __device__ void verify_sig_serial(const VerifyParams& v, int lanes, unsigned lon
       gsize = min((int64_t)v.group, v.batch - gb);
       for (int64_t j = lane; j < gsize; j += lanes) {
         const int64_t b = gb + j;
-        double sr = 0, si = 0, en = 0, tr = 0, ti = 0;
+        double q[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         const SigIn<real>* pi = rin + b * v.sig_slots_in;
         for (int64_t k = 0; k < v.sig_slots_in; k++) {
           const SigIn<real> r = pi[k];
-          sr += (double)r.sr; si += (double)r.si; en += (double)r.en;
+          q[0] += (double)r.sr; q[1] += (double)r.si; q[2] += (double)r.en;
         }
         const SigOut<real>* po = rout + b * v.sig_slots_out;
         for (int64_t k = 0; k < v.sig_slots_out; k++) {
           const SigOut<real> r = po[k];
-          tr += (double)r.tr; ti += (double)r.ti;
+          q[3] += (double)r.tr; q[4] += (double)r.ti;
         }
-        sig_accumulate(v, c, (int)j, sr, si, en, tr, ti);
+        if (v.chk2) {
+          const SigChk<real>* pc = rchk + b * v.sig_slots_out;
+          for (int64_t k = 0; k < v.sig_slots_out; k++) {
+            const SigChk<real> r = pc[k];
+            q[5] += (double)r.tr; q[6] += (double)r.ti; q[7] += (double)r.sr; q[8] += (double)r.si;
+          }
+        }
+        sig_accumulate(v, c, (int)j, q);
       }
     }
     for (int off = lanes >> 1; off > 0; off >>= 1) sig_group_merge(c, sig_group_shfl(c, off));
@@ -399,17 +421,19 @@ __device__ void verify_sig_serial(const VerifyParams& v, int lanes, unsigned lon
 // on another) and restores sig_acc and the count for the next exec.
 template <typename real>
 __device__ void verify_sig_split(const VerifyParams& v, unsigned long long& clean_max) {
-  __shared__ double sred[8][5];
+  constexpr int NQ = 9;
+  __shared__ double sred[8][NQ];
   __shared__ int s_last;
   const SigIn<real>* rin = reinterpret_cast<const SigIn<real>*>(v.sig_in);
   const SigOut<real>* rout = reinterpret_cast<const SigOut<real>*>(v.sig_out);
+  const SigChk<real>* rchk = reinterpret_cast<const SigChk<real>*>(v.sig_chk);
   const int64_t split = v.sig_split;
   const int64_t nunits = v.batch * split;
   for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
     const int64_t b = u / split, sl = u - b * split;
     const int64_t i0 = v.sig_slots_in * sl / split, i1 = v.sig_slots_in * (sl + 1) / split;
     const int64_t o0 = v.sig_slots_out * sl / split, o1 = v.sig_slots_out * (sl + 1) / split;
-    double a[5] = {0, 0, 0, 0, 0};
+    double a[NQ] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t k = i0 + threadIdx.x; k < i1; k += blockDim.x) {
       const SigIn<real> r = rin[b * v.sig_slots_in + k];
       a[0] += (double)r.sr; a[1] += (double)r.si; a[2] += (double)r.en;
@@ -417,22 +441,26 @@ __device__ void verify_sig_split(const VerifyParams& v, unsigned long long& clea
     for (int64_t k = o0 + threadIdx.x; k < o1; k += blockDim.x) {
       const SigOut<real> r = rout[b * v.sig_slots_out + k];
       a[3] += (double)r.tr; a[4] += (double)r.ti;
+      if (v.chk2) {
+        const SigChk<real> c = rchk[b * v.sig_slots_out + k];
+        a[5] += (double)c.tr; a[6] += (double)c.ti; a[7] += (double)c.sr; a[8] += (double)c.si;
+      }
     }
 #pragma unroll
-    for (int q = 0; q < 5; q++)
+    for (int q = 0; q < NQ; q++)
       for (int off = 16; off > 0; off >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], off);
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0)
-      for (int q = 0; q < 5; q++) sred[w][q] = a[q];
+      for (int q = 0; q < NQ; q++) sred[w][q] = a[q];
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int q = 0; q < 5; q++) {
+      for (int q = 0; q < NQ; q++) {
         double t = 0.0;
         for (int ww = 0; ww < (int)(blockDim.x >> 5); ww++) t += sred[ww][q];
         a[q] = t;
       }
       double* acc = v.sig_acc + b * kSigAcc;
-      for (int q = 0; q < 5; q++) atomicAdd(acc + q, a[q]);
+      for (int q = 0; q < NQ; q++) atomicAdd(acc + q, a[q]);
       __threadfence();
       const int64_t g = b / v.group;
       const int64_t gsize = min((int64_t)v.group, v.batch - g * v.group);
@@ -442,9 +470,9 @@ __device__ void verify_sig_split(const VerifyParams& v, unsigned long long& clea
         SigGroup c = sig_group_zero();
         for (int64_t j = 0; j < gsize; j++) {
           double* aj = v.sig_acc + (g * v.group + j) * kSigAcc;
-          sig_accumulate(v, c, (int)j, __ldcg(aj + 0), __ldcg(aj + 1), __ldcg(aj + 2), __ldcg(aj + 3),
-                         __ldcg(aj + 4));
-          for (int q = 0; q < 5; q++) aj[q] = 0.0;
+          double q[NQ];
+          for (int k = 0; k < NQ; k++) { q[k] = __ldcg(aj + k); aj[k] = 0.0; }
+          sig_accumulate(v, c, (int)j, q);
         }
         v.part_cnt[g] = 0u;
         decide_sig_group(v, g, gsize, c, clean_max);
@@ -605,6 +633,20 @@ __global__ void c128_to_c64_kernel(const double2* a, float2* b, int64_t n) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     b[k] = float2{(float)a[k].x, (float)a[k].y};
+}
+
+__global__ void gather_classes_kernel(const double2* src, double2* dst, int64_t M, int64_t nl) {
+  const int64_t n = M * nl;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t L = i / nl, k = i - L * nl;
+    dst[i] = src[L + M * k];
+  }
+}
+
+cudaError_t launch_gather_classes(const void* src, void* dst, int64_t M, int64_t nl, cudaStream_t s) {
+  gather_classes_kernel<<<fix_grid(M * nl, 1), 256, 0, s>>>(reinterpret_cast<const double2*>(src),
+                                                          reinterpret_cast<double2*>(dst), M, nl);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gen_signs(void* r, int64_t n, unsigned long long seed, cudaStream_t s) {

@@ -180,6 +180,12 @@ __device__ __forceinline__ void warp_records(const Partials<real>& a, const Pass
   }
 }
 
+// Last-pass records with the second check: [r^T y | r2^T y, u2^T z] of the
+// warp's share of the tile, one SigOut and one SigChk record per (signal, slot).
+template <typename real>
+__device__ __forceinline__ void sig_flush_chk(const Partials<real>& a, const PassParams& p, long long sig,
+                                              long long slot);
+
 // Recursive halving over the lanes of a shuffle group: with V values held
 // and the next exchange at lane distance OFF, a lane keeps the half of its
 // values selected by its bit OFF and adds its partner's copy of that half;
@@ -240,6 +246,20 @@ __device__ __forceinline__ void sig_flush(const Partials<real>& a, const PassPar
     if (idx >= O && idx < O + 2)
       reinterpret_cast<real*>(reinterpret_cast<SigOut<real>*>(p.sig_out) + sig * p.sig_slots + slot)[idx - O] = v[0];
   }
+}
+
+template <typename real>
+__device__ __forceinline__ void sig_flush_chk(const Partials<real>& a, const PassParams& p, long long sig,
+                                              long long slot) {
+  real v[8] = {a.t1r, a.t1i, (real)0, (real)0, a.t2r, a.t2i, a.s2r, a.s2i};
+  const int lane = threadIdx.x & 31;
+  int idx = 0;
+  Halve<real, 8, 16>::run(v, lane, idx);
+  if (lane & 3) return;
+  if (idx < 2)
+    reinterpret_cast<real*>(reinterpret_cast<SigOut<real>*>(p.sig_out) + sig * p.sig_slots + slot)[idx] = v[0];
+  else if (idx >= 4)
+    reinterpret_cast<real*>(reinterpret_cast<SigChk<real>*>(p.sig_chk) + sig * p.sig_slots + slot)[idx - 4] = v[0];
 }
 
 // The chunks of one thread block and their tiles, as TileCursor, for the v3
@@ -652,6 +672,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
   // a line produces the outputs k = j0 + q TPL, q < E, of its line.
   cT wv[E];
   unsigned smask = 0;           // sign bit of r_k for each of the thread's outputs
+  unsigned smask2 = 0;          // ... of r2_k (second check, last pass)
   int k0 = 0;                   // (k of output q = 0) mod 3
   Partials<real> acc;
   bool setup_done = false;
@@ -659,7 +680,24 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
   // column role), the output side in the last (single or last role): the
   // other side is compiled out of each role
   constexpr bool IN_CK = ROLE != V3_LAST, OUT_CK = ROLE != V3_COLS;
+  // the last pass of a multi-pass plan may carry a second check across
+  // itself: its input z against u2 (held in wv, which the input side of the
+  // whole-transform check does not use in this role), its output against r2
+  constexpr bool CHK2 = ROLE == V3_LAST;
   auto setup_positions = [&](long long hi, long long lo0) {
+    if (CHK2 && p.chk2) {
+      const cT* lt = reinterpret_cast<const cT*>(p.ltab);
+      const long long L = hi * p.out_hi + (lo0 + c0) * p.out_lo;    // the line's first output
+#pragma unroll
+      for (int r = 0; r < E; r++) wv[r] = ldg_c(lt + L * NSUB + j0 + r * G::TPL);
+      smask2 = 0;
+      const long long kp0 = L + (long long)j0 * p.out_es;
+#pragma unroll
+      for (int q = 0; q < E; q++) {
+        const long long kpos = kp0 + (long long)(q * G::TPL) * p.out_es;
+        smask2 |= (unsigned)(splitmix64_at(p.rseed2, (unsigned long long)kpos) >> 63) << q;
+      }
+    }
     if (IN_CK && p.abft_in) {
       const cT* wtab = reinterpret_cast<const cT*>(p.wtab);
       const long long lo = ROLE == V3_SINGLE ? 0 : lo0 + c0;
@@ -793,6 +831,16 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
         if (!p.sigrec) { acc.s2r = fma(wgt, sr, acc.s2r); acc.s2i = fma(wgt, si, acc.s2i); }
         acc.en += en;
       }
+      if (CHK2 && p.chk2) {
+        // u2^T z over this thread's values (the last pass's input)
+        real sr = 0, si = 0;
+#pragma unroll
+        for (int r = 0; r < E; r++) {
+          sr = fma(wv[r].x, v[r].x, sr); sr = fma(-wv[r].y, v[r].y, sr);
+          si = fma(wv[r].x, v[r].y, si); si = fma(wv[r].y, v[r].x, si);
+        }
+        acc.s2r += sr; acc.s2i += si;
+      }
       if (fst == -1) {
 #pragma unroll
         for (int r = 0; r < E; r++)
@@ -881,12 +929,12 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
         for (int q = 0; q < E; q++)
           if (fs.index == j0 + q * G::TPL) v[q] = faulted(v[q], fs);
       }
-      if (OUT_CK && p.abft_out && valid) {
-        // T += sum_q s_q w3^(k0 + q dl) y_q: group the outputs by q mod 3
+      // sum_q s_q w3^(k0 + q dl) y_q for the sign mask m: the outputs grouped by q mod 3
+      auto rsum = [&](unsigned m, real& tr, real& ti) {
         real a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
 #pragma unroll
         for (int q = 0; q < E; q++) {
-          const bool neg = (smask >> q) & 1u;
+          const bool neg = (m >> q) & 1u;
           const real yr = neg ? -v[q].x : v[q].x, yi = neg ? -v[q].y : v[q].y;
           if (q % 3 == 0) { a0r += yr; a0i += yi; }
           else if (q % 3 == 1) { a1r += yr; a1i += yi; }
@@ -894,10 +942,20 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
         }
         const real hr = (real)-0.5, hs = (real)0.86602540378443864676;
         const real s1 = (dl == 1) ? -hs : hs;
-        real tr = a0r + (hr * a1r - s1 * a1i) + (hr * a2r + s1 * a2i);
-        real ti = a0i + (hr * a1i + s1 * a1r) + (hr * a2i - s1 * a2r);
+        tr = a0r + (hr * a1r - s1 * a1i) + (hr * a2r + s1 * a2i);
+        ti = a0i + (hr * a1i + s1 * a1r) + (hr * a2i - s1 * a2r);
         if (k0 == 1) { real x = hr * tr + hs * ti; ti = hr * ti - hs * tr; tr = x; }
         else if (k0 == 2) { real x = hr * tr - hs * ti; ti = hr * ti + hs * tr; tr = x; }
+      };
+      if (CHK2 && p.chk2) {
+        real tr, ti;
+        rsum(smask2, tr, ti);
+        acc.t2r += tr; acc.t2i += ti;
+      }
+      if (OUT_CK && p.abft_out && valid) {
+        // T += r^T y over this thread's outputs
+        real tr, ti;
+        rsum(smask, tr, ti);
         acc.t1r += tr; acc.t1i += ti;
         if (!p.sigrec) {
           acc.t2r = fma(wgt, tr, acc.t2r); acc.t2i = fma(wgt, ti, acc.t2i);
@@ -913,6 +971,9 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
         if constexpr (ROLE == V3_SINGLE) {
           if constexpr (G::WL) sig_flush<real, G::TPL, IN_CK, OUT_CK>(acc, p, b0, 0, valid);
           else sig_flush<real, 32, IN_CK, OUT_CK>(acc, p, b0, warp % G::WPL, valid);
+        } else if (CHK2 && p.chk2) {
+          sig_flush_chk<real>(acc, p, tb, (long long)cur.lb * 8 + warp);
+          acc.t2r = acc.t2i = acc.s2r = acc.s2i = (real)0;
         } else {
           sig_flush<real, 32, IN_CK, OUT_CK>(acc, p, tb, (long long)cur.lb * 8 + warp, true);
         }

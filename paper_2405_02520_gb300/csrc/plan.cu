@@ -153,6 +153,11 @@ struct tfft_plan_s {
   int64_t sslots_in = 1, sslots_out = 1;
   int sig_split = 1;
   double* sig_acc = nullptr;
+  // second check across the last pass (multi-pass plans with per-signal records)
+  int chk2 = 0;
+  void* ltab = nullptr;             // u2[L][n], N entries
+  void* sig_chk = nullptr;
+  unsigned long long rseed2 = 0;
   int vsplit = 1;                   // verification blocks per group
   double* part_acc = nullptr;       // split verification: per-group accumulators
   unsigned* part_cnt = nullptr;
@@ -233,7 +238,8 @@ void free_plan(tfft_plan_s* p) {
   if (p->d2h) cudaStreamDestroy(p->d2h);
   void* bufs[] = {p->tw_sub, p->twN_lo, p->twN_hi, p->wt_lo, p->wt_hi, p->wtab, p->tmp, p->rec_in, p->rec_out,
                   p->lists_mem, p->counters, p->log, p->ws_c1, p->ws_acc, p->stage_in, p->stage_out,
-                  p->err_flag, p->part_acc, p->part_cnt, p->sig_in, p->sig_out, p->sig_acc};
+                  p->err_flag, p->part_acc, p->part_cnt, p->sig_in, p->sig_out, p->sig_acc, p->ltab,
+                  p->sig_chk};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& q : p->pp)
@@ -468,6 +474,11 @@ void plan_slots(tfft_plan_s* p) {
     };
     p->sslots_in = per_signal(f);
     p->sslots_out = per_signal(l);
+    // a multi-pass plan also checks its last pass on its own, against a
+    // second left vector (its table takes N entries, built from 48 N bytes of
+    // temporary memory at plan time: up to 2^26 elements)
+    p->chk2 = p->passes > 1 && p->n <= (int64_t(1) << 26);
+    p->rseed2 = p->rseed + 1ull;
   }
   if (p->one_sided) {          // every signal is its own verification group
     p->vG = 1;
@@ -841,6 +852,54 @@ int plan_wtable(tfft_plan_s* p) {
   return 0;
 }
 
+// u2 for the second check across the last pass: r2_k = s2_k w3^k (signs
+// from SplitMix64 seeded rseed2); the last pass maps its input line with
+// output offset L (a class of k modulo M = N / n_last) to the outputs
+// L + M k by an n_last-point DFT, so u2[L][n] = sum_k r2[L + M k] w_nl^(n k):
+// the classes gathered into rows and transformed by the library's own
+// complex128 path, then rounded to the plan's element type.
+int plan_ltab(tfft_plan_s* p) {
+  if (!p->chk2) return 0;
+  const int64_t n = p->n, nl = p->pp[p->passes - 1].nsub, M = n / nl;
+  void* r = nullptr; void* g = nullptr; void* u = nullptr;
+  cudaError_t e = cudaMalloc(&r, n * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&g, n * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&u, n * 16);
+  if (e == cudaSuccess) e = launch_gen_signs(r, n, p->rseed2, nullptr);
+  if (e == cudaSuccess) e = launch_gather_classes(r, g, M, nl, nullptr);
+  int rc = e == cudaSuccess ? 0 : cuda_fail(e);
+  tfft_plan_t q = nullptr;
+  if (!rc) {
+    tfft_plan_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.n = nl; o.batch = M; o.dtype = TFFT_C128; o.abft_mode = TFFT_ABFT_OFF;
+    rc = tfft_plan_ex(&q, &o);
+  }
+  if (!rc) rc = tfft_exec(q, g, u, nullptr);
+  if (!rc) {
+    e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+  }
+  if (q) tfft_destroy(q);
+  cudaFree(r);
+  cudaFree(g);
+  if (rc) { if (u) cudaFree(u); return rc; }
+  if (p->dtype == TFFT_C64) {
+    void* u32 = nullptr;
+    e = cudaMalloc(&u32, n * 8);
+    if (e == cudaSuccess) e = launch_c128_to_c64(u, u32, n, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    cudaFree(u);
+    if (e != cudaSuccess) { if (u32) cudaFree(u32); return cuda_fail(e); }
+    p->ltab = u32;
+    p->workspace_bytes += n * 8;
+  } else {
+    p->ltab = u;
+    p->workspace_bytes += n * 16;
+  }
+  return 0;
+}
+
 int plan_workspace(tfft_plan_s* p) {
   const size_t sig = (size_t)p->n * p->esize;
   // correction slots: at most 8, within a 1 GiB budget for c1 and the partial sum
@@ -877,6 +936,11 @@ int plan_workspace(tfft_plan_s* p) {
     TFFT_CUDA(cudaMalloc(&p->sig_in, rin * (size_t)p->batch * (size_t)p->sslots_in));
     TFFT_CUDA(cudaMalloc(&p->sig_out, rout * (size_t)p->batch * (size_t)p->sslots_out));
     p->workspace_bytes += (int64_t)(rin * p->batch * p->sslots_in + rout * p->batch * p->sslots_out);
+    if (p->chk2) {
+      const size_t rc2 = p->dtype == TFFT_C64 ? sizeof(SigChk<float>) : sizeof(SigChk<double>);
+      TFFT_CUDA(cudaMalloc(&p->sig_chk, rc2 * (size_t)p->batch * (size_t)p->sslots_out));
+      p->workspace_bytes += (int64_t)(rc2 * p->batch * p->sslots_out);
+    }
     p->sig_split = sig_split_of(p->sslots_in + p->sslots_out, p->batch, p->sms);
     if (p->sig_split > 1) {
       const size_t acc = (size_t)p->batch * kSigAcc * sizeof(double);
@@ -1053,6 +1117,13 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
         a.sig_in = static_cast<unsigned char*>(p->sig_in) + (size_t)b0 * p->sslots_in * rin;
         a.sig_out = static_cast<unsigned char*>(p->sig_out) + (size_t)b0 * p->sslots_out * rout;
         a.sig_slots = (i == 0) ? p->sslots_in : p->sslots_out;
+        if (p->chk2 && i == p->passes - 1) {
+          const size_t rc2 = p->dtype == TFFT_C64 ? sizeof(SigChk<float>) : sizeof(SigChk<double>);
+          a.chk2 = 1;
+          a.sig_chk = static_cast<unsigned char*>(p->sig_chk) + (size_t)b0 * p->sslots_out * rc2;
+          a.ltab = p->ltab;
+          a.rseed2 = p->rseed2;
+        }
       } else if (p->abft) {
         a.rec_in = p->rec_in + vgroup0 * p->slots_in;
         a.rec_out = p->rec_out + vgroup0 * p->slots_out;
@@ -1219,6 +1290,14 @@ int exec_range(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
       // smallest normal number of the element type
       const double tiny = p->dtype == TFFT_C64 ? 1.1754943508222875e-38 : 2.2250738585072014e-308;
       v.tau_floor = v.kappa_u_log2n_sqrtn * std::sqrt((double)p->n) * tiny;
+      if (p->chk2) {
+        const size_t rc2 = p->dtype == TFFT_C64 ? sizeof(SigChk<float>) : sizeof(SigChk<double>);
+        v.chk2 = 1;
+        v.sig_chk = static_cast<const unsigned char*>(p->sig_chk) + (size_t)b0s * p->sslots_out * rc2;
+        // the last pass alone: its n_last-point transform's rounding
+        const int lgl = ilog2(p->pp[p->passes - 1].nsub) + 4;
+        v.kappa_u_chk2 = p->kappa * u * lgl * std::sqrt((double)p->n);
+      }
     }
     FixParams f{};
     f.n = p->n; f.batch = nb; f.group = p->vG; f.dtype = p->dtype;
@@ -1352,6 +1431,7 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   if (!rc) rc = plan_tables(p);
   if (!rc) rc = plan_workspace(p);
   if (!rc) rc = plan_wtable(p);
+  if (!rc) rc = plan_ltab(p);
   if (rc) { free_plan(p); return rc; }
   *out = p;
   return TFFT_SUCCESS;

@@ -55,6 +55,11 @@ struct RecOut {
 // own, and forms the group checksums X e_1, X e_3 (Section III) from them.
 template <typename real> struct SigIn { real sr, si, en, pad; };
 template <typename real> struct SigOut { real tr, ti; };
+// Second check of a multi-pass plan, across its last pass only (the last
+// pass's own input z and output y, a second left vector r2 with independent
+// signs): r2^T y_b and u2^T z_b over the share, u2 the image of r2 through
+// the last pass (per output class L, the DFT of r2 restricted to L).
+template <typename real> struct SigChk { real tr, ti, sr, si; };
 
 struct Counters {
   unsigned long long detected, corrected, recomputed, uncorrectable;
@@ -190,6 +195,13 @@ struct PassParams {
   void* sig_in;           // SigIn<real>
   void* sig_out;          // SigOut<real>
   int64_t sig_slots;
+  // second check across the last pass (chk2 = 1, last pass only): records
+  // sig_chk[b sig_slots + k] (SigChk<real>), u2 = ltab[L nsub + n] for the
+  // line whose outputs start at L, signs of r2 from SplitMix64 seeded rseed2
+  int chk2;
+  void* sig_chk;
+  const void* ltab;
+  unsigned long long rseed2;
   double out_scale;       // 1 unless normalising on the last pass
   int log2C, log2LO, log2LB;   // log2 of C, LO and line_blocks (all powers of two; v3 kernels)
   FaultSite fault;
@@ -298,9 +310,14 @@ struct VerifyParams {
   int sig_split;
   double* sig_acc;              // batch x kSigAcc
   double tau_floor;             // smallest threshold (the element type's tiny values)
+  // second check across the last pass: records sig_chk[b sig_slots_out + k],
+  // threshold kappa u (log2 n_last + 4) sqrt(N) sqrt(E_b)
+  int chk2;
+  const void* sig_chk;
+  double kappa_u_chk2;
 };
 constexpr int kVerifyAcc = 12;
-constexpr int kSigAcc = 6;
+constexpr int kSigAcc = 10;
 // records a signal may hold for the one-thread-per-signal verification
 constexpr int64_t kSigSerialMax = 256;
 int sig_split_of(int64_t recs, int64_t batch, int sms);
@@ -329,6 +346,9 @@ cudaError_t launch_fix_gather(const FixParams& f, cudaStream_t s);
 // r_k = s_k w3^k (SplitMix64 signs) as complex128, and a complex128 -> complex64 copy.
 cudaError_t launch_gen_signs(void* r, int64_t n, unsigned long long seed, cudaStream_t s);
 cudaError_t launch_c128_to_c64(const void* src, void* dst, int64_t n, cudaStream_t s);
+// dst[L nl + k] = src[L + M k] for L < M, k < nl (complex128): the classes of
+// a vector of length M nl laid out as rows
+cudaError_t launch_gather_classes(const void* src, void* dst, int64_t M, int64_t nl, cudaStream_t s);
 cudaError_t launch_fix_apply(const FixParams& f, cudaStream_t s);
 
 }  // namespace tfft

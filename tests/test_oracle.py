@@ -535,3 +535,19 @@ def test_per_signal_two_faulty_signals_are_not_located():
     yf[6, 40] -= 0.5j
     v = abft.verify_group_signals(xg, yf, w, r, n, 2.0 ** -52, 2.0)
     assert v.detected and v.flagged == [2, 6] and v.located == -1
+
+
+@pytest.mark.parametrize("n,n_last", [(64, 8), (1024, 32), (4096, 1024)])
+def test_last_pass_vector_is_the_image_of_r2_through_the_last_pass(n, n_last):
+    """For any last-pass input z (one row per output class L) the last pass's
+    output, written out by its definition y[L + M k] = sum_m z[L][m] w^(m k),
+    satisfies r2^T y = sum_{L, m} u2[L][m] z[L][m]."""
+    r2, u2 = abft.last_pass_vector(n, n_last, seed=20240503)
+    m_cls = n // n_last
+    rng = np.random.default_rng(n)
+    z = rng.standard_normal((m_cls, n_last)) + 1j * rng.standard_normal((m_cls, n_last))
+    k = np.arange(n_last)
+    y = np.empty(n, dtype=np.complex128)
+    for L in range(m_cls):
+        y[L + m_cls * k] = oracle.dft_naive(z[L])
+    assert abs(r2 @ y - np.sum(u2 * z)) <= 1e-9 * np.sqrt(n) * np.linalg.norm(z)
