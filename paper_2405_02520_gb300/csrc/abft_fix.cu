@@ -218,50 +218,198 @@ __global__ void verify_kernel(const VerifyParams v, int lanes_per_group) {
 // Per-signal records (written by the tile kernels): every signal is tested on
 // its own -- d_b = r^T y'_b - w^T x_b against tau_b = kappa u (log2 N + 4)
 // sqrt(N) ||x_b|| -- and the group's two-sided checksums of Section III are
-// formed in FP64 from the same sums: D1 = sum_b d_b = T1 - S1 (right-side
-// vector e_1) and D2 = sum_b (b+1) d_b = T2 - S2 (e_3), tested against the
-// group threshold.  A group is flagged when a signal or the group sum exceeds
-// its threshold (or is not finite).  Location: the one flagged signal; with
-// none flagged (a group-level detection) the quotient D2 / D1 = b* + 1; with
-// several flagged the group is recomputed (outside the single-event model).
-// The quotient is logged in every case.
+// formed from the same sums: D1 = sum_b d_b = T1 - S1 (right-side vector
+// e_1) and D2 = sum_b (b+1) d_b = T2 - S2 (e_3), tested against the group
+// threshold.  Multi-pass plans add a second per-signal test across their
+// last pass (second left vector r2, threshold with log2 n_last).  A group is
+// flagged when a signal or the group sum exceeds its threshold (or is not
+// finite).  Location: the one flagged signal; with none flagged (a group-level
+// detection) the quotient D2 / D1 = b* + 1; with several flagged the group is
+// recomputed (outside the single-event model).  The quotient is logged in
+// every case.
+//
+// Numerics: a signal's records are added with compensated sums in the
+// element type (Neumaier's variant of Kahan summation for complex64), so the
+// sums carry a few units of rounding whatever their length, and the
+// residual is formed from the compensated parts; the tests and the group
+// sums then run in the element type.  Only the cross-block accumulators of
+// the split mode are FP64 (atomics in the L2), and the group's decision
+// converts to FP64 for its log entry.  GB300's FP64 rate is a small fraction
+// of its FP32 rate, and a batch of short signals has a million of them.
+
+template <typename real> struct CSum;
+template <> struct CSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ void merge(const CSum& o) { add(o.s); c += o.c; }
+  __device__ __forceinline__ CSum shfl(int off) const {
+    CSum r;
+    r.s = __shfl_xor_sync(0xffffffffu, s, off);
+    r.c = __shfl_xor_sync(0xffffffffu, c, off);
+    return r;
+  }
+};
+template <> struct CSum<double> {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void merge(const CSum& o) { s += o.s; }
+  __device__ __forceinline__ CSum shfl(int off) const {
+    CSum r;
+    r.s = __shfl_xor_sync(0xffffffffu, s, off);
+    return r;
+  }
+};
+
+// The nine sums of one signal: w^T x (re, im), ||x||^2, r^T y (re, im), and
+// for the second check r2^T y and u2^T z (re, im each).
+constexpr int kSigQ = 9;
+template <typename real>
+struct SigSums {
+  CSum<real> q[kSigQ];
+  __device__ __forceinline__ void merge(const SigSums& o) {
+#pragma unroll
+    for (int k = 0; k < kSigQ; k++) q[k].merge(o.q[k]);
+  }
+  __device__ __forceinline__ SigSums shfl(int off) const {
+    SigSums r;
+#pragma unroll
+    for (int k = 0; k < kSigQ; k++) r.q[k] = q[k].shfl(off);
+    return r;
+  }
+};
+
+// Adds records [k0, k1) of signal b (SigIn / SigOut / SigChk slots k).
+template <typename real>
+__device__ __forceinline__ void sig_add_records(const VerifyParams& v, int64_t b, int64_t i0, int64_t i1,
+                                                int64_t o0, int64_t o1, int64_t step, SigSums<real>& a) {
+  const SigIn<real>* rin = reinterpret_cast<const SigIn<real>*>(v.sig_in) + b * v.sig_slots_in;
+  const SigOut<real>* rout = reinterpret_cast<const SigOut<real>*>(v.sig_out) + b * v.sig_slots_out;
+  for (int64_t k = i0; k < i1; k += step) {
+    const SigIn<real> r = rin[k];
+    a.q[0].add(r.sr); a.q[1].add(r.si); a.q[2].add(r.en);
+  }
+  for (int64_t k = o0; k < o1; k += step) {
+    const SigOut<real> r = rout[k];
+    a.q[3].add(r.tr); a.q[4].add(r.ti);
+  }
+  if (v.chk2) {
+    const SigChk<real> * rc = reinterpret_cast<const SigChk<real>*>(v.sig_chk) + b * v.sig_slots_out;
+    for (int64_t k = o0; k < o1; k += step) {
+      const SigChk<real> r = rc[k];
+      a.q[5].add(r.tr); a.q[6].add(r.ti); a.q[7].add(r.sr); a.q[8].add(r.si);
+    }
+  }
+}
+
+// The group state, merged over its signals.
+template <typename real>
+struct SigGroup {
+  real d1r, d1i, d2r, d2i, en;   // group sums (finite signals only)
+  int nflag, flagj, nonf;        // flagged signals, the lowest flagged index, non-finite ones
+  real cmax;                     // largest clean |d| / tau of the signal tests
+  real fres, ftau;               // residual and threshold of the lowest flagged signal
+  __device__ __forceinline__ void zero() {
+    d1r = d1i = d2r = d2i = en = (real)0;
+    nflag = 0; flagj = 0x7fffffff; nonf = 0;
+    cmax = fres = ftau = (real)0;
+  }
+  __device__ __forceinline__ void merge(const SigGroup& b) {
+    d1r += b.d1r; d1i += b.d1i; d2r += b.d2r; d2i += b.d2i; en += b.en;
+    if (b.nflag > 0 && (nflag == 0 || b.flagj < flagj)) { flagj = b.flagj; fres = b.fres; ftau = b.ftau; }
+    nflag += b.nflag; nonf += b.nonf;
+    cmax = cmax > b.cmax ? cmax : b.cmax;
+  }
+  __device__ __forceinline__ SigGroup shfl(int off) const {
+    SigGroup o;
+    const unsigned m = 0xffffffffu;
+    o.d1r = __shfl_xor_sync(m, d1r, off); o.d1i = __shfl_xor_sync(m, d1i, off);
+    o.d2r = __shfl_xor_sync(m, d2r, off); o.d2i = __shfl_xor_sync(m, d2i, off);
+    o.en = __shfl_xor_sync(m, en, off);
+    o.nflag = __shfl_xor_sync(m, nflag, off); o.flagj = __shfl_xor_sync(m, flagj, off);
+    o.nonf = __shfl_xor_sync(m, nonf, off);
+    o.cmax = __shfl_xor_sync(m, cmax, off);
+    o.fres = __shfl_xor_sync(m, fres, off); o.ftau = __shfl_xor_sync(m, ftau, off);
+    return o;
+  }
+};
+
+// Signal j's (0-based within its group) tests from its sums s[0..8] (value
+// and compensation per sum), added to the group state.
+template <typename real>
+__device__ __forceinline__ void sig_test(const VerifyParams& v, SigGroup<real>& c, int j, const real* hi,
+                                         const real* lo) {
+  // the residual from the compensated parts: (t - s) = (t_hi - s_hi) + (t_lo - s_lo)
+  const real dr = (hi[3] - hi[0]) + (lo[3] - lo[0]);
+  const real di = (hi[4] - hi[1]) + (lo[4] - lo[1]);
+  const real en = hi[2] > (real)0 ? hi[2] : (real)0;
+  const real se = sqrt(en);
+  const real d = sqrt(dr * dr + di * di);
+  real tb = (real)v.kappa_u_log2n_sqrtn * se;
+  if (tb < (real)v.tau_floor) tb = (real)v.tau_floor;
+  const bool fin = isfinite(d);
+  bool fail = !fin || d > tb;
+  real fres = d, ftau = tb, ratio = tb > (real)0 ? d / tb : (real)0;
+  bool nonfin = !fin;
+  if (v.chk2) {
+    // the last pass on its own, against the second left vector
+    const real er = (hi[5] - hi[7]) + (lo[5] - lo[7]);
+    const real ei = (hi[6] - hi[8]) + (lo[6] - lo[8]);
+    const real d2 = sqrt(er * er + ei * ei);
+    real t2 = (real)v.kappa_u_chk2 * se;
+    if (t2 < (real)v.tau_floor) t2 = (real)v.tau_floor;
+    const bool fin2 = isfinite(d2);
+    nonfin = nonfin || !fin2;
+    if (!fail && (!fin2 || d2 > t2)) { fail = true; fres = d2; ftau = t2; }
+    const real r2 = t2 > (real)0 ? d2 / t2 : (real)0;
+    if (r2 > ratio) ratio = r2;
+  }
+  if (fin) {
+    c.en += en;
+    c.d1r += dr; c.d1i += di;
+    c.d2r += (real)(j + 1) * dr;
+    c.d2i += (real)(j + 1) * di;
+  }
+  if (fail) {
+    if (c.nflag == 0 || j < c.flagj) { c.flagj = j; c.fres = fres; c.ftau = ftau; }
+    c.nflag++;
+    c.nonf += nonfin ? 1 : 0;
+  } else if (ratio > c.cmax) {
+    c.cmax = ratio;
+  }
+}
 
 // The decision for group g (one thread): detection, location, work lists,
 // counters and the fault log.
-struct SigGroup {
-  double d1r, d1i, d2r, d2i, en;   // group sums (finite signals only)
-  int nflag, flagj, nonf;          // flagged signals, the lowest flagged index, non-finite ones
-  int flagmax;                     // highest flagged index
-  double cmax;                     // largest clean |d_b| / tau_b
-  double fres, ftau;               // residual and threshold of the lowest flagged signal
-};
-
-__device__ __forceinline__ double tau_of(const VerifyParams& v, double en) {
-  return fmax(v.kappa_u_log2n_sqrtn * sqrt(fmax(en, 0.0)), v.tau_floor);
-}
-
-__device__ void decide_sig_group(const VerifyParams& v, int64_t g, int64_t gsize, const SigGroup& c,
+template <typename real>
+__device__ void decide_sig_group(const VerifyParams& v, int64_t g, int64_t gsize, const SigGroup<real>& c,
                                  unsigned long long& clean_max) {
-  const double res = sqrt(c.d1r * c.d1r + c.d1i * c.d1i);
-  const double tau = tau_of(v, c.en);
+  const real res = sqrt(c.d1r * c.d1r + c.d1i * c.d1i);
+  real tau = (real)v.kappa_u_log2n_sqrtn * sqrt(c.en > (real)0 ? c.en : (real)0);
+  if (tau < (real)v.tau_floor) tau = (real)v.tau_floor;
   const bool gfin = isfinite(res) && isfinite(c.d2r) && isfinite(c.d2i);
   if (c.nflag == 0 && gfin && !(res > tau)) {
-    const double ratio = fmax(tau > 0 ? res / tau : 0.0, c.cmax);
-    clean_max = max(clean_max, (unsigned long long)__double_as_longlong(ratio));
+    real ratio = tau > (real)0 ? res / tau : (real)0;
+    if (c.cmax > ratio) ratio = c.cmax;
+    clean_max = max(clean_max, (unsigned long long)__double_as_longlong((double)ratio));
     return;
   }
   atomicAdd(&v.counters->detected, 1ull);
   const int64_t gb = g * v.group;
   double qr = NAN, qi = NAN;
-  if (gfin && res > 0) {
-    const double den = c.d1r * c.d1r + c.d1i * c.d1i;
-    qr = (c.d2r * c.d1r + c.d2i * c.d1i) / den;
-    qi = (c.d2i * c.d1r - c.d2r * c.d1i) / den;
+  if (gfin && res > (real)0) {
+    const double a = c.d1r, bb = c.d1i, e = c.d2r, f = c.d2i;
+    const double den = a * a + bb * bb;
+    qr = (e * a + f * bb) / den;
+    qi = (f * a - e * bb) / den;
   }
   int64_t bstar = -1;
   if (c.nflag == 1) {
     bstar = c.flagj;                                     // the one signal whose own test failed
-  } else if (c.nflag == 0 && gfin && res > 0) {
+  } else if (c.nflag == 0 && gfin && res > (real)0) {
     const double m = rint(qr);
     if (fabs(qr - m) < 0.25 && fabs(qi) < 0.25 && m >= 1.0 && m <= (double)gsize) bstar = (int64_t)m - 1;
   }
@@ -295,190 +443,88 @@ __device__ void decide_sig_group(const VerifyParams& v, int64_t g, int64_t gsize
   ev.nonfinite = (c.nonf > 0 || !gfin) ? 1 : 0;
   // the located signal's own residual and threshold when one signal failed,
   // else the group's
-  ev.residual = c.nflag == 1 ? c.fres : res;
-  ev.tau = c.nflag == 1 ? c.ftau : tau;
+  ev.residual = (double)(c.nflag == 1 ? c.fres : res);
+  ev.tau = (double)(c.nflag == 1 ? c.ftau : tau);
   ev.q_re = qr;
   ev.q_im = qi;
   v.log[slot % kLogRing] = ev;
 }
 
-// Adds signal j's (0-based within group g) sums to the group: q[0..4] =
-// w^T x, ||x||^2, r^T y; q[5..8] = r2^T y, u2^T z of the second check when
-// the plan has it.
-__device__ __forceinline__ void sig_accumulate(const VerifyParams& v, SigGroup& c, int j, const double* q) {
-  const double sr = q[0], si = q[1], en = q[2], tr = q[3], ti = q[4];
-  const double dr = tr - sr, di = ti - si;
-  const double d = sqrt(dr * dr + di * di);
-  const double tb = tau_of(v, en);
-  bool fin = isfinite(d);
-  bool fail = !fin || d > tb;
-  double fres = d, ftau = tb;
-  if (v.chk2) {
-    // the last pass on its own, against the second left vector
-    const double er = q[5] - q[7], ei = q[6] - q[8];
-    const double d2 = sqrt(er * er + ei * ei);
-    const double t2 = fmax(v.kappa_u_chk2 * sqrt(fmax(en, 0.0)), v.tau_floor);
-    const bool fin2 = isfinite(d2);
-    if (!fail && (!fin2 || d2 > t2)) { fail = true; fres = d2; ftau = t2; }
-    fin = fin && fin2;
-    if (!fail) c.cmax = fmax(c.cmax, t2 > 0 ? d2 / t2 : 0.0);
-  }
-  c.en += isfinite(d) ? en : 0.0;
-  if (fail) {
-    if (c.nflag == 0 || j < c.flagj) { c.flagj = j; c.fres = fres; c.ftau = ftau; }
-    c.flagmax = max(c.flagmax, j);
-    c.nflag++;
-    c.nonf += fin ? 0 : 1;
-  } else {
-    c.cmax = fmax(c.cmax, tb > 0 ? d / tb : 0.0);
-  }
-  if (isfinite(d)) {
-    c.d1r += dr; c.d1i += di;
-    c.d2r = fma((double)(j + 1), dr, c.d2r);
-    c.d2i = fma((double)(j + 1), di, c.d2i);
-  }
-}
-
-__device__ __forceinline__ SigGroup sig_group_zero() {
-  SigGroup c;
-  c.d1r = c.d1i = c.d2r = c.d2i = c.en = 0.0;
-  c.nflag = 0; c.flagj = 0x7fffffff; c.nonf = 0; c.flagmax = -1;
-  c.cmax = 0.0; c.fres = 0.0; c.ftau = 0.0;
-  return c;
-}
-
-// Combines two partial group states (lanes or blocks holding different signals).
-__device__ __forceinline__ void sig_group_merge(SigGroup& a, const SigGroup& b) {
-  a.d1r += b.d1r; a.d1i += b.d1i; a.d2r += b.d2r; a.d2i += b.d2i; a.en += b.en;
-  if (b.nflag > 0 && (a.nflag == 0 || b.flagj < a.flagj)) { a.flagj = b.flagj; a.fres = b.fres; a.ftau = b.ftau; }
-  a.flagmax = max(a.flagmax, b.flagmax);
-  a.nflag += b.nflag; a.nonf += b.nonf;
-  a.cmax = fmax(a.cmax, b.cmax);
-}
-
-__device__ __forceinline__ SigGroup sig_group_shfl(const SigGroup& c, int off) {
-  SigGroup o;
-  const unsigned m = 0xffffffffu;
-  o.d1r = __shfl_xor_sync(m, c.d1r, off); o.d1i = __shfl_xor_sync(m, c.d1i, off);
-  o.d2r = __shfl_xor_sync(m, c.d2r, off); o.d2i = __shfl_xor_sync(m, c.d2i, off);
-  o.en = __shfl_xor_sync(m, c.en, off);
-  o.nflag = __shfl_xor_sync(m, c.nflag, off); o.flagj = __shfl_xor_sync(m, c.flagj, off);
-  o.nonf = __shfl_xor_sync(m, c.nonf, off); o.flagmax = __shfl_xor_sync(m, c.flagmax, off);
-  o.cmax = __shfl_xor_sync(m, c.cmax, off);
-  o.fres = __shfl_xor_sync(m, c.fres, off); o.ftau = __shfl_xor_sync(m, c.ftau, off);
-  return o;
-}
-
-// One thread per signal: `lanes` (a power of two <= 32) consecutive lanes
-// take one group, lane j its signals j, j + lanes, ...; each sums its
-// records in FP64 (four independent partial sums), the lanes combine by
-// shuffles and the group's first lane decides.
+// Few records per signal: `lanes` (a power of two <= 32) consecutive lanes
+// take one group, lane j its signals j, j + lanes, ...; each adds its
+// records, tests the signal, the lanes combine by shuffles and the group's
+// first lane decides.
 template <typename real>
 __device__ void verify_sig_serial(const VerifyParams& v, int lanes, unsigned long long& clean_max) {
   const int lane = threadIdx.x % lanes;
   const int64_t per_block = blockDim.x / lanes;
-  const SigIn<real>* rin = reinterpret_cast<const SigIn<real>*>(v.sig_in);
-  const SigOut<real>* rout = reinterpret_cast<const SigOut<real>*>(v.sig_out);
-  const SigChk<real>* rchk = reinterpret_cast<const SigChk<real>*>(v.sig_chk);
   for (int64_t g0 = (int64_t)blockIdx.x * per_block; g0 < v.ngroups; g0 += (int64_t)gridDim.x * per_block) {
     const int64_t g = g0 + threadIdx.x / lanes;
-    SigGroup c = sig_group_zero();
+    SigGroup<real> c;
+    c.zero();
     int64_t gsize = 0;
     if (g < v.ngroups) {
       const int64_t gb = g * v.group;
       gsize = min((int64_t)v.group, v.batch - gb);
       for (int64_t j = lane; j < gsize; j += lanes) {
-        const int64_t b = gb + j;
-        double q[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        const SigIn<real>* pi = rin + b * v.sig_slots_in;
-        for (int64_t k = 0; k < v.sig_slots_in; k++) {
-          const SigIn<real> r = pi[k];
-          q[0] += (double)r.sr; q[1] += (double)r.si; q[2] += (double)r.en;
-        }
-        const SigOut<real>* po = rout + b * v.sig_slots_out;
-        for (int64_t k = 0; k < v.sig_slots_out; k++) {
-          const SigOut<real> r = po[k];
-          q[3] += (double)r.tr; q[4] += (double)r.ti;
-        }
-        if (v.chk2) {
-          const SigChk<real>* pc = rchk + b * v.sig_slots_out;
-          for (int64_t k = 0; k < v.sig_slots_out; k++) {
-            const SigChk<real> r = pc[k];
-            q[5] += (double)r.tr; q[6] += (double)r.ti; q[7] += (double)r.sr; q[8] += (double)r.si;
-          }
-        }
-        sig_accumulate(v, c, (int)j, q);
+        SigSums<real> a;
+        sig_add_records(v, gb + j, 0, v.sig_slots_in, 0, v.sig_slots_out, 1, a);
+        real hi[kSigQ], lo[kSigQ];
+#pragma unroll
+        for (int k = 0; k < kSigQ; k++) { hi[k] = a.q[k].s; lo[k] = a.q[k].c; }
+        sig_test(v, c, (int)j, hi, lo);
       }
     }
-    for (int off = lanes >> 1; off > 0; off >>= 1) sig_group_merge(c, sig_group_shfl(c, off));
+    for (int off = lanes >> 1; off > 0; off >>= 1) c.merge(c.shfl(off));
     if (g < v.ngroups && lane == 0) decide_sig_group(v, g, gsize, c, clean_max);
   }
 }
 
-// Many records per signal: block u takes slice u % sig_split of signal
-// u / sig_split, adds its FP64 sums into sig_acc[b] and counts itself in
-// part_cnt[g]; the block that completes group g decides it (no block waits
-// on another) and restores sig_acc and the count for the next exec.
+// Many records per signal: warp u takes slice u % sig_split of signal
+// u / sig_split (its lanes stride over the slice), adds its compensated sums
+// into the FP64 accumulators sig_acc[b] and counts itself in part_cnt[g]; the
+// warp that completes group g tests its signals (one lane per signal) and
+// decides it -- no warp waits on another -- and restores sig_acc and the count.
 template <typename real>
 __device__ void verify_sig_split(const VerifyParams& v, unsigned long long& clean_max) {
-  constexpr int NQ = 9;
-  __shared__ double sred[8][NQ];
-  __shared__ int s_last;
-  const SigIn<real>* rin = reinterpret_cast<const SigIn<real>*>(v.sig_in);
-  const SigOut<real>* rout = reinterpret_cast<const SigOut<real>*>(v.sig_out);
-  const SigChk<real>* rchk = reinterpret_cast<const SigChk<real>*>(v.sig_chk);
   const int64_t split = v.sig_split;
   const int64_t nunits = v.batch * split;
-  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t u = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); u < nunits; u += (int64_t)gridDim.x * wpb) {
     const int64_t b = u / split, sl = u - b * split;
     const int64_t i0 = v.sig_slots_in * sl / split, i1 = v.sig_slots_in * (sl + 1) / split;
     const int64_t o0 = v.sig_slots_out * sl / split, o1 = v.sig_slots_out * (sl + 1) / split;
-    double a[NQ] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int64_t k = i0 + threadIdx.x; k < i1; k += blockDim.x) {
-      const SigIn<real> r = rin[b * v.sig_slots_in + k];
-      a[0] += (double)r.sr; a[1] += (double)r.si; a[2] += (double)r.en;
-    }
-    for (int64_t k = o0 + threadIdx.x; k < o1; k += blockDim.x) {
-      const SigOut<real> r = rout[b * v.sig_slots_out + k];
-      a[3] += (double)r.tr; a[4] += (double)r.ti;
-      if (v.chk2) {
-        const SigChk<real> c = rchk[b * v.sig_slots_out + k];
-        a[5] += (double)c.tr; a[6] += (double)c.ti; a[7] += (double)c.sr; a[8] += (double)c.si;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; q++)
-      for (int off = 16; off > 0; off >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], off);
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0)
-      for (int q = 0; q < NQ; q++) sred[w][q] = a[q];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int q = 0; q < NQ; q++) {
-        double t = 0.0;
-        for (int ww = 0; ww < (int)(blockDim.x >> 5); ww++) t += sred[ww][q];
-        a[q] = t;
-      }
+    SigSums<real> a;
+    sig_add_records(v, b, i0 + lane, i1, o0 + lane, o1, 32, a);
+    for (int off = 16; off > 0; off >>= 1) a.merge(a.shfl(off));
+    const int64_t g = b / v.group;
+    const int64_t gsize = min((int64_t)v.group, v.batch - g * v.group);
+    int last = 0;
+    if (lane == 0) {
       double* acc = v.sig_acc + b * kSigAcc;
-      for (int q = 0; q < NQ; q++) atomicAdd(acc + q, a[q]);
+      for (int k = 0; k < kSigQ; k++) atomicAdd(acc + k, (double)a.q[k].s + (double)a.q[k].c);
       __threadfence();
-      const int64_t g = b / v.group;
-      const int64_t gsize = min((int64_t)v.group, v.batch - g * v.group);
-      s_last = atomicAdd(v.part_cnt + g, 1u) == (unsigned)(gsize * split - 1);
-      if (s_last) {
-        __threadfence();
-        SigGroup c = sig_group_zero();
-        for (int64_t j = 0; j < gsize; j++) {
-          double* aj = v.sig_acc + (g * v.group + j) * kSigAcc;
-          double q[NQ];
-          for (int k = 0; k < NQ; k++) { q[k] = __ldcg(aj + k); aj[k] = 0.0; }
-          sig_accumulate(v, c, (int)j, q);
-        }
-        v.part_cnt[g] = 0u;
-        decide_sig_group(v, g, gsize, c, clean_max);
-      }
+      last = atomicAdd(v.part_cnt + g, 1u) == (unsigned)(gsize * split - 1);
+      if (last) __threadfence();
     }
-    __syncthreads();
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) continue;
+    SigGroup<real> c;
+    c.zero();
+    for (int64_t j = lane; j < gsize; j += 32) {
+      double* aj = v.sig_acc + (g * v.group + j) * kSigAcc;
+      double q[kSigQ];
+      for (int k = 0; k < kSigQ; k++) { q[k] = __ldcg(aj + k); aj[k] = 0.0; }
+      real hi[kSigQ], lo[kSigQ];
+      for (int k = 0; k < kSigQ; k++) { hi[k] = (real)q[k]; lo[k] = (real)(q[k] - (double)hi[k]); }
+      sig_test(v, c, (int)j, hi, lo);
+    }
+    for (int off = 16; off > 0; off >>= 1) c.merge(c.shfl(off));
+    if (lane == 0) {
+      v.part_cnt[g] = 0u;
+      decide_sig_group(v, g, gsize, c, clean_max);
+    }
   }
 }
 
@@ -486,7 +532,7 @@ template <typename real>
 __global__ void verify_sig_kernel(const VerifyParams v, int lanes) {
   __shared__ unsigned long long smax[8];
   unsigned long long clean_max = 0;   // bits of the largest clean ratio (a nonnegative double)
-  if (v.sig_split > 1) verify_sig_split<real>(v, clean_max);
+  if (v.sig_split > 0) verify_sig_split<real>(v, clean_max);
   else verify_sig_serial<real>(v, lanes, clean_max);
   for (int off = 16; off > 0; off >>= 1) clean_max = max(clean_max, __shfl_xor_sync(0xffffffffu, clean_max, off));
   if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = clean_max;
@@ -499,12 +545,12 @@ __global__ void verify_sig_kernel(const VerifyParams v, int lanes) {
 }
 
 int sig_split_of(int64_t recs, int64_t batch, int sms) {
-  if (recs <= kSigSerialMax) return 1;
-  // about 2048 records a block, and enough blocks to cover the SMs twice
-  int64_t want = (recs + 2047) / 2048;
-  const int64_t cover = (2 * (int64_t)sms + batch - 1) / batch;
-  want = std::max(want, std::min(cover, (recs + 255) / 256));
-  return (int)std::max<int64_t>(2, std::min<int64_t>(want, 4096));
+  if (recs <= kSigSerialMax) return 0;               // one lane per signal
+  // warps of at most 1024 records, and at least 16 warps per SM in all
+  int64_t want = (recs + 1023) / 1024;
+  const int64_t cover = (16 * (int64_t)sms + batch - 1) / batch;
+  want = std::max(want, std::min(cover, (recs + 127) / 128));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, 1 << 16));
 }
 
 int verify_split(int64_t recs, int64_t ngroups, int sms) {
@@ -522,7 +568,7 @@ cudaError_t launch_verify(const VerifyParams& vin, cudaStream_t s) {
     int lanes = 1;
     while (lanes < v.group && lanes < 32) lanes <<= 1;
     int64_t blocks;
-    if (v.sig_split > 1) blocks = v.batch * v.sig_split;
+    if (v.sig_split > 0) blocks = (v.batch * v.sig_split + threads / 32 - 1) / (threads / 32);
     else blocks = (v.ngroups * lanes + threads - 1) / threads;
     blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)v.max_blocks));
     if (v.dtype == 0) verify_sig_kernel<float><<<(unsigned)blocks, threads, 0, s>>>(v, lanes);

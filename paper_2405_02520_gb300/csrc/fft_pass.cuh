@@ -45,6 +45,7 @@ __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
   return {fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)};
 }
 
+
 // cos(pi m / 8) and sin(pi m / 8) for m = 0..15: the only angles a radix-2^k
 // butterfly with k <= 4 needs.  Values of the trigonometric functions at
 // multiples of pi/8 (cos(pi/8) = sqrt(2 + sqrt 2)/2, sin(pi/8) = sqrt(2 - sqrt 2)/2).

@@ -833,11 +833,23 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
       }
       if (CHK2 && p.chk2) {
         // u2^T z over this thread's values (the last pass's input)
-        real sr = 0, si = 0;
+        real sr, si;
+        if constexpr (sizeof(real) == 4) {
+          float2 P = {0.f, 0.f};
+          float im = 0.f;
 #pragma unroll
-        for (int r = 0; r < E; r++) {
-          sr = fma(wv[r].x, v[r].x, sr); sr = fma(-wv[r].y, v[r].y, sr);
-          si = fma(wv[r].x, v[r].y, si); si = fma(wv[r].y, v[r].x, si);
+          for (int r = 0; r < E; r++) {
+            P = __ffma2_rn(wv[r], v[r], P);
+            im = fmaf(wv[r].x, v[r].y, im); im = fmaf(wv[r].y, v[r].x, im);
+          }
+          sr = P.x - P.y; si = im;
+        } else {
+          sr = 0; si = 0;
+#pragma unroll
+          for (int r = 0; r < E; r++) {
+            sr = fma(wv[r].x, v[r].x, sr); sr = fma(-wv[r].y, v[r].y, sr);
+            si = fma(wv[r].x, v[r].y, si); si = fma(wv[r].y, v[r].x, si);
+          }
         }
         acc.s2r += sr; acc.s2i += si;
       }

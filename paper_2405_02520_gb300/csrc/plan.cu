@@ -151,7 +151,7 @@ struct tfft_plan_s {
   int sigrec = 0;
   void* sig_in = nullptr; void* sig_out = nullptr;
   int64_t sslots_in = 1, sslots_out = 1;
-  int sig_split = 1;
+  int sig_split = 0;
   double* sig_acc = nullptr;
   // second check across the last pass (multi-pass plans with per-signal records)
   int chk2 = 0;
@@ -941,8 +941,8 @@ int plan_workspace(tfft_plan_s* p) {
       TFFT_CUDA(cudaMalloc(&p->sig_chk, rc2 * (size_t)p->batch * (size_t)p->sslots_out));
       p->workspace_bytes += (int64_t)(rc2 * p->batch * p->sslots_out);
     }
-    p->sig_split = sig_split_of(p->sslots_in + p->sslots_out, p->batch, p->sms);
-    if (p->sig_split > 1) {
+    p->sig_split = sig_split_of(p->sslots_in + p->sslots_out * (p->chk2 ? 3 : 1), p->batch, p->sms);
+    if (p->sig_split > 0) {
       const size_t acc = (size_t)p->batch * kSigAcc * sizeof(double);
       TFFT_CUDA(cudaMalloc(&p->sig_acc, acc));
       TFFT_CUDA(cudaMemset(p->sig_acc, 0, acc));

@@ -304,9 +304,10 @@ struct VerifyParams {
   const void* sig_in;
   const void* sig_out;
   int64_t sig_slots_in, sig_slots_out;
-  // signals with many records: `sig_split` blocks per signal add their slice
+  // signals with many records: `sig_split` warps per signal add their slice
   // into sig_acc[b] (kSigAcc sums) and count themselves in part_cnt[g]; the
-  // last block of a group decides it and restores the sums and the count
+  // last warp of a group decides it and restores the sums and the count
+  // (0: one lane per signal adds all its records)
   int sig_split;
   double* sig_acc;              // batch x kSigAcc
   double tau_floor;             // smallest threshold (the element type's tiny values)
@@ -319,7 +320,7 @@ struct VerifyParams {
 constexpr int kVerifyAcc = 12;
 constexpr int kSigAcc = 10;
 // records a signal may hold for the one-thread-per-signal verification
-constexpr int64_t kSigSerialMax = 256;
+constexpr int64_t kSigSerialMax = 48;
 int sig_split_of(int64_t recs, int64_t batch, int sms);
 // blocks per group for a group of `recs` records when there are `ngroups`
 // groups on `sms` multiprocessors (1 = no split)
