@@ -147,6 +147,11 @@ typedef struct tfft_plan_opts {
                            once, the exec's output is not valid and
                            tfft_report returns TFFT_ERR_TIMEOUT; for testing
                            the timeout path                                   */
+    int first_pass_log2; /* two-pass plans: log2 of the first pass's
+                           sub-transform length N1 (the second takes N/N1);
+                           0 the planner's choice; TFFT_ERR_INVALID_ARG when
+                           the plan is not two-pass or a factor is out of
+                           range                                              */
 } tfft_plan_opts;
 
 enum tfft_precision { TFFT_PREC_FP32 = 0, TFFT_PREC_TF32X3 = 1, TFFT_PREC_TF32 = 2, TFFT_PREC_BF16X3 = 3 };
@@ -394,6 +399,17 @@ int tfft_ragged_destroy(tfft_ragged_t r);
  * TFFT_ERR_TIMEOUT if the product did not complete within the wait bound.
  */
 int tfft_tc_selftest(const float *a, const float *bt, float *d, int terms);
+
+/*
+ * tfft_measure_fma_peak -- measures the fused multiply-add throughput of the
+ * current device (no counterpart in the paper; the denominator of the
+ * roofline of transforms the arithmetic units bound, complex128 on GB300):
+ * 8 x 256 threads per SM each run eight independent chains of `iters`
+ * multiply-adds in FP64 (`fp64` = 1) or FP32 (0), timed with CUDA events after
+ * one shorter warm-up launch.  *tflops receives 2 flops per multiply-add over
+ * the elapsed time.  Synchronous.  Allocates and frees one small buffer.
+ */
+int tfft_measure_fma_peak(int fp64, int iters, double *tflops);
 
 /* Static string for a status code. */
 const char *tfft_error_string(int status);

@@ -250,13 +250,22 @@ def verify_group_signals(xg: np.ndarray, yg: np.ndarray, w: np.ndarray, r: np.nd
                          group_tau=float(tau_g), quotient=q)
 
 
-def last_pass_vector(n: int, n_last: int, seed: int) -> tuple:
+def second_left_vector(n: int, kind: str = "signed_wang", seed: int = 0, radix: int = 16) -> np.ndarray:
+    """r2_k = r_k w3^floor(radix k / N): the left vector of :func:`vectors`
+    times a phase that steps with the top bits of k (radix = the radix of the
+    transform's last stage, 16 for complex64 and 8 for complex128 here)."""
+    r, _ = vectors(n, kind, seed)
+    k = np.arange(n, dtype=np.int64)
+    return r * left_vector(radix)[(radix * k) // n]
+
+
+def last_pass_vector(n: int, n_last: int, seed: int, kind: str = "signed_wang", radix: int = 16) -> tuple:
     """(r2, u2) of the second check across the last pass of a multi-pass
     transform.  The last pass takes the line of output class L (outputs
     L + M k, M = N / n_last) from its input z[L] by an n_last-point DFT, so
     r2^T y = sum_L u2[L] . z[L] with u2[L][m] = sum_k r2[L + M k] w^(m k)
-    (w = e^{-2 pi i / n_last}).  r2 is the signed e_Wang vector of `seed`."""
-    r2 = random_left_vector(n, seed) * left_vector(n)
+    (w = e^{-2 pi i / n_last}); r2 is :func:`second_left_vector`."""
+    r2 = second_left_vector(n, kind, seed, radix)
     m_cls = n // n_last
     rows = r2.reshape(n_last, m_cls).T            # rows[L][k] = r2[L + M k]
     return r2, _fft(rows)

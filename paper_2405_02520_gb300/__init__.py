@@ -47,7 +47,7 @@ class PlanOpts(ctypes.Structure):
                 ("detect_only", ctypes.c_int), ("max_faults", ctypes.c_int),
                 ("force_passes", ctypes.c_int), ("checksum_vector", ctypes.c_int),
                 ("checksum_seed", ctypes.c_uint64), ("direction", ctypes.c_int), ("normalize", ctypes.c_int),
-                ("precision", ctypes.c_int), ("wait_polls", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("wait_polls", ctypes.c_int), ("first_pass_log2", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
                                      ctypes.POINTER(I), I64],
                 "tfft_ragged_destroy": [P],
                 "tfft_tc_selftest": [P, P, P, I],
+                "tfft_measure_fma_peak": [I, I, ctypes.POINTER(ctypes.c_double)],
                 "tfft_error_string": [I],
                 "tfft_last_cuda_error": [],
             }
@@ -167,9 +168,10 @@ def tfft_plan_ex(n: int, batch: int, dtype: int = TFFT_C64, abft_mode: int = TFF
                  group: int = 0, kappa: float = 0.0, detect_only: bool = False, max_faults: int = 0,
                  force_passes: int = 0, checksum_vector: int = TFFT_R_SIGNED_WANG, checksum_seed: int = 0,
                  direction: int = TFFT_FORWARD, normalize: bool = False, precision: int = TFFT_PREC_FP32,
-                 wait_polls: int = 0) -> int:
+                 wait_polls: int = 0, first_pass_log2: int = 0) -> int:
     o = PlanOpts(n, batch, dtype, abft_mode, group, kappa, int(detect_only), max_faults, force_passes,
-                 checksum_vector, checksum_seed, direction, int(normalize), precision, wait_polls)
+                 checksum_vector, checksum_seed, direction, int(normalize), precision, wait_polls,
+                 first_pass_log2)
     h = ctypes.c_void_p()
     _check(lib().tfft_plan_ex(ctypes.byref(h), ctypes.byref(o)), "tfft_plan_ex")
     return h.value
@@ -297,6 +299,13 @@ def tfft_tc_selftest(a, bt, d, terms: int) -> None:
 def tfft_exec_noalloc(n: int, batch: int, x, y, stream=None) -> None:
     """Allocation-free two-pass complex64 transform (see include/tfft.h)."""
     _check(lib().tfft_exec_noalloc(n, batch, _ptr(x), _ptr(y), _stream(stream)), "tfft_exec_noalloc")
+
+
+def tfft_measure_fma_peak(fp64: bool, iters: int) -> float:
+    """Measured multiply-add throughput of the current device, TFLOP/s."""
+    v = ctypes.c_double()
+    _check(lib().tfft_measure_fma_peak(int(bool(fp64)), iters, ctypes.byref(v)), "tfft_measure_fma_peak")
+    return v.value
 
 
 def tfft_error_string(code: int) -> str:

@@ -664,12 +664,13 @@ cudaError_t launch_fix_apply(const FixParams& f, cudaStream_t s) {
 }
 
 // ------------------------------------------------ random checksum vector
-__global__ void gen_signs_kernel(double2* r, int64_t n, unsigned long long seed) {
+__global__ void gen_signs_kernel(double2* r, int64_t n, unsigned long long seed, int qdiv, int sign) {
   const double h = 0.86602540378443864676;   // sqrt(3)/2: w3 = -1/2 - i h
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const double s = (splitmix64_at(seed, (unsigned long long)k) >> 63) ? -1.0 : 1.0;
-    const int m = (int)(k % 3);
+    const double s = (sign && (splitmix64_at(seed, (unsigned long long)k) >> 63)) ? -1.0 : 1.0;
+    // w3^k, times w3^floor(qdiv k / n) for the second left vector
+    const int m = (int)((k + (qdiv ? ((int64_t)qdiv * k) / n : 0)) % 3);
     const double re = m == 0 ? 1.0 : -0.5, im = m == 0 ? 0.0 : (m == 1 ? -h : h);
     r[k] = double2{s * re, s * im};
   }
@@ -695,8 +696,8 @@ cudaError_t launch_gather_classes(const void* src, void* dst, int64_t M, int64_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_gen_signs(void* r, int64_t n, unsigned long long seed, cudaStream_t s) {
-  gen_signs_kernel<<<fix_grid(n, 1), 256, 0, s>>>(reinterpret_cast<double2*>(r), n, seed);
+cudaError_t launch_gen_signs(void* r, int64_t n, unsigned long long seed, cudaStream_t s, int qdiv, int sign) {
+  gen_signs_kernel<<<fix_grid(n, 1), 256, 0, s>>>(reinterpret_cast<double2*>(r), n, seed, qdiv, sign);
   return cudaGetLastError();
 }
 

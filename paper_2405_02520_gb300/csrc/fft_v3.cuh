@@ -60,12 +60,13 @@ __host__ __device__ constexpr int v3_tw_offset(int nsub, int e, int stage) {
 // The table is staged in shared memory when it takes at most this many bytes.
 constexpr int kV3TwSmemMax = 8192;
 
-template <typename real, int NSUB, int E, int ROLE>
+template <typename real, int NSUB, int E, int ROLE, int NT = 256>
 struct V3 {
   using cT = typename Cplx<real>::T;
   static constexpr int ES = (int)sizeof(cT);                // 8 or 16 bytes
   static constexpr int NSUBV = NSUB;
-  static constexpr int T = 256;                             // threads per block
+  static constexpr int T = NT;                              // threads per block
+  static constexpr int NW = NT / 32;                        // warps per block
   static constexpr int TILE = T * E;                        // values per tile
   static constexpr int C = TILE / NSUB;                     // lines per tile
   static constexpr int TPL = NSUB / E;                      // threads per line
@@ -394,7 +395,10 @@ constexpr int v3_min_blocks() { return sizeof(real) == 4 ? 2 : 1; }
 template <typename real, int TC>
 constexpr int v3_min_blocks_tc() { return TC == 0 ? v3_min_blocks<real>() : (v3_tc_aliased(TC) ? 2 : 1); }
 
-// 256 threads (eight warps), two blocks per SM for complex64.  Thread 0 starts the first
+// NT = 256 threads (eight warps), two blocks per SM for complex64; the wide
+// form, NT = 512 (sixteen warps, one block per SM), takes tiles of 8192
+// complex64 values so that column and last passes of 512 to 2048 points keep
+// 32- to 128-byte rows.  Thread 0 starts the first
 // nbuf tile loads; afterwards the last warp to finish a tile stores it and
 // refills its buffer with the tile nbuf ahead, so no warp waits for another
 // except on data that has not arrived yet.
@@ -405,10 +409,11 @@ constexpr int v3_min_blocks_tc() { return TC == 0 ? v3_min_blocks<real>() : (v3_
 // matrix -- one product per warpgroup and stage, the accumulator in tensor
 // memory; TC = 1 multiplies TF32-rounded operands, TC = 3 the three-term
 // split (x_hi w_hi + x_hi w_lo + x_lo w_hi) that keeps about 21 bits.
-template <typename real, int NSUB, int E, int ROLE, int TC = 0>
-__global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_kernel(const __grid_constant__ PassParams p) {
-  static_assert(TC == 0 || (sizeof(real) == 4 && E == 16), "tensor-core DFT: complex64, radix 16");
-  using G = V3<real, NSUB, E, ROLE>;
+template <typename real, int NSUB, int E, int ROLE, int TC = 0, int NT = 256>
+__global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() : 1)) fft_v3_kernel(const __grid_constant__ PassParams p) {
+  static_assert(TC == 0 || (sizeof(real) == 4 && E == 16 && NT == 256), "tensor-core DFT: complex64, radix 16");
+  static_assert(NT == 256 || NT == 512, "eight or sixteen warps");
+  using G = V3<real, NSUB, E, ROLE, NT>;
   constexpr bool TCA = v3_tc_aliased(TC);
   constexpr bool BOXA = TCA && ROLE == V3_SINGLE && G::C == 1;
   static_assert(!TCA || 2 * 16384 <= G::SCR * G::ES, "tensor-core operands fit in the line scratch");
@@ -418,7 +423,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
   using cT = typename G::cT;
   static_assert(E % G::PG == 0, "a thread's stage-0 values start on a pad group");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ V3Cursor ldc[8];
+  __shared__ V3Cursor ldc[G::NW];
   __shared__ unsigned arrivals[8];   // per buffer: warps done with the tile, cumulative
   __shared__ unsigned readers[8];    // per buffer: warps done reading the input box, cumulative
   __shared__ unsigned copied[8];     // per buffer: warps done copying the tile out (last pass), cumulative
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
       issued[s]++;
       ld.advance(p);
     }
-    for (int w = 0; w < 8; w++) ldc[w] = ld;
+    for (int w = 0; w < G::NW; w++) ldc[w] = ld;
   }
   // stage twiddles: from the plan's table, staged next to the scratch when small
   const cT* twt = reinterpret_cast<const cT*>(p.tw_stage);
@@ -546,7 +551,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
     if constexpr (G::WL) {
       __syncwarp();
     } else if constexpr (G::WPL * 32 == G::T) {
-      asm volatile("bar.sync 1, 256;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(G::T) : "memory");
     } else {
       asm volatile("bar.sync %0, %1;" ::"r"(2 + c0), "r"(32 * G::WPL) : "memory");
     }
@@ -672,7 +677,6 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
   // a line produces the outputs k = j0 + q TPL, q < E, of its line.
   cT wv[E];
   unsigned smask = 0;           // sign bit of r_k for each of the thread's outputs
-  unsigned smask2 = 0;          // ... of r2_k (second check, last pass)
   int k0 = 0;                   // (k of output q = 0) mod 3
   Partials<real> acc;
   bool setup_done = false;
@@ -682,7 +686,11 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
   constexpr bool IN_CK = ROLE != V3_LAST, OUT_CK = ROLE != V3_COLS;
   // the last pass of a multi-pass plan may carry a second check across
   // itself: its input z against u2 (held in wv, which the input side of the
-  // whole-transform check does not use in this role), its output against r2
+  // whole-transform check does not use in this role), its output against
+  // r2_k = r_k w3^floor(E k / N).  Output q of this thread (k = L + (N/NSUB)
+  // (j0 + q NSUB/E)) has floor(E k / N) = q, so r2 differs from r on the
+  // thread's outputs by w3^(q mod 3): the output side is a second
+  // combination of the sums over q mod 3 that the first check forms.
   constexpr bool CHK2 = ROLE == V3_LAST;
   auto setup_positions = [&](long long hi, long long lo0) {
     if (CHK2 && p.chk2) {
@@ -690,13 +698,6 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
       const long long L = hi * p.out_hi + (lo0 + c0) * p.out_lo;    // the line's first output
 #pragma unroll
       for (int r = 0; r < E; r++) wv[r] = ldg_c(lt + L * NSUB + j0 + r * G::TPL);
-      smask2 = 0;
-      const long long kp0 = L + (long long)j0 * p.out_es;
-#pragma unroll
-      for (int q = 0; q < E; q++) {
-        const long long kpos = kp0 + (long long)(q * G::TPL) * p.out_es;
-        smask2 |= (unsigned)(splitmix64_at(p.rseed2, (unsigned long long)kpos) >> 63) << q;
-      }
     }
     if (IN_CK && p.abft_in) {
       const cT* wtab = reinterpret_cast<const cT*>(p.wtab);
@@ -734,7 +735,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
     cur.chunk = chunk;
     const bool nonempty = cur.decode(p);
     // one checksum record per warp and chunk
-    const long long slot = (long long)(cur.part * p.line_blocks + cur.lb) * 8 + warp;
+    const long long slot = (long long)(cur.part * p.line_blocks + cur.lb) * G::NW + warp;
     if (!nonempty) {
       if (abft && !p.list && !p.sigrec) {
         acc.zero();
@@ -941,33 +942,42 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
         for (int q = 0; q < E; q++)
           if (fs.index == j0 + q * G::TPL) v[q] = faulted(v[q], fs);
       }
-      // sum_q s_q w3^(k0 + q dl) y_q for the sign mask m: the outputs grouped by q mod 3
-      auto rsum = [&](unsigned m, real& tr, real& ti) {
+      if (OUT_CK && p.abft_out && valid) {
+        // T += r^T y over this thread's outputs: sum_q s_q w3^(k0 + q dl) y_q,
+        // the outputs grouped by q mod 3
         real a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
 #pragma unroll
         for (int q = 0; q < E; q++) {
-          const bool neg = (m >> q) & 1u;
+          const bool neg = (smask >> q) & 1u;
           const real yr = neg ? -v[q].x : v[q].x, yi = neg ? -v[q].y : v[q].y;
           if (q % 3 == 0) { a0r += yr; a0i += yi; }
           else if (q % 3 == 1) { a1r += yr; a1i += yi; }
           else { a2r += yr; a2i += yi; }
         }
         const real hr = (real)-0.5, hs = (real)0.86602540378443864676;
+        // rotate (x, y) by w3^k0
+        auto rot = [&](real& x, real& y) {
+          if (k0 == 1) { const real t = hr * x + hs * y; y = hr * y - hs * x; x = t; }
+          else if (k0 == 2) { const real t = hr * x - hs * y; y = hr * y + hs * x; x = t; }
+        };
         const real s1 = (dl == 1) ? -hs : hs;
-        tr = a0r + (hr * a1r - s1 * a1i) + (hr * a2r + s1 * a2i);
-        ti = a0i + (hr * a1i + s1 * a1r) + (hr * a2i - s1 * a2r);
-        if (k0 == 1) { real x = hr * tr + hs * ti; ti = hr * ti - hs * tr; tr = x; }
-        else if (k0 == 2) { real x = hr * tr - hs * ti; ti = hr * ti + hs * tr; tr = x; }
-      };
-      if (CHK2 && p.chk2) {
-        real tr, ti;
-        rsum(smask2, tr, ti);
-        acc.t2r += tr; acc.t2i += ti;
-      }
-      if (OUT_CK && p.abft_out && valid) {
-        // T += r^T y over this thread's outputs
-        real tr, ti;
-        rsum(smask, tr, ti);
+        real tr = a0r + (hr * a1r - s1 * a1i) + (hr * a2r + s1 * a2i);
+        real ti = a0i + (hr * a1i + s1 * a1r) + (hr * a2i - s1 * a2r);
+        rot(tr, ti);
+        if (CHK2 && p.chk2) {
+          // r2 on these outputs: w3^(q dl) w3^(q mod 3) -- group q mod 3 = g
+          // takes w3^(g (dl + 1)): (w3^2, w3) for dl = 1, (1, 1) for dl = 2
+          real ur, ui;
+          if (dl == 1) {
+            ur = a0r + (hr * a1r - hs * a1i) + (hr * a2r + hs * a2i);
+            ui = a0i + (hr * a1i + hs * a1r) + (hr * a2i - hs * a2r);
+          } else {
+            ur = a0r + a1r + a2r;
+            ui = a0i + a1i + a2i;
+          }
+          rot(ur, ui);
+          acc.t2r += ur; acc.t2i += ui;
+        }
         acc.t1r += tr; acc.t1i += ti;
         if (!p.sigrec) {
           acc.t2r = fma(wgt, tr, acc.t2r); acc.t2i = fma(wgt, ti, acc.t2i);
@@ -984,17 +994,17 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
           if constexpr (G::WL) sig_flush<real, G::TPL, IN_CK, OUT_CK>(acc, p, b0, 0, valid);
           else sig_flush<real, 32, IN_CK, OUT_CK>(acc, p, b0, warp % G::WPL, valid);
         } else if (CHK2 && p.chk2) {
-          sig_flush_chk<real>(acc, p, tb, (long long)cur.lb * 8 + warp);
+          sig_flush_chk<real>(acc, p, tb, (long long)cur.lb * G::NW + warp);
           acc.t2r = acc.t2i = acc.s2r = acc.s2i = (real)0;
         } else {
-          sig_flush<real, 32, IN_CK, OUT_CK>(acc, p, tb, (long long)cur.lb * 8 + warp, true);
+          sig_flush<real, 32, IN_CK, OUT_CK>(acc, p, tb, (long long)cur.lb * G::NW + warp, true);
         }
         acc.s1r = acc.s1i = acc.en = acc.t1r = acc.t1i = (real)0;
       }
       if constexpr (G::LM_IN != G::LM_OUT) {
         // every warp has read its input from the box before any output lands there
         if (lane == 0) {
-          const unsigned want = 8u * (wrap + 1u);
+          const unsigned want = (unsigned)G::NW * (wrap + 1u);
           long long it = 0;
           while (ld_acquire(&readers[s]) < want) {
             if (++it >= kWaitLimit || ((it & 1023) == 0 && *abort_flag)) {
@@ -1023,7 +1033,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
         if (lane == 0) {
           const unsigned old = atom_add_acq_rel(&arrivals[s], 1u);
           V3Cursor& ld = ldc[warp];
-          if (old == 8u * wrap + 7u && !*abort_flag) {
+          if (old == (unsigned)G::NW * wrap + (unsigned)(G::NW - 1) && !*abort_flag) {
             issue_store(p, tb, se, hi, lo0, reinterpret_cast<const cT*>(tile));
             bulk_commit();
             if (ld.valid(p)) {
@@ -1043,7 +1053,7 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
         __syncwarp();
         if (lane == 0) {
           red_add_release(&arrivals[s], 1u);
-          const unsigned want = 8u * (wrap + 1u);
+          const unsigned want = (unsigned)G::NW * (wrap + 1u);
           long long it = 0;
           while (ld_acquire(&arrivals[s]) < want) {
             if (++it >= kWaitLimit || ((it & 1023) == 0 && *abort_flag)) {
@@ -1054,12 +1064,12 @@ __global__ void __launch_bounds__(256, (v3_min_blocks_tc<real, TC>())) fft_v3_ke
           }
         }
         __syncwarp();
-        copy_out<G, ROLE>(p, tb, se, hi, lo0, tile, lane, warp * (NSUB / 8), (warp + 1) * (NSUB / 8));
+        copy_out<G, ROLE>(p, tb, se, hi, lo0, tile, lane, warp * (NSUB / G::NW), (warp + 1) * (NSUB / G::NW));
         __syncwarp();
         if (lane == 0) {
           V3Cursor& ld = ldc[warp];
           const unsigned old = atom_add_acq_rel(&copied[s], 1u);
-          if (old == 8u * wrap + 7u && !*abort_flag && ld.valid(p)) {
+          if (old == (unsigned)G::NW * wrap + (unsigned)(G::NW - 1) && !*abort_flag && ld.valid(p)) {
             fence_proxy_async();
             issue_load(p, ld, reinterpret_cast<cT*>(tile), &full[s]);
             issued[s]++;

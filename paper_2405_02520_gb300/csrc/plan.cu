@@ -98,6 +98,7 @@ struct PassPlan {
   int vC = 0;                      // v3 lines per tile
   int vdt = 0;                     // v3 kernel family (launch_v3 dtype code)
   int vtc = 0;                     // v3 tensor-core variant (3 split TF32, 1 TF32), 0 none
+  int vnt = 256;                   // v3 threads per block (256, or 512 for the wide tiles)
   int64_t vLB = 0;                 // v3 line blocks per signal
   unsigned buf_bytes = 0;
   size_t tsmem = 0;
@@ -157,7 +158,6 @@ struct tfft_plan_s {
   int chk2 = 0;
   void* ltab = nullptr;             // u2[L][n], N entries
   void* sig_chk = nullptr;
-  unsigned long long rseed2 = 0;
   int vsplit = 1;                   // verification blocks per group
   double* part_acc = nullptr;       // split verification: per-group accumulators
   unsigned* part_cnt = nullptr;
@@ -349,10 +349,17 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
   // input rows; 32-byte output column runs), which beats three passes for
   // N = 2^19; a 1024-point first pass (32-byte input column runs) does not
   const int64_t LASTMAX2 = c64 ? 2 * NSUBMAX : NSUBMAX;
+  // complex64 two-pass plans run on the 512-thread tiles up to 2048-point
+  // factors (32- to 128-byte rows); measured with the checksums on (2^28
+  // elements), two passes with a 2048-point first pass beat three up to
+  // N = 2^20 (2.26 / 2.48 ms against 2.90 / 2.74 ms at 2^19 / 2^20) and
+  // lose from 2^21 (2.58 against 2.56 ms, 2.76 against 2.49 ms at 2^22)
+  const int64_t FMAX2 = c64 ? 2048 : NSUBMAX;
+  const int64_t TWO_PASS_MAX = c64 ? (int64_t(1) << 20) : (int64_t)NSUBMAX * LASTMAX2;
   int passes;
   if (o->force_passes) passes = o->force_passes;
   else if (n <= TILE) passes = 1;
-  else if (n <= (int64_t)NSUBMAX * LASTMAX2) passes = 2;
+  else if (n <= TWO_PASS_MAX) passes = 2;
   else passes = 3;
   const int m = ilog2(n);
   int mf[3] = {m, 0, 0};
@@ -370,12 +377,28 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
     mf[0] = 8;
     mf[1] = m - 8;
   }
+  // N = 2^19 and 2^20: a 2048-point first pass (512-thread tiles, 32-byte
+  // rows) and a 256- or 512-point last pass
+  if (passes == 2 && c64 && !o->force_passes && (m == 19 || m == 20)) {
+    mf[0] = 11;
+    mf[1] = m - 11;
+  }
+  // the caller's choice of the first factor (two passes)
+  if (o->first_pass_log2) {
+    if (passes != 2 || o->first_pass_log2 < 1 || o->first_pass_log2 >= m) return TFFT_ERR_INVALID_ARG;
+    mf[0] = o->first_pass_log2;
+    mf[1] = m - mf[0];
+  }
   if (passes == 1 && n > TILE) return TFFT_ERR_INVALID_ARG;
   for (int i = 1; i < passes; i++)
     if (mf[i] < 1) return TFFT_ERR_INVALID_ARG;
-  if (passes > 1)
+  if (passes == 2 && c64) {
+    for (int i = 0; i < 2; i++)
+      if ((int64_t(1) << mf[i]) > FMAX2) return TFFT_ERR_INVALID_ARG;
+  } else if (passes > 1) {
     for (int i = 0; i < passes; i++)
       if ((int64_t(1) << mf[i]) > (passes == 2 && i == 1 ? LASTMAX2 : NSUBMAX)) return TFFT_ERR_INVALID_ARG;
+  }
   p->passes = passes;
 
   int G = o->group > 0 ? o->group : 16;
@@ -456,8 +479,8 @@ void plan_slots(tfft_plan_s* p) {
   const PassPlan& f = p->pp[0];
   const PassPlan& l = p->pp[p->passes - 1];
   // v3 writes one record per warp and chunk, the other kernels one per chunk
-  p->slots_in = (int64_t)f.parts * (f.v3 ? f.vLB * 8 : f.line_blocks);
-  p->slots_out = (int64_t)l.parts * (l.v3 ? l.vLB * 8 : l.line_blocks);
+  p->slots_in = (int64_t)f.parts * (f.v3 ? f.vLB * (f.vnt / 32) : f.line_blocks);
+  p->slots_out = (int64_t)l.parts * (l.v3 ? l.vLB * (l.vnt / 32) : l.line_blocks);
   p->vG = p->G;
   p->vgroups = p->ngroups;
   // per-signal records when the passes that encode (the first and the last)
@@ -467,7 +490,7 @@ void plan_slots(tfft_plan_s* p) {
   p->sigrec = p->abft && f.v3 && l.v3;
   if (p->sigrec) {
     auto per_signal = [&](const PassPlan& q) -> int64_t {
-      if (q.role != 0) return q.vLB * 8;
+      if (q.role != 0) return q.vLB * (q.vnt / 32);
       const int E = p->dtype == TFFT_C64 ? 16 : 8;
       const int64_t tpl = q.nsub / E;
       return tpl > 32 ? tpl / 32 : 1;
@@ -478,7 +501,6 @@ void plan_slots(tfft_plan_s* p) {
     // second left vector (its table takes N entries, built from 48 N bytes of
     // temporary memory at plan time: up to 2^26 elements)
     p->chk2 = p->passes > 1 && p->n <= (int64_t(1) << 26);
-    p->rseed2 = p->rseed + 1ull;
   }
   if (p->one_sided) {          // every signal is its own verification group
     p->vG = 1;
@@ -626,23 +648,28 @@ int plan_v3(tfft_plan_s* p) {
   const int vdt = c64 ? 0 : 1;
   const int vtc = p->prec == TFFT_PREC_TF32X3 ? 3
                 : p->prec == TFFT_PREC_BF16X3 ? 2 : (p->prec == TFFT_PREC_TF32 ? 1 : 0);
-  const int64_t E = c64 ? 16 : 8, TILE = 256 * E;
+  const int64_t E = c64 ? 16 : 8;
   const int64_t B = p->batch;
-  for (int i = 0; i < p->passes; i++) {
+  // one pass on the v3 kernel of `nt` threads (tiles of nt E values); false
+  // when that kernel has no instantiation for the pass or its tiles do not fit
+  auto try_v3 = [&](int i, int nt) -> bool {
     PassPlan& q = p->pp[i];
+    const int64_t TILE = nt * E;
+    const bool wide = nt == 512;
     const int64_t nsub = q.nsub;
     const int role = q.lines_are_signals ? 0 : (i == p->passes - 1 ? 2 : 1);
     const int64_t C = TILE / nsub;
-    if (C < 1 || TILE % nsub) continue;
-    if (role == 0 && (C > p->G || p->G % C)) continue;
-    if (role != 0 && (C > q.LO || q.LO % C)) continue;
+    if (C < 1 || TILE % nsub) return false;
+    if (role == 0 && (C > p->G || p->G % C)) return false;
+    if (role != 0 && (C > q.LO || q.LO % C)) return false;
     // chunk indices are 32-bit in the v3 kernels (chunks <= groups x line blocks x G)
-    if (p->ngroups * (q.lines_are_signals ? 1 : q.LO * q.HI / C) * (int64_t)p->G >= (int64_t(1) << 31)) continue;
+    if (p->ngroups * (q.lines_are_signals ? 1 : q.LO * q.HI / C) * (int64_t)p->G >= (int64_t(1) << 31)) return false;
     int bps = 0;
     auto attrs = [&](size_t sm, int* b) {
+      if (wide) return v3_attrs_wide(role, (int)nsub, sm, b);
       return vtc ? v3_attrs_tc(vtc, role, (int)nsub, sm, b) : v3_attrs(vdt, role, (int)nsub, sm, b);
     };
-    if (attrs(48 * 1024, &bps) != cudaSuccess) { cudaGetLastError(); continue; }
+    if (attrs(48 * 1024, &bps) != cudaSuccess) { cudaGetLastError(); return false; }
     TileMap mi{}, mo{};
     MapGeom gi = q.gin, go = q.gout;
     const int64_t rows = std::min<int64_t>(nsub, 256);
@@ -660,7 +687,7 @@ int plan_v3(tfft_plan_s* p) {
     };
     const int64_t N1 = p->pp[0].nsub, M = p->n / N1;
     if (role == 0) {
-      if (nsub * es % 16) continue;
+      if (nsub * es % 16) return false;
       mi.kind = mo.kind = 1; mi.layout = mo.layout = 0; mi.nbox = mo.nbox = 1; mi.nbx = mo.nbx = 1;
       gi = MapGeom{}; go = MapGeom{};
     } else if (role == 1) {
@@ -693,7 +720,7 @@ int plan_v3(tfft_plan_s* p) {
         gi.box[0] = (uint32_t)(S * u); gi.box[1] = (uint32_t)(nsub / S); gi.box[2] = (uint32_t)C;
       } else {
         const int64_t N2 = q.HI;
-        if (nsub * u > 256) continue;
+        if (nsub * u > 256) return false;
         mi.ay = 1; mi.bz = N1; mi.cz = 1;
         gi.rank = 3; gi.dims[0] = nsub * u; gi.dims[1] = N2; gi.dims[2] = B * N1;
         gi.strides[0] = nsub * es; gi.strides[1] = M * es;
@@ -709,25 +736,25 @@ int plan_v3(tfft_plan_s* p) {
         go = MapGeom{}; go.rank = 3; go.dims[0] = N1 * u; go.dims[1] = N2; go.dims[2] = B * N3;
         go.strides[0] = N1 * es; go.strides[1] = N1 * N2 * es; go.box[1] = 1; go.box[2] = (uint32_t)rows;
         // element-major rows along z for the three-pass output: one box of nsub rows
-        if (nsub > 256) continue;
+        if (nsub > 256) return false;
       }
       em(mo, go);
     }
-    if (role != 0 && (!geom_ok(gi) || !geom_ok(go))) continue;
+    if (role != 0 && (!geom_ok(gi) || !geom_ok(go))) return false;
     mi.bytes = mo.bytes = (unsigned)(C * nsub * es);
-    const size_t scr = (size_t)v3_scratch_bytes(vdt, (int)nsub);
+    const size_t scr = wide ? (size_t)v3_wide_scratch_bytes((int)nsub) : (size_t)v3_scratch_bytes(vdt, (int)nsub);
     const unsigned buf = (unsigned)((C * nsub * es + 1023) / 1024 * 1024);
     // complex64 (and the tensor-core forms whose operands sit in the line
     // scratch): two blocks per SM, each with at most 110 KB of dynamic
     // shared memory; complex128 and the split-TF32 form (separate operands):
     // one block per SM
     const size_t fixed = scr + (size_t)v3_twiddle_smem_bytes(vdt, (int)nsub) + (size_t)v3_tc_bytes(vtc) + 1024 + 1024;
-    size_t budget = (c64 && (vtc == 0 || v3_tc_two_blocks(vtc)) ? 110 : 220) * 1024;
+    size_t budget = (c64 && !wide && (vtc == 0 || v3_tc_two_blocks(vtc)) ? 110 : 220) * 1024;
     if (vtc && fixed + 2 * (size_t)buf > budget) budget = 220 * 1024;   // one block per SM
-    if (fixed + 2 * (size_t)buf > budget) continue;
+    if (fixed + 2 * (size_t)buf > budget) return false;
     const int nbuf = (int)std::min<size_t>(4, (budget - fixed) / buf);
     const size_t smem = (size_t)nbuf * buf + fixed;
-    if (attrs(smem, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
+    if (attrs(smem, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); return false; }
     // the occupancy query reports one block of the scratch-aliased
     // tensor-core forms per SM; their registers (128) and shared memory
     // (two blocks of at most 110 KB plus 2 KB of static and reserved
@@ -738,7 +765,17 @@ int plan_v3(tfft_plan_s* p) {
     q.vC = (int)C;
     q.vLB = q.lines_are_signals ? 1 : q.LO * q.HI / C;
     q.map_in = mi; q.map_out = mo; q.gin = gi; q.gout = go;
-    q.nbuf = nbuf; q.buf_bytes = buf; q.tsmem = smem; q.tbps = bps;
+    q.nbuf = nbuf; q.buf_bytes = buf; q.tsmem = smem; q.tbps = bps; q.vnt = nt;
+    return true;
+  };
+  for (int i = 0; i < p->passes; i++) {
+    const PassPlan& q = p->pp[i];
+    const int role = q.lines_are_signals ? 0 : (i == p->passes - 1 ? 2 : 1);
+    // complex64 column and last passes of 512 to 2048 points: the 512-thread
+    // tiles (twice the lines, twice the row bytes) first
+    const bool wide = c64 && !vtc && role != 0 && q.nsub >= 512 && q.nsub <= 2048;
+    if (wide && try_v3(i, 512)) continue;
+    try_v3(i, 256);
   }
   return 0;
 }
@@ -852,8 +889,13 @@ int plan_wtable(tfft_plan_s* p) {
   return 0;
 }
 
-// u2 for the second check across the last pass: r2_k = s2_k w3^k (signs
-// from SplitMix64 seeded rseed2); the last pass maps its input line with
+// u2 for the second check across the last pass: r2_k = r_k w3^floor(E k / N)
+// with E the radix of the last stage, 16 (complex64) or 8 (complex128): the
+// checksum vector times a phase that steps with the top bits of k.  On the E
+// outputs of a last-stage butterfly r2 is r times w3^(q mod 3), so a fault
+// confined to them is seen through two sums of the same random signs at
+// frequencies a third of a cycle apart (correlated by 1/16 and 1/8); the
+// last pass maps its input line with
 // output offset L (a class of k modulo M = N / n_last) to the outputs
 // L + M k by an n_last-point DFT, so u2[L][n] = sum_k r2[L + M k] w_nl^(n k):
 // the classes gathered into rows and transformed by the library's own
@@ -865,7 +907,8 @@ int plan_ltab(tfft_plan_s* p) {
   cudaError_t e = cudaMalloc(&r, n * 16);
   if (e == cudaSuccess) e = cudaMalloc(&g, n * 16);
   if (e == cudaSuccess) e = cudaMalloc(&u, n * 16);
-  if (e == cudaSuccess) e = launch_gen_signs(r, n, p->rseed2, nullptr);
+  if (e == cudaSuccess)
+    e = launch_gen_signs(r, n, p->rseed, nullptr, p->dtype == TFFT_C64 ? 16 : 8, p->rvec == RVEC_SIGNED_WANG ? 1 : 0);
   if (e == cudaSuccess) e = launch_gather_classes(r, g, M, nl, nullptr);
   int rc = e == cudaSuccess ? 0 : cuda_fail(e);
   tfft_plan_t q = nullptr;
@@ -1038,8 +1081,9 @@ int launch_pass(tfft_plan_s* p, PassParams& a, int i, int kind, cudaStream_t s) 
   }
   cudaError_t e;
   if (v3)
-    e = q.vtc ? launch_v3_tc(q.vtc, q.role, q.nsub, a, grid, q.tsmem, s)
-              : launch_v3(q.vdt, q.role, q.nsub, a, grid, q.tsmem, s);
+    e = q.vnt == 512 ? launch_v3_wide(q.role, q.nsub, a, grid, q.tsmem, s)
+        : q.vtc      ? launch_v3_tc(q.vtc, q.role, q.nsub, a, grid, q.tsmem, s)
+                     : launch_v3(q.vdt, q.role, q.nsub, a, grid, q.tsmem, s);
   else if (tma)
     e = p->dtype == TFFT_C64 ? launch_tile_f32(a, q.E, grid, q.tsmem, s) : launch_tile_f64(a, q.E, grid, q.tsmem, s);
   else
@@ -1100,7 +1144,7 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
     }
     if (main_exec && p->pp[i].v3) {
       const PassPlan& q = p->pp[i];
-      a.C = q.vC; a.nthreads = 256; a.line_blocks = q.vLB;
+      a.C = q.vC; a.nthreads = q.vnt; a.line_blocks = q.vLB;
       a.nchunks = ng * q.parts * q.vLB;
       a.log2C = ilog2(q.vC); a.log2LO = ilog2(q.LO); a.log2LB = ilog2(q.vLB);
     }
@@ -1122,7 +1166,6 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
           a.chk2 = 1;
           a.sig_chk = static_cast<unsigned char*>(p->sig_chk) + (size_t)b0 * p->sslots_out * rc2;
           a.ltab = p->ltab;
-          a.rseed2 = p->rseed2;
         }
       } else if (p->abft) {
         a.rec_in = p->rec_in + vgroup0 * p->slots_in;
@@ -1397,7 +1440,7 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   if ((o->direction != TFFT_FORWARD && o->direction != TFFT_INVERSE) || (o->normalize != 0 && o->normalize != 1))
     return TFFT_ERR_INVALID_ARG;
   if (o->precision < TFFT_PREC_FP32 || o->precision > TFFT_PREC_BF16X3) return TFFT_ERR_INVALID_ARG;
-  if (o->wait_polls < -1) return TFFT_ERR_INVALID_ARG;
+  if (o->wait_polls < -1 || o->first_pass_log2 < 0) return TFFT_ERR_INVALID_ARG;
   if (o->precision != TFFT_PREC_FP32 && o->dtype != TFFT_C64) return TFFT_ERR_UNSUPPORTED;
   int dev = 0, count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) return TFFT_ERR_NO_DEVICE;

@@ -56,9 +56,11 @@ struct RecOut {
 template <typename real> struct SigIn { real sr, si, en, pad; };
 template <typename real> struct SigOut { real tr, ti; };
 // Second check of a multi-pass plan, across its last pass only (the last
-// pass's own input z and output y, a second left vector r2 with independent
-// signs): r2^T y_b and u2^T z_b over the share, u2 the image of r2 through
-// the last pass (per output class L, the DFT of r2 restricted to L).
+// pass's own input z and output y, a second left vector
+// r2_k = r_k w3^floor(E k / N), E = 16 or 8 the radix of the last stage):
+// r2^T y_b and u2^T z_b over the share, u2
+// the image of r2 through the last pass (per output class L, the DFT of r2
+// restricted to L).
 template <typename real> struct SigChk { real tr, ti, sr, si; };
 
 struct Counters {
@@ -197,11 +199,11 @@ struct PassParams {
   int64_t sig_slots;
   // second check across the last pass (chk2 = 1, last pass only): records
   // sig_chk[b sig_slots + k] (SigChk<real>), u2 = ltab[L nsub + n] for the
-  // line whose outputs start at L, signs of r2 from SplitMix64 seeded rseed2
+  // line whose outputs start at L; r2_k = r_k w3^floor(E k / N), E the radix
+  // of the last stage (16 complex64, 8 complex128)
   int chk2;
   void* sig_chk;
   const void* ltab;
-  unsigned long long rseed2;
   double out_scale;       // 1 unless normalising on the last pass
   int log2C, log2LO, log2LB;   // log2 of C, LO and line_blocks (all powers of two; v3 kernels)
   FaultSite fault;
@@ -231,6 +233,11 @@ cudaError_t launch_v3(int dtype, int role, int nsub, const PassParams& p, int gr
 cudaError_t v3_attrs(int dtype, int role, int nsub, size_t smem, int* blocks_per_sm);
 int v3_scratch_bytes(int dtype, int nsub);
 int v3_twiddle_smem_bytes(int dtype, int nsub);
+// 512-thread v3 kernels (v3_f32_wide.cu, complex64): column (role 1) and last
+// (role 2) passes of 512, 1024 and 2048 points in tiles of 8192 values.
+cudaError_t launch_v3_wide(int role, int nsub, const PassParams& p, int grid, size_t smem, cudaStream_t s);
+cudaError_t v3_attrs_wide(int role, int nsub, size_t smem, int* blocks_per_sm);
+int v3_wide_scratch_bytes(int nsub);
 // Tensor-core variants (v3_tc.cu): tc = 3 split TF32, 1 plain TF32.
 cudaError_t launch_v3_tc(int tc, int role, int nsub, const PassParams& p, int grid, size_t smem, cudaStream_t s);
 cudaError_t v3_attrs_tc(int tc, int role, int nsub, size_t smem, int* blocks_per_sm);
@@ -344,8 +351,11 @@ struct FixParams {
   const int* err_flag;
 };
 cudaError_t launch_fix_gather(const FixParams& f, cudaStream_t s);
-// r_k = s_k w3^k (SplitMix64 signs) as complex128, and a complex128 -> complex64 copy.
-cudaError_t launch_gen_signs(void* r, int64_t n, unsigned long long seed, cudaStream_t s);
+// r_k = s_k w3^k (SplitMix64 signs; s_k = 1 with sign = 0) as complex128 --
+// times w3^floor(qdiv k / n) with qdiv > 0 (the second left vector, qdiv the
+// radix of the last stage) -- and a complex128 -> complex64 copy.
+cudaError_t launch_gen_signs(void* r, int64_t n, unsigned long long seed, cudaStream_t s, int qdiv = 0,
+                             int sign = 1);
 cudaError_t launch_c128_to_c64(const void* src, void* dst, int64_t n, cudaStream_t s);
 // dst[L nl + k] = src[L + M k] for L < M, k < nl (complex128): the classes of
 // a vector of length M nl laid out as rows

@@ -53,7 +53,7 @@ def test_error_strings_and_no_device_status():
 def test_struct_layouts_match_header_sizes():
     """The ctypes mirrors must have the C sizes (8-byte aligned fields)."""
     import paper_2405_02520_gb300 as t
-    assert ctypes.sizeof(t.PlanOpts) == 80
+    assert ctypes.sizeof(t.PlanOpts) == 88
     assert ctypes.sizeof(t.Stats) == 7 * 8
     assert ctypes.sizeof(t.FaultEvent) == 3 * 8 + 2 * 4 + 4 * 8
     assert ctypes.sizeof(t.Fault) == 4 * 4 + 3 * 8 + 8

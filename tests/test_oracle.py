@@ -551,3 +551,31 @@ def test_last_pass_vector_is_the_image_of_r2_through_the_last_pass(n, n_last):
     for L in range(m_cls):
         y[L + m_cls * k] = oracle.dft_naive(z[L])
     assert abs(r2 @ y - np.sum(u2 * z)) <= 1e-9 * np.sqrt(n) * np.linalg.norm(z)
+
+
+def test_second_vector_sees_a_butterfly_fault_independently():
+    """On the sixteen outputs c + q N/16 of a last-stage butterfly, a fault of
+    the butterfly's input m is the tone A w16^(q m).  Its projections on r and
+    on r2 = r w3^floor(16 k / N) are the sums of the same random signs at two
+    frequencies a third of a cycle apart: over all classes and tones both are
+    small together about as often as independent projections would be, and
+    never both below a tenth of the fault's norm.  (The complex128 kernels'
+    last stage has radix 8: r2 = r w3^floor(8 k / N), the same argument.)"""
+    n = 1 << 14
+    r, _ = abft.vectors(n, "signed_wang", seed=20240502)
+    r2 = abft.second_left_vector(n, "signed_wang", seed=20240502)
+    q = np.arange(16)
+    p1, p2 = [], []
+    for c in range(0, n // 16, 7):
+        k = c + q * (n // 16)
+        for m in range(16):
+            tone = np.exp(-2j * np.pi * q * m / 16)
+            p1.append(abs(r[k] @ tone) / 4.0)          # |r^T a| / ||a||
+            p2.append(abs(r2[k] @ tone) / 4.0)
+    p1, p2 = np.array(p1), np.array(p2)
+    small1, small2 = p1 < 0.3, p2 < 0.3
+    joint = np.mean(small1 & small2)
+    assert np.mean(small1) > 0.02 and np.mean(small2) > 0.02      # each alone has a tail
+    assert joint <= 3.0 * np.mean(small1) * np.mean(small2) + 1e-3
+    assert np.max(np.minimum(p1, p2)) > 0.5 and np.min(np.maximum(p1, p2)) > 0.1
+    assert abs(np.corrcoef(p1, p2)[0, 1]) < 0.2
