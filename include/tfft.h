@@ -13,11 +13,17 @@
  * output side with r, where r_j = s_j exp(-2 pi i j / 3) (Wang's e_Wang
  * vector of Section II with seeded random signs s_j = +-1; plain e_Wang is an
  * option), and across each group of G consecutive signals with the all-ones
- * vector and the index weights (1, 2, ..., G).  A silent data corruption in a
- * group is detected from the unweighted checksums, the faulty signal is named
- * by the quotient of the weighted and unweighted residuals, and it is
+ * vector and the index weights (1, 2, ..., G).  The left-side checksums are
+ * formed per signal (d_b = r^T y_b - w^T x_b) and the group's two-sided
+ * residuals from them; a silent data corruption is detected when a signal's
+ * own residual or the group's exceeds its threshold, the faulty signal is
+ * the one whose own test failed (or, for a detection by the group test
+ * alone, the quotient of the weighted and unweighted residuals), and it is
  * corrected by subtracting the batch-checksum divergence
- * (sum_b y'_b - W sum_b x_b) -- no recomputation of that signal.
+ * (sum_b y'_b - W sum_b x_b) -- no recomputation of that signal.  Multi-pass
+ * plans (up to 2^26 points) also check their last pass on its own against a
+ * second left vector r2_j = r_j w3^floor(E j / n), E the radix of that
+ * pass's last stage (16 complex64, 8 complex128).
  *
  * Data layout (all entry points): `batch` signals of `n` complex values,
  * signal-major [batch][n], each value interleaved (re, im); complex64 is two
@@ -104,9 +110,12 @@ typedef struct tfft_plan_opts {
     int abft_mode;
     int group;          /* G: signals per checksum group (default 16)          */
     double kappa;       /* detection threshold constant (default 2); the
-                           threshold is kappa*u*(log2(n)+4)*sqrt(n)*sqrt(E_g), E_g
-                           the group's input energy sum_b ||x_b||^2, u the
-                           unit roundoff of dtype                               */
+                           threshold is kappa*u*(log2(n)+4)*sqrt(n)*sqrt(E),
+                           E the input energy ||x_b||^2 of the signal for its
+                           own test and sum_b ||x_b||^2 of the group for the
+                           group test, u the unit roundoff of dtype (the
+                           second check of a multi-pass plan takes log2 of
+                           its last pass's length in place of log2(n))      */
     int detect_only;    /* 1: detect and locate but leave outputs uncorrected  */
     int max_faults;     /* groups corrected per exec (default: as many as fit
                            a 1 GiB budget, at most 8); more are counted
@@ -204,14 +213,16 @@ int tfft_exec_host(tfft_plan_t p, const void *host_in, void *host_out, tfft_stre
 int tfft_report(tfft_plan_t p, int64_t *detected, int64_t *corrected);
 
 typedef struct tfft_stats {
-    int64_t detected;       /* groups flagged by the residual test             */
+    int64_t detected;       /* groups flagged (a signal's test or the group's)    */
     int64_t corrected;      /* fixed by the checksum correction                */
     int64_t recomputed;     /* fixed by recomputing the whole group            */
     int64_t uncorrectable;  /* detected, not fixed (lists full / detect_only)  */
     int64_t execs;          /* tfft_exec calls since plan / reset              */
     int64_t launches;       /* kernels launched since plan / reset             */
-    double max_clean_ratio; /* largest |T1 - S1| / threshold over the groups
-                               that were NOT flagged (calibration of kappa)     */
+    double max_clean_ratio; /* largest residual / threshold of any test (a
+                               signal's own, its last-pass check, the group's)
+                               in the groups that were NOT flagged
+                               (calibration of kappa)                           */
 } tfft_stats;
 
 int tfft_report_ex(tfft_plan_t p, tfft_stats *stats);
@@ -226,8 +237,9 @@ typedef struct tfft_fault_event {
     int64_t signal;         /* located signal (batch index), -1 if not located  */
     int32_t action;         /* 1 corrected, 2 group recomputed, 3 uncorrected   */
     int32_t nonfinite;      /* the residual or a partial sum was not finite     */
-    double residual;        /* |T1 - S1|                                        */
-    double tau;             /* threshold                                        */
+    double residual;        /* the failing signal's residual when one signal
+                               failed its own test, else |T1 - S1|              */
+    double tau;             /* the threshold it was compared with               */
     double q_re, q_im;      /* quotient (T2 - S2) / (T1 - S1)                   */
 } tfft_fault_event;
 
