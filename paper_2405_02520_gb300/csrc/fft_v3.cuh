@@ -104,14 +104,6 @@ __device__ __forceinline__ uint32_t atom_add_acq_rel(unsigned* a, unsigned v) {
   return old;
 }
 
-__device__ __forceinline__ void red_add_release(unsigned* a, unsigned v) {
-  asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_u32(a)), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* a) {
-  unsigned v;
-  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(a)) : "memory");
-  return v;
-}
 
 // Bounded wait on an mbarrier phase (at most `limit` polls); gives up early
 // once another warp has recorded a timeout in *abort.
@@ -425,7 +417,6 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ V3Cursor ldc[G::NW];
   __shared__ unsigned arrivals[8];   // per buffer: warps done with the tile, cumulative
-  __shared__ unsigned readers[8];    // per buffer: warps done reading the input box, cumulative
   __shared__ unsigned copied[8];     // per buffer: warps done copying the tile out (last pass), cumulative
   __shared__ unsigned issued[8];     // per buffer: tile loads issued into it, cumulative
   __shared__ int s_abort;
@@ -442,7 +433,6 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
     for (int s = 0; s < nbuf; s++) {
       mbar_init(&full[s], 1);
       arrivals[s] = 0;
-      readers[s] = 0;
       copied[s] = 0;
       issued[s] = 0;
     }
@@ -546,6 +536,12 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
   // this thread's line and butterfly index inside the tile
   const int c0 = G::WL ? warp * G::LPW + lane / G::TPL : warp / G::WPL;
   const int j0 = G::WL ? lane % G::TPL : (warp % G::WPL) * 32 + lane;
+
+  // All warps of the block at one point of the same tile (the last pass's
+  // two box hand-overs): a hardware barrier, on which waiting warps take no
+  // issue slots.  Every warp runs the same sequence of tiles, also after a
+  // timed-out wait, so each barrier is reached by all of them.
+  auto tile_sync = [&]() { asm volatile("bar.sync 15, %0;" ::"n"(G::T) : "memory"); };
 
   auto line_sync = [&]() {
     if constexpr (G::WL) {
@@ -799,12 +795,6 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
 #pragma unroll
         for (int r = 0; r < E; r++) v[r].y = -v[r].y;
       }
-      if constexpr (G::LM_IN != G::LM_OUT) {
-        // the output box overlaps other warps' input lines: announce that
-        // this warp's input values are in registers
-        __syncwarp();
-        if (lane == 0) red_add_release(&readers[s], 1u);
-      }
       if (IN_CK && p.abft_in && valid) {
         real sr, si, en;
         if constexpr (sizeof(real) == 4) {
@@ -1002,19 +992,9 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
         acc.s1r = acc.s1i = acc.en = acc.t1r = acc.t1i = (real)0;
       }
       if constexpr (G::LM_IN != G::LM_OUT) {
-        // every warp has read its input from the box before any output lands there
-        if (lane == 0) {
-          const unsigned want = (unsigned)G::NW * (wrap + 1u);
-          long long it = 0;
-          while (ld_acquire(&readers[s]) < want) {
-            if (++it >= kWaitLimit || ((it & 1023) == 0 && *abort_flag)) {
-              *abort_flag = 1;
-              atomicExch(p.err_flag, 1);
-              break;
-            }
-          }
-        }
-        __syncwarp();
+        // the output box overlaps other warps' input lines: every warp has
+        // its input in registers before any output lands there
+        tile_sync();
       }
       if (p.conj_out || p.out_scale != 1.0) {
         const real sc = (real)p.out_scale, si = p.conj_out ? -sc : sc;
@@ -1047,23 +1027,10 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
         __syncwarp();
       } else {
         // the last pass's element-major box is written by all warps: once all
-        // eight have written, each copies out its eighth of the rows with
-        // plain stores, and the last to finish refills the buffer (no store
-        // in flight holds the box)
-        __syncwarp();
-        if (lane == 0) {
-          red_add_release(&arrivals[s], 1u);
-          const unsigned want = (unsigned)G::NW * (wrap + 1u);
-          long long it = 0;
-          while (ld_acquire(&arrivals[s]) < want) {
-            if (++it >= kWaitLimit || ((it & 1023) == 0 && *abort_flag)) {
-              *abort_flag = 1;
-              atomicExch(p.err_flag, 1);
-              break;
-            }
-          }
-        }
-        __syncwarp();
+        // have written, each copies out its share of the rows with plain
+        // stores, and the last to finish refills the buffer (no store in
+        // flight holds the box)
+        tile_sync();
         copy_out<G, ROLE>(p, tb, se, hi, lo0, tile, lane, warp * (NSUB / G::NW), (warp + 1) * (NSUB / G::NW));
         __syncwarp();
         if (lane == 0) {
