@@ -161,6 +161,14 @@ typedef struct tfft_plan_opts {
                            0 the planner's choice; TFFT_ERR_INVALID_ARG when
                            the plan is not two-pass or a factor is out of
                            range                                              */
+    int tile_threads;   /* threads of the tile kernels of complex64 column and
+                           last passes of 512 to 2048 points (FP32): 256 (tiles
+                           of 4096 values, two blocks per SM) or 512 (tiles of
+                           8192, one block per SM, twice the lines a tile and
+                           twice the bytes a row) where that form has a kernel
+                           for the pass, else the other; 0 the planner's
+                           choice; other passes ignore it;
+                           TFFT_ERR_INVALID_ARG for any other value           */
 } tfft_plan_opts;
 
 enum tfft_precision { TFFT_PREC_FP32 = 0, TFFT_PREC_TF32X3 = 1, TFFT_PREC_TF32 = 2, TFFT_PREC_BF16X3 = 3 };
@@ -307,6 +315,10 @@ typedef struct tfft_info {
     int direction;           /* TFFT_FORWARD / TFFT_INVERSE                    */
     int normalize;           /* 1: output scaled by 1/N                        */
     int precision;           /* TFFT_PREC_*                                    */
+    int tile_threads[3];     /* threads a block of each pass's tile kernel
+                                (256 or 512; 0: a pass on the fallback kernels) */
+    int tuned;               /* 1: the pass configuration was taken from the
+                                autotuner's table (tfft_autotune)              */
 } tfft_info;
 
 int tfft_plan_info(tfft_plan_t p, tfft_info *info);
@@ -322,6 +334,47 @@ int tfft_set_timing(tfft_plan_t p, int enable);
 int tfft_timing(tfft_plan_t p, double *ms_per_kind, int64_t *launches_per_kind, int nkinds);
 
 int tfft_destroy(tfft_plan_t p);
+
+/*
+ * Autotuner: the run-time form of the paper's kernel-parameter search
+ * (Section IV-B "Kernel Parameters", Table I: the decomposition of N and the
+ * tile parameters are chosen per N by measurement).  tfft_autotune times,
+ * on the caller's device buffers in[batch][n] and out[batch][n] (not
+ * overlapping, 16-byte aligned, in holding representative finite data) and
+ * stream, every configuration the planner admits for *opts: pass count 1-3,
+ * the first factor of two-pass plans, and 256- or 512-thread tiles for the
+ * complex64 column and last passes of 512 to 2048 points, plus the
+ * planner's own choice.  Each is planned, run twice untimed, then `reps`
+ * (1-1000) times between CUDA events; out is overwritten.  opts must leave
+ * force_passes, first_pass_log2 and tile_threads at 0 (TFFT_ERR_INVALID_ARG
+ * otherwise).  Synchronises the stream.
+ *
+ * The fastest configuration goes into a process-wide table: a later
+ * tfft_plan / tfft_plan_ex whose options leave those three fields at 0 and
+ * match an entry's n, dtype, abft_mode and precision is built with the
+ * entry's configuration (the entry whose batch is nearest in log2; the
+ * plan's tfft_info.tuned is 1).  If the environment variable TFFT_TUNE_CACHE
+ * names a file, the table is first read from it (lines
+ * "tfft-tune-1 n batch dtype abft_mode precision passes first_pass_log2
+ * tile_threads ms"; others are skipped) and every result is appended to it
+ * (a file that cannot be written leaves the in-memory entry in place).
+ */
+typedef struct tfft_tune_result {
+    int passes;              /* the fastest configuration: pass count           */
+    int first_pass_log2;     /* log2 of its first factor (two passes), else 0   */
+    int tile_threads;        /* 256 or 512                                      */
+    int candidates;          /* configurations timed                            */
+    double ms;               /* its mean time per tfft_exec                     */
+    double default_ms;       /* the planner's own choice's time                 */
+} tfft_tune_result;
+
+int tfft_autotune(const tfft_plan_opts *opts, const void *in, void *out, tfft_stream_t stream, int reps,
+                  tfft_tune_result *result);
+/* 1 and *tuned = *opts with the table's configuration when an entry applies
+ * to *opts, 0 when none does; no device work. */
+int tfft_tune_lookup(const tfft_plan_opts *opts, tfft_plan_opts *tuned);
+/* Empties the in-memory table; TFFT_TUNE_CACHE is read again on next use. */
+int tfft_tune_clear(void);
 
 /*
  * tfft_exec_noalloc -- the plain forward transform (no ABFT) of `batch`

@@ -47,7 +47,8 @@ class PlanOpts(ctypes.Structure):
                 ("detect_only", ctypes.c_int), ("max_faults", ctypes.c_int),
                 ("force_passes", ctypes.c_int), ("checksum_vector", ctypes.c_int),
                 ("checksum_seed", ctypes.c_uint64), ("direction", ctypes.c_int), ("normalize", ctypes.c_int),
-                ("precision", ctypes.c_int), ("wait_polls", ctypes.c_int), ("first_pass_log2", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("wait_polls", ctypes.c_int), ("first_pass_log2", ctypes.c_int),
+                ("tile_threads", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -69,6 +70,11 @@ class Fault(ctypes.Structure):
                 ("index", ctypes.c_int64), ("factor", ctypes.c_double)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int), ("first_pass_log2", ctypes.c_int), ("tile_threads", ctypes.c_int),
+                ("candidates", ctypes.c_int), ("ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("batch", ctypes.c_int64), ("dtype", ctypes.c_int),
                 ("abft_mode", ctypes.c_int), ("passes", ctypes.c_int), ("nsub", ctypes.c_int * 3),
@@ -77,7 +83,8 @@ class Info(ctypes.Structure):
                 ("max_faults", ctypes.c_int), ("kappa", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_int64), ("launches_per_exec", ctypes.c_int),
                 ("checksum_vector", ctypes.c_int), ("checksum_seed", ctypes.c_uint64),
-                ("direction", ctypes.c_int), ("normalize", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("direction", ctypes.c_int), ("normalize", ctypes.c_int), ("precision", ctypes.c_int),
+                ("tile_threads", ctypes.c_int * 3), ("tuned", ctypes.c_int)]
 
 
 def lib() -> ctypes.CDLL:
@@ -115,6 +122,9 @@ def lib() -> ctypes.CDLL:
                 "tfft_ragged_destroy": [P],
                 "tfft_tc_selftest": [P, P, P, I],
                 "tfft_measure_fma_peak": [I, I, ctypes.POINTER(ctypes.c_double)],
+                "tfft_autotune": [ctypes.POINTER(PlanOpts), P, P, P, I, ctypes.POINTER(TuneResult)],
+                "tfft_tune_lookup": [ctypes.POINTER(PlanOpts), ctypes.POINTER(PlanOpts)],
+                "tfft_tune_clear": [],
                 "tfft_error_string": [I],
                 "tfft_last_cuda_error": [],
             }
@@ -168,10 +178,10 @@ def tfft_plan_ex(n: int, batch: int, dtype: int = TFFT_C64, abft_mode: int = TFF
                  group: int = 0, kappa: float = 0.0, detect_only: bool = False, max_faults: int = 0,
                  force_passes: int = 0, checksum_vector: int = TFFT_R_SIGNED_WANG, checksum_seed: int = 0,
                  direction: int = TFFT_FORWARD, normalize: bool = False, precision: int = TFFT_PREC_FP32,
-                 wait_polls: int = 0, first_pass_log2: int = 0) -> int:
+                 wait_polls: int = 0, first_pass_log2: int = 0, tile_threads: int = 0) -> int:
     o = PlanOpts(n, batch, dtype, abft_mode, group, kappa, int(detect_only), max_faults, force_passes,
                  checksum_vector, checksum_seed, direction, int(normalize), precision, wait_polls,
-                 first_pass_log2)
+                 first_pass_log2, tile_threads)
     h = ctypes.c_void_p()
     _check(lib().tfft_plan_ex(ctypes.byref(h), ctypes.byref(o)), "tfft_plan_ex")
     return h.value
@@ -306,6 +316,39 @@ def tfft_measure_fma_peak(fp64: bool, iters: int) -> float:
     v = ctypes.c_double()
     _check(lib().tfft_measure_fma_peak(int(bool(fp64)), iters, ctypes.byref(v)), "tfft_measure_fma_peak")
     return v.value
+
+
+def _opts(n: int, batch: int, dtype: int, abft_mode: int, **kw) -> PlanOpts:
+    o = PlanOpts()
+    o.n, o.batch, o.dtype, o.abft_mode = n, batch, dtype, abft_mode
+    for k, v in kw.items():
+        setattr(o, k, int(v) if not isinstance(v, float) else v)
+    return o
+
+
+def tfft_autotune(n: int, batch: int, dtype: int, abft_mode: int, x, y, stream=None, reps: int = 5,
+                  **opts) -> dict:
+    """Times every admissible pass configuration on x -> y and records the
+    fastest in the autotuner's table (see include/tfft.h); returns it."""
+    o = _opts(n, batch, dtype, abft_mode, **opts)
+    r = TuneResult()
+    _check(lib().tfft_autotune(ctypes.byref(o), _ptr(x), _ptr(y), _stream(stream), reps, ctypes.byref(r)),
+           "tfft_autotune")
+    return {f: getattr(r, f) for f, _ in TuneResult._fields_}
+
+
+def tfft_tune_lookup(n: int, batch: int, dtype: int, abft_mode: int, **opts):
+    """The table's configuration for these options as (passes, first_pass_log2,
+    tile_threads), or None."""
+    o = _opts(n, batch, dtype, abft_mode, **opts)
+    t = PlanOpts()
+    rc = lib().tfft_tune_lookup(ctypes.byref(o), ctypes.byref(t))
+    _check(min(rc, 0), "tfft_tune_lookup")
+    return (t.force_passes, t.first_pass_log2, t.tile_threads) if rc == 1 else None
+
+
+def tfft_tune_clear() -> None:
+    _check(lib().tfft_tune_clear(), "tfft_tune_clear")
 
 
 def tfft_error_string(code: int) -> str:

@@ -134,6 +134,8 @@ struct tfft_plan_s {
   int one_sided = 0;                 // per-signal checksums (verification groups of one)
   int prec = TFFT_PREC_FP32;         // arithmetic of the radix-16 butterflies
   long long wait_limit = 1ll << 20;  // polls of a tile-arrival wait
+  int tile_threads = 0;              // column / last passes of 512..2048 points: 0 auto, 256, 512
+  int tuned = 0;                     // the pass configuration came from the autotuner's table
   int vG = 16;                       // signals per verification group
   int64_t vgroups = 0;               // verification groups
   int cap_fix = 1, cap_rec = 1;
@@ -370,12 +372,18 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
   // ... except a 512-point last pass (three radix stages and 64-byte output
   // rows), which runs slower than a 512-point first pass
   if (passes > 1 && mf[passes - 1] == 9 && mf[0] < 9) std::swap(mf[0], mf[passes - 1]);
-  // with the checksums on, N = 2^17 and 2^18 run faster as a 256-point column
-  // pass (whose input checksum costs less than the 512-point one's) and a
-  // 512- or 1024-point last pass: 1.86 / 2.05 ms against 1.91 / 2.12 ms
-  if (passes == 2 && c64 && o->abft_mode != TFFT_ABFT_OFF && !o->force_passes && (m == 17 || m == 18)) {
+  // measured at 2^28 elements (every first factor and tile size timed):
+  // N = 2^17 with the checksums on runs fastest as 256 x 512 (1.97 ms against
+  // 2.01 for 512 x 256, whose 512-point input checksum costs more), without
+  // them as 512 x 256 (1.62 against 1.67); N = 2^18 as 1024 x 256 (2.14 ms on,
+  // 1.76 off, against 2.19 / 1.83 for 512 x 512)
+  if (passes == 2 && c64 && o->abft_mode != TFFT_ABFT_OFF && !o->force_passes && m == 17) {
     mf[0] = 8;
-    mf[1] = m - 8;
+    mf[1] = 9;
+  }
+  if (passes == 2 && c64 && !o->force_passes && m == 18) {
+    mf[0] = 10;
+    mf[1] = 8;
   }
   // N = 2^19 and 2^20: a 2048-point first pass (512-thread tiles, 32-byte
   // rows) and a 256- or 512-point last pass
@@ -771,11 +779,16 @@ int plan_v3(tfft_plan_s* p) {
   for (int i = 0; i < p->passes; i++) {
     const PassPlan& q = p->pp[i];
     const int role = q.lines_are_signals ? 0 : (i == p->passes - 1 ? 2 : 1);
-    // complex64 column and last passes of 512 to 2048 points: the 512-thread
-    // tiles (twice the lines, twice the row bytes) first
+    // complex64 column and last passes of 1024 and 2048 points: the
+    // 512-thread tiles (twice the lines, twice the row bytes) first; 512-point
+    // passes run faster on the 256-thread tiles (two blocks per SM): 0.89
+    // against 0.94 ms (column) and 0.94 against 0.96 ms (last) at 2^28
+    // elements.  The caller's tile_threads reorders the two.
     const bool wide = c64 && !vtc && role != 0 && q.nsub >= 512 && q.nsub <= 2048;
-    if (wide && try_v3(i, 512)) continue;
-    try_v3(i, 256);
+    const bool wide_first = wide && (p->tile_threads == 512 || (p->tile_threads == 0 && q.nsub >= 1024));
+    if (wide_first && try_v3(i, 512)) continue;
+    if (try_v3(i, 256)) continue;
+    if (wide && !wide_first) try_v3(i, 512);
   }
   return 0;
 }
@@ -1422,12 +1435,9 @@ int plan_set_signal_offsets(tfft_plan_t p, const long long* d_off, const int64_t
   return TFFT_SUCCESS;
 }
 
-}  // namespace tfft
-
-// =================================================================== C ABI
-extern "C" {
-
-int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
+// Builds a plan from the options as given (no autotuner table); `tuned`
+// marks a plan whose pass configuration came from that table.
+int plan_create(tfft_plan_t* out, const tfft_plan_opts* o, int tuned) {
   if (!out || !o) return TFFT_ERR_INVALID_ARG;
   *out = nullptr;
   if (!is_pow2(o->n) || o->n > (int64_t(1) << 29) || o->batch < 1) return TFFT_ERR_INVALID_ARG;
@@ -1441,6 +1451,7 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
     return TFFT_ERR_INVALID_ARG;
   if (o->precision < TFFT_PREC_FP32 || o->precision > TFFT_PREC_BF16X3) return TFFT_ERR_INVALID_ARG;
   if (o->wait_polls < -1 || o->first_pass_log2 < 0) return TFFT_ERR_INVALID_ARG;
+  if (o->tile_threads != 0 && o->tile_threads != 256 && o->tile_threads != 512) return TFFT_ERR_INVALID_ARG;
   if (o->precision != TFFT_PREC_FP32 && o->dtype != TFFT_C64) return TFFT_ERR_UNSUPPORTED;
   int dev = 0, count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) return TFFT_ERR_NO_DEVICE;
@@ -1462,6 +1473,8 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   p->prec = o->precision;
   p->normalize = o->normalize;
   p->wait_limit = o->wait_polls == 0 ? (1ll << 20) : (o->wait_polls < 0 ? 0 : (long long)o->wait_polls);
+  p->tile_threads = o->tile_threads;
+  p->tuned = tuned;
   p->device = dev;
   p->sms = prop.multiProcessorCount;
   int rc = plan_build(p, o);
@@ -1478,6 +1491,23 @@ int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
   if (rc) { free_plan(p); return rc; }
   *out = p;
   return TFFT_SUCCESS;
+}
+
+}  // namespace tfft
+
+// =================================================================== C ABI
+extern "C" {
+
+int tfft_plan_ex(tfft_plan_t* out, const tfft_plan_opts* o) {
+  if (!out || !o) return TFFT_ERR_INVALID_ARG;
+  // options that leave the pass configuration to the planner take the
+  // autotuner's entry for this transform when there is one; an entry the
+  // planner does not admit (a cache file from another build) is passed over
+  tfft_plan_opts t;
+  if (!o->force_passes && !o->first_pass_log2 && !o->tile_threads && tune_lookup(o, &t) &&
+      plan_create(out, &t, 1) == TFFT_SUCCESS)
+    return TFFT_SUCCESS;
+  return plan_create(out, o, 0);
 }
 
 int tfft_plan(tfft_plan_t* out, int64_t n, int64_t batch, int dtype, int abft_mode) {
@@ -1701,6 +1731,8 @@ int tfft_plan_info(tfft_plan_t p, tfft_info* info) {
   info->checksum_seed = p->rseed;
   info->direction = p->inverse ? TFFT_INVERSE : TFFT_FORWARD;
   info->precision = p->prec;
+  for (int i = 0; i < 3; i++) info->tile_threads[i] = i < p->passes && p->pp[i].v3 ? p->pp[i].vnt : 0;
+  info->tuned = p->tuned;
   info->normalize = p->normalize;
   return TFFT_SUCCESS;
 }

@@ -7,8 +7,16 @@
 #include <cuda_runtime.h>
 
 struct tfft_plan_s;   // the plan (plan.cu); tfft_plan_t in include/tfft.h
+struct tfft_plan_opts;
 
 namespace tfft {
+
+// A plan built from the options exactly as given, without the autotuner's
+// table (plan.cu); `tuned` marks one whose pass configuration came from it.
+int plan_create(tfft_plan_s** out, const tfft_plan_opts* o, int tuned);
+// The autotuner's entry for these options (tune.cu): true, with *tuned a
+// copy of *o whose pass count, first factor and tile threads are the entry's.
+bool tune_lookup(const tfft_plan_opts* o, tfft_plan_opts* tuned);
 
 // How the butterflies of one radix stage are dealt to the threads of a tile.
 // ROW: consecutive threads take consecutive butterflies of one line (the
