@@ -544,6 +544,98 @@ __global__ void verify_sig_kernel(const VerifyParams v, int lanes) {
   }
 }
 
+// Many signals with a few dozen to a few hundred records each: one block of
+// kVT threads per unit of `gpb` consecutive groups (or one group in rounds
+// of kVT / L signals when a group has more).  L consecutive lanes add one
+// signal's records (lane l takes records l, l + L, ...; L a power of two
+// near the record count, at most 32) and combine by shuffles; the signal
+// sums go to shared memory and the unit's groups are decided there.  No
+// atomics and no cross-block accumulators: the split mode's per-signal
+// FP64 atomics and fences cost more than the records themselves here.
+constexpr int kVT = 256;
+
+// Groups [0, ng) of a one-round unit, signal j of the unit's sums at
+// sm[j 2 kSigQ]: Dl lanes per group (a power of two, at most 32), lane d its
+// signals d, d + Dl, ...; the group's first lane decides.
+template <typename real>
+__device__ void decide_unit(const VerifyParams& v, int64_t g0, int ng, const real* sm,
+                            unsigned long long& clean_max) {
+  int Dl = 1;
+  while (Dl < v.group && Dl < 32) Dl <<= 1;
+  const int per_warp = 32 / Dl;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane / Dl, d = lane % Dl;
+  for (int q0 = warp * per_warp; q0 < ng; q0 += (kVT / 32) * per_warp) {
+    const int q = q0 + sub;
+    SigGroup<real> c;
+    c.zero();
+    int64_t gsize = 0;
+    if (q < ng) {
+      gsize = min((int64_t)v.group, v.batch - (g0 + q) * v.group);
+      for (int64_t j = d; j < gsize; j += Dl) {
+        const real* sj = sm + ((int64_t)q * v.group + j) * 2 * kSigQ;
+        sig_test(v, c, (int)j, sj, sj + kSigQ);
+      }
+    }
+    for (int off = Dl >> 1; off > 0; off >>= 1) c.merge(c.shfl(off));
+    if (q < ng && d == 0) decide_sig_group(v, g0 + q, gsize, c, clean_max);
+  }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kVT, 2) verify_sig_blocks(const VerifyParams v, int lanes) {
+  __shared__ real sm[kVT * 2 * kSigQ];
+  __shared__ unsigned long long smax[kVT / 32];
+  unsigned long long clean_max = 0;   // bits of the largest clean ratio (a nonnegative double)
+  const int L = lanes, spb = kVT / L, gpb = v.sig_gpb;
+  const int t = threadIdx.x, jj = t / L, l = t % L, warp = t >> 5, lane = t & 31;
+  const int64_t nunits = (v.ngroups + gpb - 1) / gpb;
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int64_t g0 = u * gpb;
+    const int ng = (int)min((int64_t)gpb, v.ngroups - g0);
+    const int64_t bfirst = g0 * v.group;
+    const int64_t nsig = min(v.batch, (g0 + ng) * v.group) - bfirst;
+    const int64_t rounds = (nsig + spb - 1) / spb;
+    SigGroup<real> c;                 // a unit of one group in rounds: warp 0 tests, round by round
+    c.zero();
+    for (int64_t r = 0; r < rounds; r++) {
+      const int64_t j = r * spb + jj;
+      SigSums<real> a;
+      if (j < nsig) sig_add_records(v, bfirst + j, l, v.sig_slots_in, l, v.sig_slots_out, L, a);
+      for (int off = L >> 1; off > 0; off >>= 1) a.merge(a.shfl(off));
+      if (l == 0 && j < nsig) {
+        real* dst = sm + (int64_t)jj * 2 * kSigQ;
+#pragma unroll
+        for (int k = 0; k < kSigQ; k++) { dst[k] = a.q[k].s; dst[kSigQ + k] = a.q[k].c; }
+      }
+      __syncthreads();
+      if (rounds == 1) {
+        decide_unit(v, g0, ng, sm, clean_max);
+      } else if (warp == 0) {
+        const int64_t jend = min(nsig, (r + 1) * spb);
+        for (int64_t jx = r * spb + lane; jx < jend; jx += 32) {
+          const real* sj = sm + (jx - r * spb) * 2 * kSigQ;
+          sig_test(v, c, (int)jx, sj, sj + kSigQ);
+        }
+      }
+      __syncthreads();
+    }
+    if (rounds > 1 && warp == 0) {
+      const int64_t gsize = min((int64_t)v.group, v.batch - g0 * v.group);
+      for (int off = 16; off > 0; off >>= 1) c.merge(c.shfl(off));
+      if (lane == 0) decide_sig_group(v, g0, gsize, c, clean_max);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) clean_max = max(clean_max, __shfl_xor_sync(0xffffffffu, clean_max, off));
+  if (lane == 0) smax[warp] = clean_max;
+  __syncthreads();
+  if (t == 0) {
+    unsigned long long m = 0;
+    for (int w = 0; w < kVT / 32; w++) m = max(m, smax[w]);
+    if (m) atomicMax(&v.counters->max_clean_ratio_bits, m);
+  }
+}
+
 int sig_split_of(int64_t recs, int64_t batch, int sms) {
   if (recs <= kSigSerialMax) return 0;               // one lane per signal
   // warps of at most 1024 records, and at least 16 warps per SM in all
@@ -551,6 +643,16 @@ int sig_split_of(int64_t recs, int64_t batch, int sms) {
   const int64_t cover = (16 * (int64_t)sms + batch - 1) / batch;
   want = std::max(want, std::min(cover, (recs + 127) / 128));
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, 1 << 16));
+}
+
+int sig_block_geom(int64_t rin, int64_t rout, int64_t group, int64_t ngroups, int sms, int* gpb) {
+  const int64_t rmax = std::max<int64_t>(1, std::max(rin, rout));
+  int L = 1;
+  while (L < 32 && L < rmax) L <<= 1;
+  const int64_t spb = kVT / L;
+  *gpb = group <= spb ? (int)(spb / group) : 1;
+  const int64_t units = (ngroups + *gpb - 1) / *gpb;
+  return units >= sms ? L : 0;
 }
 
 int verify_split(int64_t recs, int64_t ngroups, int sms) {
@@ -564,6 +666,13 @@ int verify_split(int64_t recs, int64_t ngroups, int sms) {
 cudaError_t launch_verify(const VerifyParams& vin, cudaStream_t s) {
   const int threads = 256;
   VerifyParams v = vin;
+  if (v.sigrec && v.sig_blk_lanes > 0) {
+    const int64_t units = (v.ngroups + v.sig_gpb - 1) / v.sig_gpb;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)v.max_blocks));
+    if (v.dtype == 0) verify_sig_blocks<float><<<(unsigned)blocks, kVT, 0, s>>>(v, v.sig_blk_lanes);
+    else verify_sig_blocks<double><<<(unsigned)blocks, kVT, 0, s>>>(v, v.sig_blk_lanes);
+    return cudaGetLastError();
+  }
   if (v.sigrec) {
     int lanes = 1;
     while (lanes < v.group && lanes < 32) lanes <<= 1;

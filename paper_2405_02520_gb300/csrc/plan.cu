@@ -156,6 +156,7 @@ struct tfft_plan_s {
   int64_t sslots_in = 1, sslots_out = 1;
   int sig_split = 0;
   double* sig_acc = nullptr;
+  int sig_blk_lanes = 0, sig_gpb = 1;   // block verification in place of the split mode
   // second check across the last pass (multi-pass plans with per-signal records)
   int chk2 = 0;
   void* ltab = nullptr;             // u2[L][n], N entries
@@ -998,6 +999,12 @@ int plan_workspace(tfft_plan_s* p) {
       p->workspace_bytes += (int64_t)(rc2 * p->batch * p->sslots_out);
     }
     p->sig_split = sig_split_of(p->sslots_in + p->sslots_out * (p->chk2 ? 3 : 1), p->batch, p->sms);
+    // many signals of a few dozen to a few hundred records: one block per
+    // unit of groups, decided in shared memory (no per-signal atomics)
+    if (p->sig_split > 0) {
+      p->sig_blk_lanes = sig_block_geom(p->sslots_in, p->sslots_out, p->vG, p->vgroups, p->sms, &p->sig_gpb);
+      if (p->sig_blk_lanes > 0) p->sig_split = 0;
+    }
     if (p->sig_split > 0) {
       const size_t acc = (size_t)p->batch * kSigAcc * sizeof(double);
       TFFT_CUDA(cudaMalloc(&p->sig_acc, acc));
@@ -1340,6 +1347,7 @@ int exec_range(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
       v.sig_out = static_cast<const unsigned char*>(p->sig_out) + (size_t)b0s * p->sslots_out * rout;
       v.sig_slots_in = p->sslots_in; v.sig_slots_out = p->sslots_out;
       v.sig_split = p->sig_split;
+      v.sig_blk_lanes = p->sig_blk_lanes; v.sig_gpb = p->sig_gpb;
       v.sig_acc = p->sig_acc ? p->sig_acc + b0s * kSigAcc : nullptr;
       v.part_cnt = p->part_cnt ? p->part_cnt + vg0 : nullptr;
       // a threshold never below that of signals whose every value is the

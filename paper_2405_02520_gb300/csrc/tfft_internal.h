@@ -325,6 +325,9 @@ struct VerifyParams {
   // (0: one lane per signal adds all its records)
   int sig_split;
   double* sig_acc;              // batch x kSigAcc
+  // (sig_blk_lanes > 0, in place of the split mode) one block per unit of
+  // sig_gpb groups, sig_blk_lanes lanes adding one signal's records
+  int sig_blk_lanes, sig_gpb;
   double tau_floor;             // smallest threshold (the element type's tiny values)
   // second check across the last pass: records sig_chk[b sig_slots_out + k],
   // threshold kappa u (log2 n_last + 4) sqrt(N) sqrt(E_b)
@@ -337,6 +340,10 @@ constexpr int kSigAcc = 10;
 // records a signal may hold for the one-thread-per-signal verification
 constexpr int64_t kSigSerialMax = 48;
 int sig_split_of(int64_t recs, int64_t batch, int sms);
+// lanes per signal of the block verification for signals of rin input-side
+// and rout output-side records in `ngroups` groups of `group` (and *gpb, its
+// groups per block), or 0 when it would not give every SM a block
+int sig_block_geom(int64_t rin, int64_t rout, int64_t group, int64_t ngroups, int sms, int* gpb);
 // blocks per group for a group of `recs` records when there are `ngroups`
 // groups on `sms` multiprocessors (1 = no split)
 int verify_split(int64_t recs, int64_t ngroups, int sms);

@@ -44,3 +44,39 @@ def test_split_verify_clean_fault_clean(log2n, batch):
     assert rel_err_rows(yt.cpu().numpy(), ref).max() <= tol(n, t.TFFT_C64)
     assert t.tfft_report(plan) == (1, 1)
     t.tfft_destroy(plan)
+
+
+@pytest.mark.parametrize("log2n,batch,group,mode", [
+    (8, 512, 64, t.TFFT_ABFT_TWO_SIDED),     # four groups in a verification block
+    (8, 300, 7, t.TFFT_ABFT_TWO_SIDED),      # a group size that is no power of two, a short last group
+    (10, 96, 0, t.TFFT_ABFT_ONE_SIDED),      # every signal its own group
+    (16, 70, 64, t.TFFT_ABFT_TWO_SIDED),     # one group per block, its signals in rounds
+    (13, 100, 16, t.TFFT_ABFT_TWO_SIDED),    # sixteen lanes per signal
+])
+def test_verification_layouts_clean_and_one_fault(log2n, batch, group, mode):
+    """Whatever the block layout of the verification (groups per block,
+    lanes per signal, rounds), clean execs are clean and a value added to
+    one input element is detected, named and corrected."""
+    n = 1 << log2n
+    x = uniform_batch(n, batch, seed=3300 + log2n + group)
+    ref = oracle_fft(x)
+    plan = t.tfft_plan_ex(n, batch, t.TFFT_C64, mode, group=group)
+    try:
+        y, _ = run_gpu(x, t.TFFT_C64, plan=plan)
+        assert rel_err_rows(y, ref).max() <= tol(n, t.TFFT_C64)
+        assert t.tfft_report(plan) == (0, 0)
+        info = t.tfft_plan_info(plan)
+        sig = batch - 2
+        fault = dict(mode=t.TFFT_FAULT_ADD, pass_=0, stage=-1, signal=sig,
+                     line=min(3, info["lines_per_signal"][0] - 1), index=5, factor=100.0)
+        y, _ = run_gpu(x, t.TFFT_C64, plan=plan, fault=fault)
+        assert rel_err_rows(y, ref).max() <= tol(n, t.TFFT_C64)
+        assert t.tfft_report(plan) == (1, 1)
+        ev, _ = t.tfft_fault_log(plan)
+        assert ev[-1]["signal"] == sig
+        t.tfft_set_fault(plan, mode=t.TFFT_FAULT_NONE)
+        y, _ = run_gpu(x, t.TFFT_C64, plan=plan)
+        assert rel_err_rows(y, ref).max() <= tol(n, t.TFFT_C64)
+        assert t.tfft_report(plan) == (1, 1)
+    finally:
+        t.tfft_destroy(plan)
