@@ -556,7 +556,10 @@ RAGGED_COUNT, RAGGED_LOG2 = 20000, (6, 16)
 def ragged_measure(t, torch, stream, args, peak):
     """A ragged batch: 20,000 signals, log2 length uniform over {6..16},
     U[-1,1) re/im, seed 5, packed back to back; autotuned plan, graph-replayed
-    execs, ABFT on and off; beside it the staged form (gather, transform,
+    execs, ABFT on and off, in the bucket-stream form (one plan per bucket on
+    its own stream) and the persistent form (pass families: one persistent
+    launch per pass role and sub-transform length pulling size-sorted items
+    from an atomic counter); beside them the staged form (gather, transform,
     scatter) and one plan per length run one after another on the same
     signals grouped by length beforehand (the grouping not timed).  Bytes
     counted as algorithmic: 16 B per element per pass of each bucket's plan."""
@@ -569,9 +572,12 @@ def ragged_measure(t, torch, stream, args, peak):
     xr.imag.uniform_(-1, 1, generator=g)
     yr = torch.empty_like(xr)
     out = {"signals": RAGGED_COUNT, "log2_lengths": list(RAGGED_LOG2), "elements": total, "seed": 5}
-    for mode, key, staged in ((t.TFFT_ABFT_TWO_SIDED, "ms", False), (t.TFFT_ABFT_OFF, "ms_abft_off", False),
-                              (t.TFFT_ABFT_TWO_SIDED, "ms_staged", True)):
-        r = t.Ragged(lengths.tolist(), abft_mode=mode, autotune=True, staged=staged)
+    for mode, key, staged, persistent in ((t.TFFT_ABFT_TWO_SIDED, "ms", False, False),
+                                          (t.TFFT_ABFT_OFF, "ms_abft_off", False, False),
+                                          (t.TFFT_ABFT_TWO_SIDED, "ms_persistent", False, True),
+                                          (t.TFFT_ABFT_OFF, "ms_persistent_abft_off", False, True),
+                                          (t.TFFT_ABFT_TWO_SIDED, "ms_staged", True, False)):
+        r = t.Ragged(lengths.tolist(), abft_mode=mode, autotune=True, staged=staged, persistent=persistent)
         for _ in range(max(3, args.warmup)):
             r.exec(xr, yr, stream)
         torch.cuda.synchronize()
@@ -583,12 +589,18 @@ def ragged_measure(t, torch, stream, args, peak):
         e1.record(stream)
         torch.cuda.synchronize()
         out[key] = round(e0.elapsed_time(e1) / k, 4)
-        if key == "ms":
+        if key in ("ms", "ms_persistent"):
             info = dict(r.info())
             st = r.report()
-            out["detected_clean"] = st["detected"]
-            out["buckets"] = {str(n): p for n, p in sorted(info.items())}
-            out["in_place_buckets"] = sum(r.layout().values())
+            pre = "" if key == "ms" else "persistent_"
+            out[pre + "detected_clean"] = st["detected"]
+            if key == "ms":
+                out["buckets"] = {str(n): p for n, p in sorted(info.items())}
+                out["in_place_buckets"] = sum(r.layout().values())
+            else:
+                fams, pb = r.families()
+                out["persistent_families"] = fams
+                out["persistent_buckets"] = pb
             # one fault per 1000 signals, in distinct checksum groups, one exec
             sites = ragged_fault_sites(lengths, 1, seed=5)
             for k, i in enumerate(sites):
@@ -597,8 +609,9 @@ def ragged_measure(t, torch, stream, args, peak):
                             index=(7 * k + 1) % 16, factor=3.0)
             r.exec(xr, yr, stream)
             st2 = r.report()
-            out["faults"] = {"injected": len(sites), "detected": st2["detected"] - st["detected"],
-                             "corrected": st2["corrected"] + st2["recomputed"] - st["corrected"] - st["recomputed"]}
+            out[pre + "faults"] = {"injected": len(sites), "detected": st2["detected"] - st["detected"],
+                                   "corrected": st2["corrected"] + st2["recomputed"] - st["corrected"]
+                                   - st["recomputed"]}
         r.destroy()
     # one plan per length over the same signals grouped by length
     off = np.concatenate([[0], np.cumsum(lengths)])
@@ -631,6 +644,7 @@ def ragged_measure(t, torch, stream, args, peak):
     out["gflops"] = round(fl / (out["ms"] / 1e3) / 1e9, 1)
     out["hbm_frac"] = round(alg / (out["ms"] / 1e3) / 1e9 / peak, 4)
     out["abft_overhead_pct"] = round((out["ms"] - out["ms_abft_off"]) / out["ms_abft_off"] * 100, 2)
+    out["persistent_speedup_vs_bucket_streams"] = round(out["ms"] / out["ms_persistent"], 3)
     return out
 
 

@@ -423,7 +423,17 @@ int tfft_exec_noalloc(int64_t n, int64_t batch, const void *in, void *out, tfft_
  *   TFFT_RAGGED_AUTOTUNE  time every pass count (one, two or three launches)
  *                         a bucket's length admits and keep the fastest;
  *   TFFT_RAGGED_STAGED    stage every bucket (the copy-based form, kept for
- *                         comparison).
+ *                         comparison);
+ *   TFFT_RAGGED_PERSISTENT  run the passes of the buckets whose every pass is
+ *                         on the 256-thread complex64 tile kernels as pass
+ *                         families: the passes of one role and sub-transform
+ *                         length, of all such buckets, in one persistent
+ *                         launch whose blocks take (bucket, chunk range)
+ *                         items, sorted by work, from an atomic counter; each
+ *                         family waits for the families of its buckets'
+ *                         previous pass, and each bucket then verifies and
+ *                         corrects on its own stream.  The other buckets run
+ *                         their plans alongside.
  * The caller's `lengths` array is not kept.
  *
  * tfft_ragged_exec: asynchronous on `stream`; gathers the staged buckets,
@@ -441,9 +451,11 @@ int tfft_exec_noalloc(int64_t n, int64_t batch, const void *in, void *out, tfft_
  * tfft_ragged_info: number of buckets, and up to `capacity` of their
  * lengths, pass counts and addressing (direct: 1 in place, 0 staged),
  * longest first; any of the arrays may be NULL.
+ * tfft_ragged_families: the pass families of the persistent form and the
+ * buckets that run in them (0 and 0 without TFFT_RAGGED_PERSISTENT).
  */
 typedef struct tfft_ragged_s *tfft_ragged_t;
-enum { TFFT_RAGGED_AUTOTUNE = 1, TFFT_RAGGED_STAGED = 2 };
+enum { TFFT_RAGGED_AUTOTUNE = 1, TFFT_RAGGED_STAGED = 2, TFFT_RAGGED_PERSISTENT = 4 };
 int tfft_ragged_plan(tfft_ragged_t *out, const int64_t *lengths, int64_t count, int dtype, int abft_mode,
                      int flags);
 int tfft_ragged_exec(tfft_ragged_t r, const void *in, void *out, tfft_stream_t stream);
@@ -451,6 +463,7 @@ int tfft_ragged_report(tfft_ragged_t r, tfft_stats *stats);
 int tfft_ragged_set_fault(tfft_ragged_t r, int64_t signal, const tfft_fault *fault);
 int tfft_ragged_info(tfft_ragged_t r, int64_t *buckets, int64_t *lengths, int *passes, int *direct,
                      int64_t capacity);
+int tfft_ragged_families(tfft_ragged_t r, int64_t *families, int64_t *persistent_buckets);
 int tfft_ragged_destroy(tfft_ragged_t r);
 
 /*

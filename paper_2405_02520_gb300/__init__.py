@@ -23,7 +23,7 @@ TFFT_ABFT_OFF, TFFT_ABFT_ONE_SIDED, TFFT_ABFT_TWO_SIDED = 0, 1, 2
 TFFT_R_SIGNED_WANG, TFFT_R_WANG = 0, 1
 TFFT_FORWARD, TFFT_INVERSE = 0, 1
 TFFT_PREC_FP32, TFFT_PREC_TF32X3, TFFT_PREC_TF32, TFFT_PREC_BF16X3 = 0, 1, 2, 3
-TFFT_RAGGED_AUTOTUNE, TFFT_RAGGED_STAGED = 1, 2
+TFFT_RAGGED_AUTOTUNE, TFFT_RAGGED_STAGED, TFFT_RAGGED_PERSISTENT = 1, 2, 4
 TFFT_FAULT_NONE, TFFT_FAULT_BITFLIP, TFFT_FAULT_SCALE, TFFT_FAULT_ADD, TFFT_FAULT_ADD_PAIR = 0, 1, 2, 3, 4
 TIMING_KINDS = ("first_pass", "middle_pass", "last_pass", "single_pass", "verify", "correction")
 
@@ -120,6 +120,7 @@ def lib() -> ctypes.CDLL:
                 "tfft_ragged_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I),
                                      ctypes.POINTER(I), I64],
                 "tfft_ragged_destroy": [P],
+                "tfft_ragged_families": [P, ctypes.POINTER(I64), ctypes.POINTER(I64)],
                 "tfft_tc_selftest": [P, P, P, I],
                 "tfft_measure_fma_peak": [I, I, ctypes.POINTER(ctypes.c_double)],
                 "tfft_autotune": [ctypes.POINTER(PlanOpts), P, P, P, I, ctypes.POINTER(TuneResult)],
@@ -256,10 +257,11 @@ class Ragged:
     to back (see include/tfft.h, tfft_ragged_*)."""
 
     def __init__(self, lengths, dtype: int = TFFT_C64, abft_mode: int = TFFT_ABFT_TWO_SIDED,
-                 autotune: bool = True, staged: bool = False):
+                 autotune: bool = True, staged: bool = False, persistent: bool = False):
         arr = (ctypes.c_int64 * len(lengths))(*[int(v) for v in lengths])
         h = ctypes.c_void_p()
-        flags = (TFFT_RAGGED_AUTOTUNE if autotune else 0) | (TFFT_RAGGED_STAGED if staged else 0)
+        flags = ((TFFT_RAGGED_AUTOTUNE if autotune else 0) | (TFFT_RAGGED_STAGED if staged else 0)
+                 | (TFFT_RAGGED_PERSISTENT if persistent else 0))
         _check(lib().tfft_ragged_plan(ctypes.byref(h), arr, len(lengths), dtype, abft_mode, flags),
                "tfft_ragged_plan")
         self.handle = h.value
@@ -294,6 +296,12 @@ class Ragged:
     def layout(self) -> dict:
         """{length: True if the bucket is addressed in place, False if staged}."""
         return {n: bool(d) for n, _, d in self._info()}
+
+    def families(self) -> tuple[int, int]:
+        """(pass families, buckets run in them) of the persistent form."""
+        f, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().tfft_ragged_families(self.handle, ctypes.byref(f), ctypes.byref(b)), "tfft_ragged_families")
+        return f.value, b.value
 
     def destroy(self) -> None:
         if self.handle:

@@ -262,6 +262,7 @@ __device__ __forceinline__ void sig_flush_chk(const Partials<real>& a, const Pas
 struct V3Cursor {
   long long tb, gb, sb, se;
   long long chunk;
+  long long cstep, cend;        // the block's chunk schedule: chunk, chunk + cstep, ... below cend
   unsigned lb, part, g;
   __device__ __forceinline__ bool decode(const PassParams& p) {
     const unsigned c = (unsigned)chunk;
@@ -286,16 +287,21 @@ struct V3Cursor {
     return sb < se;
   }
   __device__ __forceinline__ void settle(const PassParams& p) {
-    while (chunk < p.nchunks) {
+    while (chunk < cend) {
       if (decode(p)) { tb = sb; return; }
-      chunk += gridDim.x;
+      chunk += cstep;
     }
   }
-  __device__ __forceinline__ void start(const PassParams& p) { chunk = blockIdx.x; settle(p); }
-  __device__ __forceinline__ bool valid(const PassParams& p) const { return chunk < p.nchunks; }
+  __device__ __forceinline__ void start(const PassParams& p, long long first, long long step, long long end) {
+    chunk = first;
+    cstep = step;
+    cend = end;
+    settle(p);
+  }
+  __device__ __forceinline__ bool valid(const PassParams&) const { return chunk < cend; }
   __device__ __forceinline__ void advance(const PassParams& p) {
     tb += p.lines_are_signals ? p.C : 1;
-    if (tb >= se) { chunk += gridDim.x; settle(p); }
+    if (tb >= se) { chunk += cstep; settle(p); }
   }
   __device__ __forceinline__ long long hi(const PassParams& p) const {
     return p.lines_are_signals ? 0 : ((long long)lb << p.log2C) >> p.log2LO;
@@ -401,8 +407,32 @@ constexpr int v3_min_blocks_tc() { return TC == 0 ? v3_min_blocks<real>() : (v3_
 // matrix -- one product per warpgroup and stage, the accumulator in tensor
 // memory; TC = 1 multiplies TF32-rounded operands, TC = 3 the three-term
 // split (x_hi w_hi + x_hi w_lo + x_lo w_hi) that keeps about 21 bits.
+//
+// The block's own state (load cursors, tile counters, the timeout flag, the
+// tensor-core barriers), in static shared memory of the calling kernel: one
+// copy per block whatever the bodies it runs.
+template <int NW>
+struct V3Smem {
+  V3Cursor ldc[NW];        // per warp: the next tile to load
+  unsigned arrivals[8];    // per buffer: warps done with the tile, cumulative
+  unsigned copied[8];      // per buffer: warps done copying the tile out (last pass), cumulative
+  unsigned issued[8];      // per buffer: tile loads issued into it, cumulative
+  int s_abort;
+  uint64_t tcbar[2];
+  uint32_t tc_tmem;
+};
+
+// The body runs the chunks cfirst, cfirst + cstep, ... below cend of the pass
+// (the kernel: the grid-stride share of its block); zero_entry marks the one
+// block that resets the plan's per-exec lists.  It may run again in the same
+// block for another pass (the persistent ragged kernels): it starts and ends
+// at a block barrier, fences generic writes to its buffers before the first
+// tile copies into them, and invalidates its tile barriers before it returns.
+// Returns true when a bounded wait gave up (the block must not run another
+// body then: a copy may still be in flight into its buffers).
 template <typename real, int NSUB, int E, int ROLE, int TC = 0, int NT = 256>
-__global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() : 1)) fft_v3_kernel(const __grid_constant__ PassParams p) {
+__device__ __forceinline__ bool v3_body(const PassParams& p, long long cfirst, long long cstep, long long cend,
+                                        bool zero_entry, V3Smem<NT / 32>& vs) {
   static_assert(TC == 0 || (sizeof(real) == 4 && E == 16 && NT == 256), "tensor-core DFT: complex64, radix 16");
   static_assert(NT == 256 || NT == 512, "eight or sixteen warps");
   using G = V3<real, NSUB, E, ROLE, NT>;
@@ -415,11 +445,11 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
   using cT = typename G::cT;
   static_assert(E % G::PG == 0, "a thread's stage-0 values start on a pad group");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ V3Cursor ldc[G::NW];
-  __shared__ unsigned arrivals[8];   // per buffer: warps done with the tile, cumulative
-  __shared__ unsigned copied[8];     // per buffer: warps done copying the tile out (last pass), cumulative
-  __shared__ unsigned issued[8];     // per buffer: tile loads issued into it, cumulative
-  __shared__ int s_abort;
+  V3Cursor* ldc = vs.ldc;
+  unsigned* arrivals = vs.arrivals;
+  unsigned* copied = vs.copied;
+  unsigned* issued = vs.issued;
+  int& s_abort = vs.s_abort;
 
   const int t = threadIdx.x;
   const int warp = t >> 5, lane = t & 31;
@@ -438,7 +468,7 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
     }
     fence_mbar_init();
     s_abort = 0;
-    if (blockIdx.x == 0) {
+    if (zero_entry) {
       if (p.zero_on_entry[0]) *p.zero_on_entry[0] = 0;
       if (p.zero_on_entry[1]) *p.zero_on_entry[1] = 0;
       if (p.zero_on_entry[2]) *p.zero_on_entry[2] = 0;
@@ -447,7 +477,8 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
   __syncthreads();
   if (t == 0) {
     V3Cursor ld;
-    ld.start(p);
+    ld.start(p, cfirst, cstep, cend);
+    fence_proxy_async();                // generic writes to the buffers before the tile copies land
     for (int s = 0; s < nbuf && ld.valid(p); s++) {
       issue_load(p, ld, reinterpret_cast<cT*>(base + (size_t)s * p.buf_bytes), &full[s]);
       issued[s]++;
@@ -463,8 +494,8 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
     twt = tsm;
   }
   // tensor-core operands and accumulator (TC != 0)
-  __shared__ uint64_t tcbar[2];
-  __shared__ uint32_t tc_tmem;
+  uint64_t* tcbar = vs.tcbar;
+  uint32_t& tc_tmem = vs.tc_tmem;
   unsigned char* tc_a = nullptr;      // per warpgroup: A high [, A low], 16 KB in all
   unsigned char* tc_b = nullptr;      // DFT-16 matrix, transposed: high [, low]
   if constexpr (TC != 0) {
@@ -726,9 +757,11 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
 
   int s = 0;             // ring buffer of the current tile
   unsigned wrap = 0;     // completed passes over the ring
-  for (long long chunk = blockIdx.x; chunk < p.nchunks; chunk += gridDim.x) {
+  for (long long chunk = cfirst; chunk < cend; chunk += cstep) {
     V3Cursor cur;
     cur.chunk = chunk;
+    cur.cstep = cstep;
+    cur.cend = cend;
     const bool nonempty = cur.decode(p);
     // one checksum record per warp and chunk
     const long long slot = (long long)(cur.part * p.line_blocks + cur.lb) * G::NW + warp;
@@ -1065,6 +1098,17 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tc_tmem, 64);
   }
+  const bool gave_up = *abort_flag != 0;
+  if (t == 0 && !gave_up)
+    for (int b = 0; b < nbuf; b++) mbar_inval(&full[b]);
+  __syncthreads();
+  return gave_up;
+}
+
+template <typename real, int NSUB, int E, int ROLE, int TC = 0, int NT = 256>
+__global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() : 1)) fft_v3_kernel(const __grid_constant__ PassParams p) {
+  __shared__ V3Smem<NT / 32> vs;
+  v3_body<real, NSUB, E, ROLE, TC, NT>(p, blockIdx.x, gridDim.x, p.nchunks, blockIdx.x == 0, vs);
 }
 
 }  // namespace tfft

@@ -1072,10 +1072,11 @@ PassParams base_params(const tfft_plan_s* p, int i) {
   return a;
 }
 
-int launch_pass(tfft_plan_s* p, PassParams& a, int i, int kind, cudaStream_t s) {
+// The tile-copy parameters of pass i (buffers, bounded waits, tensor maps of
+// a.in / a.out, encoded once per pointer) for a launch on the TMA kernels.
+int prepare_tma(tfft_plan_s* p, PassParams& a, int i) {
   const PassPlan& q = p->pp[i];
-  const bool tma = q.tma && a.list == nullptr;
-  if (tma) {
+  {
     a.nbuf = q.nbuf; a.buf_bytes = q.buf_bytes; a.err_flag = p->err_flag; a.wait_limit = p->wait_limit;
     a.map_in = q.map_in; a.map_out = q.map_out;
     const void* ptrs[2] = {a.in, a.out};
@@ -1089,6 +1090,16 @@ int launch_pass(tfft_plan_s* p, PassParams& a, int i, int kind, cudaStream_t s) 
       }
       (d == 0 ? a.tmap_in : a.tmap_out) = p->enc_map[i][d];
     }
+  }
+  return 0;
+}
+
+int launch_pass(tfft_plan_s* p, PassParams& a, int i, int kind, cudaStream_t s) {
+  const PassPlan& q = p->pp[i];
+  const bool tma = q.tma && a.list == nullptr;
+  if (tma) {
+    const int rc = prepare_tma(p, a, i);
+    if (rc) return rc;
   }
   const int64_t maxgrid = (int64_t)p->sms * (tma ? q.tbps : q.bps);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.nchunks, maxgrid));
@@ -1141,6 +1152,9 @@ int kind_of(const tfft_plan_s* p, int i) {
   return i == p->passes - 1 ? 2 : 1;
 }
 
+PassParams main_params(tfft_plan_s* p, int i, const void* in, void* out, int64_t batch, bool user_io,
+                       int64_t vgroup0);
+
 // Run the passes from `in` to `out` (through tmp when there are several).
 int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool main_exec,
                const long long* list, int list_identity, int list_cap, int64_t list_block,
@@ -1148,58 +1162,16 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
   // an exec over the signals [b0, b0 + batch) of the plan (b0 = vgroup0 vG,
   // a multiple of G): `in` and `out` already point at signal b0, the records
   // of its verification groups start at group vgroup0
-  const int64_t ng = (batch + p->G - 1) / p->G;
   for (int i = 0; i < p->passes; i++) {
-    PassParams a = base_params(p, i);
-    a.batch = batch;
-    a.in = (i == 0) ? in : p->tmp;
-    a.out = (i == p->passes - 1) ? out : p->tmp;
-    if (user_io) {
-      a.soff_in = i == 0 ? p->soff : nullptr;
-      a.soff_out = i == p->passes - 1 ? p->soff : nullptr;
-    }
-    if (main_exec) {
-      a.ngroups = ng;
-      a.nchunks = ng * p->pp[i].parts * p->pp[i].line_blocks;
-    }
-    if (main_exec && p->pp[i].v3) {
-      const PassPlan& q = p->pp[i];
-      a.C = q.vC; a.nthreads = q.vnt; a.line_blocks = q.vLB;
-      a.nchunks = ng * q.parts * q.vLB;
-      a.log2C = ilog2(q.vC); a.log2LO = ilog2(q.LO); a.log2LB = ilog2(q.vLB);
-    }
-    if (main_exec) {
-      a.abft_in = p->abft && i == 0;
-      a.abft_out = p->abft && i == p->passes - 1;
-      a.slots = (i == 0) ? p->slots_in : p->slots_out;
-      if (p->passes == 1) a.slots = p->slots_in;
-      if (p->abft && p->sigrec) {
-        // records of signal b0 = vgroup0 vG onwards
-        const int64_t b0 = vgroup0 * p->vG;
-        const size_t rin = p->dtype == TFFT_C64 ? sizeof(SigIn<float>) : sizeof(SigIn<double>);
-        const size_t rout = p->dtype == TFFT_C64 ? sizeof(SigOut<float>) : sizeof(SigOut<double>);
-        a.sig_in = static_cast<unsigned char*>(p->sig_in) + (size_t)b0 * p->sslots_in * rin;
-        a.sig_out = static_cast<unsigned char*>(p->sig_out) + (size_t)b0 * p->sslots_out * rout;
-        a.sig_slots = (i == 0) ? p->sslots_in : p->sslots_out;
-        if (p->chk2 && i == p->passes - 1) {
-          const size_t rc2 = p->dtype == TFFT_C64 ? sizeof(SigChk<float>) : sizeof(SigChk<double>);
-          a.chk2 = 1;
-          a.sig_chk = static_cast<unsigned char*>(p->sig_chk) + (size_t)b0 * p->sslots_out * rc2;
-          a.ltab = p->ltab;
-        }
-      } else if (p->abft) {
-        a.rec_in = p->rec_in + vgroup0 * p->slots_in;
-        a.rec_out = p->rec_out + vgroup0 * p->slots_out;
+    PassParams a = main_exec ? main_params(p, i, in, out, batch, user_io, vgroup0) : base_params(p, i);
+    if (!main_exec) {
+      a.batch = batch;
+      a.in = (i == 0) ? in : p->tmp;
+      a.out = (i == p->passes - 1) ? out : p->tmp;
+      if (user_io) {
+        a.soff_in = i == 0 ? p->soff : nullptr;
+        a.soff_out = i == p->passes - 1 ? p->soff : nullptr;
       }
-      a.fault = p->pending;
-      for (int k = 0; k < 3; k++) a.fault_more[k] = p->pending_more[k];
-      a.nfault = p->npending;
-      if (i == 0 && p->abft) {
-        a.zero_on_entry[0] = p->lists.fix;
-        a.zero_on_entry[1] = p->lists.rec;
-        a.zero_on_entry[2] = p->cond_flag;
-      }
-    } else {
       a.list = list; a.list_identity = list_identity; a.list_cap = list_cap;
       a.list_block = list_block;
       a.ngroups = list_cap;
@@ -1210,6 +1182,61 @@ int run_passes(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, bool m
     if (rc) return rc;
   }
   return 0;
+}
+
+// The parameters of pass i of an exec over signals [b0, b0 + batch) (b0 =
+// vgroup0 vG; in and out already point at signal b0), before the tile-copy
+// parameters.
+PassParams main_params(tfft_plan_s* p, int i, const void* in, void* out, int64_t batch, bool user_io,
+                       int64_t vgroup0) {
+  const int64_t ng = (batch + p->G - 1) / p->G;
+  PassParams a = base_params(p, i);
+  a.batch = batch;
+  a.in = (i == 0) ? in : p->tmp;
+  a.out = (i == p->passes - 1) ? out : p->tmp;
+  if (user_io) {
+    a.soff_in = i == 0 ? p->soff : nullptr;
+    a.soff_out = i == p->passes - 1 ? p->soff : nullptr;
+  }
+  a.ngroups = ng;
+  a.nchunks = ng * p->pp[i].parts * p->pp[i].line_blocks;
+  if (p->pp[i].v3) {
+    const PassPlan& q = p->pp[i];
+    a.C = q.vC; a.nthreads = q.vnt; a.line_blocks = q.vLB;
+    a.nchunks = ng * q.parts * q.vLB;
+    a.log2C = ilog2(q.vC); a.log2LO = ilog2(q.LO); a.log2LB = ilog2(q.vLB);
+  }
+  a.abft_in = p->abft && i == 0;
+  a.abft_out = p->abft && i == p->passes - 1;
+  a.slots = (i == 0) ? p->slots_in : p->slots_out;
+  if (p->passes == 1) a.slots = p->slots_in;
+  if (p->abft && p->sigrec) {
+    // records of signal b0 = vgroup0 vG onwards
+    const int64_t b0 = vgroup0 * p->vG;
+    const size_t rin = p->dtype == TFFT_C64 ? sizeof(SigIn<float>) : sizeof(SigIn<double>);
+    const size_t rout = p->dtype == TFFT_C64 ? sizeof(SigOut<float>) : sizeof(SigOut<double>);
+    a.sig_in = static_cast<unsigned char*>(p->sig_in) + (size_t)b0 * p->sslots_in * rin;
+    a.sig_out = static_cast<unsigned char*>(p->sig_out) + (size_t)b0 * p->sslots_out * rout;
+    a.sig_slots = (i == 0) ? p->sslots_in : p->sslots_out;
+    if (p->chk2 && i == p->passes - 1) {
+      const size_t rc2 = p->dtype == TFFT_C64 ? sizeof(SigChk<float>) : sizeof(SigChk<double>);
+      a.chk2 = 1;
+      a.sig_chk = static_cast<unsigned char*>(p->sig_chk) + (size_t)b0 * p->sslots_out * rc2;
+      a.ltab = p->ltab;
+    }
+  } else if (p->abft) {
+    a.rec_in = p->rec_in + vgroup0 * p->slots_in;
+    a.rec_out = p->rec_out + vgroup0 * p->slots_out;
+  }
+  a.fault = p->pending;
+  for (int k = 0; k < 3; k++) a.fault_more[k] = p->pending_more[k];
+  a.nfault = p->npending;
+  if (i == 0 && p->abft) {
+    a.zero_on_entry[0] = p->lists.fix;
+    a.zero_on_entry[1] = p->lists.rec;
+    a.zero_on_entry[2] = p->cond_flag;
+  }
+  return a;
 }
 
 // The correction sequence (Section III-B) on `s`: gather the queued groups'
@@ -1306,6 +1333,8 @@ int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, c
   return 0;
 }
 
+int exec_checks(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_t b0, int64_t nb);
+
 // The exec over signals [b0, b0 + nb) (b0 a multiple of G, nb > 0): the
 // passes, the verification of their groups and the correction path, all on
 // `s`, reading in + b0 n and writing out + b0 n.
@@ -1316,6 +1345,14 @@ int exec_range(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
   const int64_t vg0 = b0 / p->vG;
   int rc = run_passes(p, in, out, s, true, nullptr, 0, 0, 0, nb, -1, true, vg0);
   if (rc) return rc;
+  return exec_checks(p, in, out, s, b0, nb);
+}
+
+// The verification and correction of an exec over signals [b0, b0 + nb)
+// whose passes have been enqueued on `s` (in and out point at signal b0).
+int exec_checks(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_t b0, int64_t nb) {
+  int rc;
+  const int64_t vg0 = b0 / p->vG;
   if (p->abft) {
     VerifyParams v{};
     v.n = p->n; v.batch = nb; v.group = p->vG; v.ngroups = (nb + p->vG - 1) / p->vG;
@@ -1409,6 +1446,42 @@ bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 }  // namespace
 
 namespace tfft {
+
+int plan_ragged_pass(tfft_plan_t p, int i, RaggedPass* rp) {
+  if (!p || !rp || i < 0 || i >= p->passes) return TFFT_ERR_INVALID_ARG;
+  const PassPlan& q = p->pp[i];
+  *rp = RaggedPass{};
+  rp->role = q.role;
+  rp->nsub = q.nsub;
+  rp->ok = p->dtype == TFFT_C64 && q.tma && q.v3 && q.vnt == 256 && q.vtc == 0 && v3_ragged_has(q.role, q.nsub);
+  if (!rp->ok) return TFFT_SUCCESS;
+  rp->smem = q.tsmem;
+  const int64_t ng = (p->batch + p->G - 1) / p->G;
+  rp->nchunks = ng * q.parts * q.vLB;
+  const int64_t per_part = (p->G + q.parts - 1) / q.parts;
+  rp->tiles_per_chunk = (int)std::max<int64_t>(1, q.role == 0 ? (per_part + q.vC - 1) / q.vC : per_part);
+  return TFFT_SUCCESS;
+}
+
+int plan_pass_params(tfft_plan_t p, const void* in, void* out, int i, PassParams* a) {
+  if (!p || !a || i < 0 || i >= p->passes) return TFFT_ERR_INVALID_ARG;
+  *a = main_params(p, i, in, out, p->batch, true, 0);
+  return prepare_tma(p, *a, i);
+}
+
+int plan_exec_checks(tfft_plan_t p, const void* in, void* out, cudaStream_t s) {
+  if (!p) return TFFT_ERR_INVALID_ARG;
+  return exec_checks(p, in, out, s, 0, p->batch);
+}
+
+void plan_exec_finish(tfft_plan_t p, cudaStream_t s) {
+  p->pending = FaultSite{};     // armed faults last one exec
+  for (auto& f : p->pending_more) f = FaultSite{};
+  p->npending = 0;
+  p->execs++;
+  p->last_stream = s;
+  p->used = true;
+}
 
 int plan_set_signal_offsets(tfft_plan_t p, const long long* d_off, const int64_t* h_off, int64_t total) {
   if (!p || !d_off || !h_off || total < p->n) return TFFT_ERR_INVALID_ARG;

@@ -19,10 +19,20 @@
 // the small buckets are launch-bound).  An exec with a test fault armed runs
 // uncaptured.  At plan time an optional autotuner times the pass counts a
 // bucket's length admits (one, two or three launches) and keeps the fastest.
+//
+// The persistent form (TFFT_RAGGED_PERSISTENT) runs the passes of the
+// buckets whose every pass is on the 256-thread complex64 tile kernels as
+// pass families instead: all passes of one role and sub-transform length, of
+// every such bucket, in one persistent launch whose blocks take (bucket,
+// chunk range) items, sorted by work, from an atomic counter.  A family waits
+// for the families of the previous pass of its buckets; each bucket then
+// verifies and corrects on its own stream.  Other buckets run their plans as
+// above, alongside.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -54,12 +64,27 @@ __global__ void ragged_copy_kernel(const Segment* seg, long long nseg, const uns
 
 struct Bucket {
   int64_t n = 0;
+  bool persistent = false;    // its passes run in the pass families
+  std::vector<int> fam;       // family of each pass (persistent buckets)
   std::vector<int64_t> sig;   // caller indices of the bucket's signals, in order
   int64_t first = 0;          // index of the bucket's first entry in the offset table
   bool direct = false;        // addressed in place through the offset table
   int64_t base = 0;           // staged: element offset of the bucket in the staging areas
   tfft_plan_t plan = nullptr;
   int passes = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+// One pass family of the persistent form: the pass `pass` (role, nsub) of
+// every member bucket.
+struct Family {
+  int pass = 0, role = 0, nsub = 0;
+  std::vector<int> members;                   // bucket indices (at most kRaggedMax)
+  std::vector<tfft::RaggedItem> items;        // .bucket: index into members
+  tfft::RaggedItem* d_items = nullptr;
+  size_t smem = 0;
+  int grid = 1;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
 };
@@ -90,6 +115,10 @@ struct tfft_ragged_s {
   void* g_out = nullptr;
   bool fault_armed = false;
   int64_t execs = 0;
+  // persistent form
+  std::vector<Family> fams;
+  unsigned long long* d_heads = nullptr;      // one item counter per family
+  int64_t fam_launches = 0;
   std::mutex mu;
 };
 
@@ -98,6 +127,12 @@ namespace {
 void free_ragged(tfft_ragged_s* r) {
   if (r->gexec) cudaGraphExecDestroy(r->gexec);
   if (r->graph) cudaGraphDestroy(r->graph);
+  for (auto& f : r->fams) {
+    if (f.d_items) cudaFree(f.d_items);
+    if (f.stream) cudaStreamDestroy(f.stream);
+    if (f.done) cudaEventDestroy(f.done);
+  }
+  if (r->d_heads) cudaFree(r->d_heads);
   for (auto& b : r->buckets) {
     if (b.plan) tfft_destroy(b.plan);
     if (b.stream) cudaStreamDestroy(b.stream);
@@ -138,23 +173,155 @@ int launch_copy(const tfft_ragged_s* r, const Segment* seg, const void* src, voi
   return e == cudaSuccess ? TFFT_SUCCESS : record_cuda_error(e);
 }
 
-// gather (staged buckets), bucket plans on their streams, scatter -- all on
-// or joined to `s`
+const void* bucket_in(const tfft_ragged_s* r, const Bucket& b, const void* in) {
+  return b.direct ? in : static_cast<const unsigned char*>(r->stage_in) + (size_t)b.base * r->esize;
+}
+void* bucket_out(const tfft_ragged_s* r, const Bucket& b, void* out) {
+  return b.direct ? out : static_cast<unsigned char*>(r->stage_out) + (size_t)b.base * r->esize;
+}
+
+// gather (staged buckets), the pass families and each persistent bucket's
+// verification, the other bucket plans on their streams, scatter -- all on or
+// joined to `s`
 int enqueue(tfft_ragged_s* r, const void* in, void* out, cudaStream_t s) {
   int rc;
   if ((rc = launch_copy(r, r->d_gather, in, r->stage_in, s))) return rc;
   cudaError_t e;
+  if (!r->fams.empty() &&
+      (e = cudaMemsetAsync(r->d_heads, 0, r->fams.size() * sizeof(unsigned long long), s)) != cudaSuccess)
+    return record_cuda_error(e);
   if ((e = cudaEventRecord(r->fork, s)) != cudaSuccess) return record_cuda_error(e);
+  // families in pass order: each after the families of its buckets' previous pass
+  for (size_t fi = 0; fi < r->fams.size(); fi++) {
+    Family& f = r->fams[fi];
+    if (f.pass == 0) {
+      if ((e = cudaStreamWaitEvent(f.stream, r->fork, 0)) != cudaSuccess) return record_cuda_error(e);
+    } else {
+      std::vector<int> deps;
+      for (int m : f.members) deps.push_back(r->buckets[m].fam[f.pass - 1]);
+      std::sort(deps.begin(), deps.end());
+      deps.erase(std::unique(deps.begin(), deps.end()), deps.end());
+      for (int d : deps)
+        if ((e = cudaStreamWaitEvent(f.stream, r->fams[d].done, 0)) != cudaSuccess) return record_cuda_error(e);
+    }
+    // the members' parameters for this (in, out), with any armed test fault
+    tfft::RaggedParams rp{};
+    for (size_t k = 0; k < f.members.size(); k++) {
+      const Bucket& b = r->buckets[f.members[k]];
+      if ((rc = tfft::plan_pass_params(b.plan, bucket_in(r, b, in), bucket_out(r, b, out), f.pass, &rp.pp[k])))
+        return rc;
+    }
+    rp.nitems = (long long)f.items.size();
+    rp.items = f.d_items;
+    rp.head = r->d_heads + fi;
+    if ((e = tfft::launch_v3_ragged(f.role, f.nsub, rp, f.grid, f.smem, f.stream)) != cudaSuccess)
+      return record_cuda_error(e);
+    r->fam_launches++;
+    if ((e = cudaEventRecord(f.done, f.stream)) != cudaSuccess) return record_cuda_error(e);
+  }
   for (auto& b : r->buckets) {
-    if ((e = cudaStreamWaitEvent(b.stream, r->fork, 0)) != cudaSuccess) return record_cuda_error(e);
-    const size_t boff = (size_t)b.base * r->esize;
-    const void* bin = b.direct ? in : static_cast<const unsigned char*>(r->stage_in) + boff;
-    void* bout = b.direct ? out : static_cast<unsigned char*>(r->stage_out) + boff;
-    if ((rc = tfft_exec(b.plan, bin, bout, (tfft_stream_t)b.stream))) return rc;
+    const void* bin = bucket_in(r, b, in);
+    void* bout = bucket_out(r, b, out);
+    if (b.persistent) {
+      if ((e = cudaStreamWaitEvent(b.stream, r->fams[b.fam.back()].done, 0)) != cudaSuccess)
+        return record_cuda_error(e);
+      if ((rc = tfft::plan_exec_checks(b.plan, bin, bout, b.stream))) return rc;
+      tfft::plan_exec_finish(b.plan, b.stream);
+    } else {
+      if ((e = cudaStreamWaitEvent(b.stream, r->fork, 0)) != cudaSuccess) return record_cuda_error(e);
+      if ((rc = tfft_exec(b.plan, bin, bout, (tfft_stream_t)b.stream))) return rc;
+    }
     if ((e = cudaEventRecord(b.done, b.stream)) != cudaSuccess) return record_cuda_error(e);
     if ((e = cudaStreamWaitEvent(s, b.done, 0)) != cudaSuccess) return record_cuda_error(e);
   }
   return launch_copy(r, r->d_scatter, r->stage_out, out, s);
+}
+
+// The pass families of the buckets whose every pass a persistent kernel
+// covers; their work items (ranges of chunks of about equal work, at least
+// four tiles each, about four per block of a full grid) sorted largest first.
+int plan_families(tfft_ragged_s* r) {
+  std::map<std::tuple<int, int, int>, int> index;
+  for (size_t bi = 0; bi < r->buckets.size(); bi++) {
+    Bucket& b = r->buckets[bi];
+    std::vector<tfft::RaggedPass> rp(b.passes);
+    bool ok = true;
+    for (int i = 0; i < b.passes && ok; i++) {
+      if (tfft::plan_ragged_pass(b.plan, i, &rp[i]) != TFFT_SUCCESS) return TFFT_ERR_INVALID_ARG;
+      ok = rp[i].ok != 0;
+    }
+    if (!ok) continue;
+    b.persistent = true;
+    b.fam.resize(b.passes);
+    for (int i = 0; i < b.passes; i++) {
+      const auto key = std::make_tuple(i, rp[i].role, rp[i].nsub);
+      auto it = index.find(key);
+      if (it != index.end() && r->fams[it->second].members.size() >= (size_t)tfft::kRaggedMax) {
+        index.erase(it);                  // a full family: the next members start another
+        it = index.end();
+      }
+      if (it == index.end()) {
+        it = index.emplace(key, (int)r->fams.size()).first;
+        r->fams.emplace_back();
+        Family& f = r->fams.back();
+        f.pass = i; f.role = rp[i].role; f.nsub = rp[i].nsub;
+      }
+      Family& f = r->fams[it->second];
+      f.smem = std::max(f.smem, rp[i].smem);
+      b.fam[i] = it->second;
+      const int mk = (int)f.members.size();
+      f.members.push_back((int)bi);
+      // the member's items, appended; sized below once every member is known
+      f.items.push_back(tfft::RaggedItem{mk, rp[i].tiles_per_chunk, 0, rp[i].nchunks});
+    }
+  }
+  // families in pass order (stable), so that a family's dependencies come first
+  std::vector<int> order(r->fams.size());
+  for (size_t k = 0; k < order.size(); k++) order[k] = (int)k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return r->fams[a].pass < r->fams[b].pass; });
+  std::vector<int> where(order.size());
+  for (size_t k = 0; k < order.size(); k++) where[order[k]] = (int)k;
+  std::vector<Family> sorted;
+  for (int k : order) sorted.push_back(std::move(r->fams[k]));
+  r->fams = std::move(sorted);
+  for (auto& b : r->buckets)
+    for (int& fi : b.fam) fi = where[fi];
+  for (auto& f : r->fams) {
+    int bps = 0;
+    cudaError_t e = tfft::v3_ragged_attrs(f.role, f.nsub, f.smem, &bps);
+    if (e != cudaSuccess || bps < 1) { cudaGetLastError(); return TFFT_ERR_UNSUPPORTED; }
+    const int64_t cap = (int64_t)r->sms * bps;
+    // one entry per member so far: {member, tiles a chunk, 0, chunks}
+    std::vector<tfft::RaggedItem> whole = std::move(f.items);
+    f.items.clear();
+    int64_t tiles = 0;
+    for (const auto& w : whole) tiles += (int64_t)w.pad * w.c1;
+    const int64_t item_tiles = std::max<int64_t>(4, (tiles + 4 * cap - 1) / (4 * cap));
+    std::vector<std::pair<int64_t, tfft::RaggedItem>> items;
+    for (const auto& w : whole) {
+      const int64_t per = std::max<int64_t>(1, (item_tiles + w.pad - 1) / w.pad);    // chunks an item
+      for (int64_t c = 0; c < w.c1; c += per) {
+        const int64_t c1 = std::min<int64_t>(w.c1, c + per);
+        items.push_back({(c1 - c) * w.pad, tfft::RaggedItem{w.bucket, 0, c, c1}});
+      }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    for (const auto& it : items) f.items.push_back(it.second);
+    f.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)f.items.size(), cap));
+    if (cudaMalloc(&f.d_items, f.items.size() * sizeof(tfft::RaggedItem)) != cudaSuccess ||
+        cudaMemcpy(f.d_items, f.items.data(), f.items.size() * sizeof(tfft::RaggedItem), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return TFFT_ERR_ALLOC;
+    }
+  }
+  if (!r->fams.empty() && cudaMalloc(&r->d_heads, r->fams.size() * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return TFFT_ERR_ALLOC;
+  }
+  return TFFT_SUCCESS;
 }
 
 // A scratch pair of the packed size for the autotuner's timings of direct
@@ -192,7 +359,8 @@ int plan_bucket(tfft_ragged_s* r, const Bucket& b, const std::vector<long long>&
 
 extern "C" int tfft_ragged_plan(tfft_ragged_t* out, const int64_t* lengths, int64_t count, int dtype,
                                 int abft_mode, int flags) {
-  if (!out || !lengths || count < 1 || (flags & ~(TFFT_RAGGED_AUTOTUNE | TFFT_RAGGED_STAGED)))
+  if (!out || !lengths || count < 1 ||
+      (flags & ~(TFFT_RAGGED_AUTOTUNE | TFFT_RAGGED_STAGED | TFFT_RAGGED_PERSISTENT)))
     return TFFT_ERR_INVALID_ARG;
   *out = nullptr;
   if (dtype != TFFT_C64 && dtype != TFFT_C128) return TFFT_ERR_UNSUPPORTED;
@@ -347,6 +515,10 @@ extern "C" int tfft_ragged_plan(tfft_ragged_t* out, const int64_t* lengths, int6
     }
     if (cudaDeviceSynchronize() != cudaSuccess) { free_ragged(r); return TFFT_ERR_CUDA; }
   }
+  if (flags & TFFT_RAGGED_PERSISTENT) {
+    const int rc = plan_families(r);
+    if (rc) { free_ragged(r); return rc; }
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) { free_ragged(r); return TFFT_ERR_CUDA; }
   *out = r;
   return TFFT_SUCCESS;
@@ -405,6 +577,7 @@ extern "C" int tfft_ragged_report(tfft_ragged_t r, tfft_stats* st) {
     st->launches += s.launches;
     st->max_clean_ratio = std::max(st->max_clean_ratio, s.max_clean_ratio);
   }
+  st->launches += r->fam_launches;
   st->execs = r->execs;
   return TFFT_SUCCESS;
 }
@@ -427,6 +600,14 @@ extern "C" int tfft_ragged_info(tfft_ragged_t r, int64_t* buckets, int64_t* leng
     if (passes) passes[k] = r->buckets[k].passes;
     if (direct) direct[k] = r->buckets[k].direct ? 1 : 0;
   }
+  return TFFT_SUCCESS;
+}
+
+extern "C" int tfft_ragged_families(tfft_ragged_t r, int64_t* families, int64_t* persistent_buckets) {
+  if (!r || !families || !persistent_buckets) return TFFT_ERR_INVALID_ARG;
+  *families = (int64_t)r->fams.size();
+  *persistent_buckets = 0;
+  for (const auto& b : r->buckets) *persistent_buckets += b.persistent ? 1 : 0;
   return TFFT_SUCCESS;
 }
 

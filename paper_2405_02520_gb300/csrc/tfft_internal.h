@@ -377,4 +377,44 @@ cudaError_t launch_c128_to_c64(const void* src, void* dst, int64_t n, cudaStream
 cudaError_t launch_gather_classes(const void* src, void* dst, int64_t M, int64_t nl, cudaStream_t s);
 cudaError_t launch_fix_apply(const FixParams& f, cudaStream_t s);
 
+// Persistent tile kernels for ragged batches (v3_ragged*.cu): one launch
+// runs one pass family -- the passes of one role (0 single, 1 column, 2 last;
+// complex64, 256 threads) and sub-transform length -- for up to kRaggedMax
+// buckets, each with its own pass parameters, all in the launch's parameter
+// block (tensor maps included, as in the batched launches).  Its blocks take
+// work items -- a range of one bucket's chunks -- in order from `items`
+// through the counter *head (zero before the launch); the plan sorts the
+// items by work, largest first.
+constexpr int kRaggedMax = 24;          // 24 x 1152 bytes of pass parameters: under 32 KB
+struct RaggedItem {
+  int bucket;             // index into pp
+  int pad;
+  long long c0, c1;       // chunks [c0, c1) of that bucket's pass
+};
+struct RaggedParams {
+  PassParams pp[kRaggedMax];
+  long long nitems;
+  const RaggedItem* items;
+  unsigned long long* head;
+};
+// whether a persistent kernel covers the family (role, nsub)
+bool v3_ragged_has(int role, int nsub);
+cudaError_t v3_ragged_attrs(int role, int nsub, size_t smem, int* bps);
+cudaError_t launch_v3_ragged(int role, int nsub, const RaggedParams& r, int grid, size_t smem, cudaStream_t s);
+
+// Plan hooks for the persistent ragged form (plan.cu): what pass i of a
+// whole-batch exec would launch, the exec's verification and correction
+// after its passes ran elsewhere, and the exec's bookkeeping.
+struct RaggedPass {
+  int ok;                 // the pass runs on a kernel the persistent form has
+  int role, nsub;
+  size_t smem;            // dynamic shared memory of a block
+  long long nchunks;      // chunks of a whole-batch exec
+  int tiles_per_chunk;    // about
+};
+int plan_ragged_pass(tfft_plan_s* p, int i, RaggedPass* rp);
+int plan_pass_params(tfft_plan_s* p, const void* in, void* out, int i, PassParams* a);
+int plan_exec_checks(tfft_plan_s* p, const void* in, void* out, cudaStream_t s);
+void plan_exec_finish(tfft_plan_s* p, cudaStream_t s);
+
 }  // namespace tfft

@@ -1,5 +1,6 @@
 """Ragged batches (signals of different lengths packed back to back) on the
-GPU against the oracle, with graph replay, re-capture and corrected faults."""
+GPU against the oracle, with graph replay, re-capture and corrected faults,
+in the bucket-stream form and the persistent pass-family form."""
 import numpy as np
 import pytest
 
@@ -35,11 +36,19 @@ def _check(lengths, x, y, *guarded):
     return worst
 
 
-@pytest.mark.parametrize("autotune,staged", [(False, False), (True, False), (False, True)])
-def test_ragged_matches_oracle_and_replays(autotune, staged):
+@pytest.mark.parametrize("autotune,staged,persistent", [(False, False, False), (True, False, False),
+                                                        (False, True, False), (False, False, True),
+                                                        (False, True, True)])
+def test_ragged_matches_oracle_and_replays(autotune, staged, persistent):
     import torch
     lengths, x = _ragged_input(400, seed=5)
-    r = t.Ragged(lengths.tolist(), autotune=autotune, staged=staged)
+    r = t.Ragged(lengths.tolist(), autotune=autotune, staged=staged, persistent=persistent)
+    fams, pb = r.families()
+    if persistent:
+        # every bucket of 256 points or more runs on the 256-thread tile kernels
+        assert pb == sum(1 for n in set(lengths.tolist()) if n >= 256) and fams >= pb, (fams, pb)
+    else:
+        assert (fams, pb) == (0, 0)
     assert sorted(n for n, _ in r.info()) == sorted(set(lengths.tolist()))
     # lengths 2^6..2^16: every offset is a multiple of 64 elements, so every
     # bucket is addressed in place unless staging is forced
@@ -65,10 +74,11 @@ def test_ragged_matches_oracle_and_replays(autotune, staged):
     r.destroy()
 
 
-def test_ragged_faults_in_two_buckets_corrected():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_ragged_faults_in_two_buckets_corrected(persistent):
     import torch
     lengths, x = _ragged_input(300, seed=55)
-    r = t.Ragged(lengths.tolist(), autotune=False)
+    r = t.Ragged(lengths.tolist(), autotune=False, persistent=persistent)
     xg = Guarded(x.shape, None, fill=torch.from_numpy(x).cuda())
     yg = Guarded(x.shape, xg.t.dtype)
     xt, yt = xg.t, yg.t
@@ -115,12 +125,13 @@ def _fault_sites(lengths, per_1000, seed):
     return out
 
 
-def test_ragged_one_fault_per_thousand_signals():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_ragged_one_fault_per_thousand_signals(persistent):
     """4000 signals (2^6..2^12 points), four faults in distinct groups in one
     exec: all detected and corrected."""
     import torch
     lengths, x = _ragged_input(4000, seed=505, lo=6, hi=12)
-    r = t.Ragged(lengths.tolist(), autotune=False)
+    r = t.Ragged(lengths.tolist(), autotune=False, persistent=persistent)
     passes = dict(r.info())
     sites = _fault_sites(lengths, 1, seed=7)
     assert len(sites) == 4
@@ -139,7 +150,8 @@ def test_ragged_one_fault_per_thousand_signals():
     r.destroy()
 
 
-def test_ragged_mixed_direct_and_staged_buckets():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_ragged_mixed_direct_and_staged_buckets(persistent):
     """Lengths 2, 8, 256, 8192 and 65536: the short signals leave the
     multi-pass buckets' offsets off the 16-element box grid, so those buckets
     are staged while the others are addressed in place; faults in a staged and
@@ -152,7 +164,7 @@ def test_ragged_mixed_direct_and_staged_buckets():
     x = np.empty(total, dtype=np.complex64)
     x.real = rng.uniform(-1, 1, total).astype(np.float32)
     x.imag = rng.uniform(-1, 1, total).astype(np.float32)
-    r = t.Ragged(lengths.tolist(), autotune=False)
+    r = t.Ragged(lengths.tolist(), autotune=False, persistent=persistent)
     lay = r.layout()
     assert lay[8192] is False and lay[256] is True and lay[2] is True, lay
     passes = dict(r.info())
@@ -174,13 +186,14 @@ def test_ragged_mixed_direct_and_staged_buckets():
     r.destroy()
 
 
-def test_ragged_one_sided_recompute_in_place():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_ragged_one_sided_recompute_in_place(persistent):
     """One-sided checks on a ragged batch addressed in place: a detected
     signal is recomputed from the caller's input and written back at its
     caller offset."""
     import torch
     lengths, x = _ragged_input(120, seed=909, lo=8, hi=14)
-    r = t.Ragged(lengths.tolist(), abft_mode=t.TFFT_ABFT_ONE_SIDED, autotune=False)
+    r = t.Ragged(lengths.tolist(), abft_mode=t.TFFT_ABFT_ONE_SIDED, autotune=False, persistent=persistent)
     assert all(r.layout().values())
     passes = dict(r.info())
     xg = Guarded(x.shape, None, fill=torch.from_numpy(x).cuda())
@@ -228,3 +241,28 @@ def test_ragged_complex128_in_place():
     st = r.report()
     assert st["detected"] == 1 and st["corrected"] + st["recomputed"] == 1, st
     r.destroy()
+
+
+def test_persistent_families_match_bucket_streams_bitwise():
+    """The pass families run the same tile-kernel body on the same chunks as
+    the buckets' own launches: the outputs agree bit for bit, clean, over
+    two execs (the second a graph replay)."""
+    import torch
+    lengths, x = _ragged_input(1500, seed=31, lo=6, hi=16)
+    xg = Guarded(x.shape, None, fill=torch.from_numpy(x).cuda())
+    outs = []
+    for persistent in (False, True):
+        r = t.Ragged(lengths.tolist(), autotune=False, persistent=persistent)
+        yg = Guarded(x.shape, xg.t.dtype)
+        for _ in range(2):
+            yg.t.zero_()
+            r.exec(xg.t, yg.t)
+            torch.cuda.synchronize()
+            outs.append(yg.t.cpu().numpy())
+        yg.check("ragged output")
+        st = r.report()
+        assert st["detected"] == 0, st
+        r.destroy()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[2], outs[3])
+    assert np.array_equal(outs[0], outs[2])
+    _check(lengths, x, outs[2], xg)
