@@ -197,6 +197,7 @@ struct tfft_plan_s {
   const void* last_in = nullptr;    // the previous whole-batch exec's buffers
   void* last_out = nullptr;
   bool cg_off = false;              // building failed once: stream launches only
+  bool cg_full = false;             // the cached graph also holds the passes
   // tfft_exec_host pipeline: copy streams and per-chunk events, made on first use
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t ev_entry = nullptr, ev_end = nullptr;
@@ -1262,7 +1263,8 @@ int enqueue_correction(tfft_plan_s* p, const FixParams& f, const void* in, void*
 // (cudaGraphSetConditional) when it queues a group, so a clean exec runs one
 // graph launch after its passes instead of the five to nine launches of the
 // correction sequence.  Returns nonzero (and leaves no graph) on any failure.
-int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, const void* in, void* out) {
+int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, const void* in, void* out,
+                           bool full) {
   if (p->cgx) { cudaGraphExecDestroy(p->cgx); p->cgx = nullptr; }
   if (p->cg) { cudaGraphDestroy(p->cg); p->cg = nullptr; }
   if (!p->gcap && cudaStreamCreateWithFlags(&p->gcap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1271,8 +1273,7 @@ int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, c
   }
   cudaGraph_t g = nullptr;
   cudaGraphConditionalHandle h{};
-  cudaGraphNode_t nodes[2];
-  size_t count = 2;
+  cudaGraphNode_t vnode = nullptr;
   cudaGraphNodeParams cp{};
   cudaGraph_t body = nullptr, out_g = nullptr;
   cudaGraphExec_t gx = nullptr;
@@ -1284,18 +1285,35 @@ int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, c
     ok = cudaStreamBeginCaptureToGraph(p->gcap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
          cudaSuccess;
     if (ok) {
-      const bool launched = launch_verify(v, p->gcap) == cudaSuccess;
-      ok = cudaStreamEndCapture(p->gcap, &out_g) == cudaSuccess && launched;
+      // the passes too (captured, not run: the plan's launch count and
+      // timing records stay as they were)
+      bool launched = true;
+      if (full) {
+        const int64_t launches = p->launches;
+        const bool timing = p->timing;
+        p->timing = false;
+        launched = run_passes(p, in, out, p->gcap, true, nullptr, 0, 0, 0, p->batch, -1, true, 0) == 0;
+        p->timing = timing;
+        p->launches = launches;
+      }
+      launched = launched && launch_verify(v, p->gcap) == cudaSuccess;
+      // the node just captured is the verification kernel
+      cudaStreamCaptureStatus st{};
+      const cudaGraphNode_t* deps = nullptr;
+      size_t ndeps = 0;
+      if (launched && cudaStreamGetCaptureInfo(p->gcap, &st, nullptr, nullptr, &deps, nullptr, &ndeps) == cudaSuccess &&
+          ndeps == 1)
+        vnode = deps[0];
+      ok = cudaStreamEndCapture(p->gcap, &out_g) == cudaSuccess && launched && vnode != nullptr;
     }
   }
-  ok = ok && cudaGraphGetNodes(g, nodes, &count) == cudaSuccess && count == 1;
   if (ok) {
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeIf;
     cp.conditional.size = 1;
     cudaGraphNode_t cn;
-    ok = cudaGraphAddNode(&cn, g, &nodes[0], nullptr, 1, &cp) == cudaSuccess;
+    ok = cudaGraphAddNode(&cn, g, &vnode, nullptr, 1, &cp) == cudaSuccess;
   }
   if (ok) {
     body = cp.conditional.phGraph_out[0];
@@ -1314,7 +1332,7 @@ int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, c
     }
   }
   cudaKernelNodeParams kp{};
-  ok = ok && cudaGraphKernelNodeGetParams(nodes[0], &kp) == cudaSuccess && kp.kernelParams;
+  ok = ok && cudaGraphKernelNodeGetParams(vnode, &kp) == cudaSuccess && kp.kernelParams;
   ok = ok && cudaGraphInstantiate(&gx, g, 0) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -1324,7 +1342,8 @@ int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, c
   }
   p->cg = g;
   p->cgx = gx;
-  p->cg_vnode = nodes[0];
+  p->cg_vnode = vnode;
+  p->cg_full = full;
   p->cg_kp = kp;
   p->cg_v = v;
   p->cg_lanes = *static_cast<int*>(kp.kernelParams[1]);
@@ -1333,7 +1352,104 @@ int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, c
   return 0;
 }
 
-int exec_checks(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_t b0, int64_t nb);
+// The verification and correction parameters of an exec over signals
+// [b0, b0 + nb) (in and out point at signal b0).
+void make_checks(tfft_plan_s* p, const void* in, void* out, int64_t b0, int64_t nb, VerifyParams& v,
+                 FixParams& f) {
+  const int64_t vg0 = b0 / p->vG;
+  v.n = p->n; v.batch = nb; v.group = p->vG; v.ngroups = (nb + p->vG - 1) / p->vG;
+  v.group_base = vg0;
+  v.slots_in = p->slots_in; v.slots_out = p->slots_out;
+  v.rec_in = p->rec_in + vg0 * p->slots_in; v.rec_out = p->rec_out + vg0 * p->slots_out;
+  // unit roundoff of the butterfly arithmetic: FP32, FP64, or the tensor-core forms
+  const double u = p->dtype != TFFT_C64 ? std::ldexp(1.0, -53)
+                 : p->prec == TFFT_PREC_TF32X3 ? std::ldexp(1.0, -20)
+                 : p->prec == TFFT_PREC_TF32 ? std::ldexp(1.0, -10)
+                 : p->prec == TFFT_PREC_BF16X3 ? std::ldexp(1.0, -17) : std::ldexp(1.0, -24);
+  // tau = kappa u (log2 N + 4) sqrt(N) sqrt(E): the log2 N term follows the
+  // rounding of the stages, the constant the fixed share of the checksum
+  // arithmetic itself (table rounding, FP32 accumulation), which dominates
+  // for very short transforms
+  const int lg = ilog2(p->n) + 4;
+  v.kappa_u_log2n_sqrtn = p->kappa * u * lg * std::sqrt((double)p->n);
+  v.detect_only = p->detect_only;
+  v.lists = p->lists; v.counters = p->counters; v.log = p->log; v.exec_index = p->execs;
+  v.max_blocks = 8 * p->sms;
+  v.split = p->vsplit; v.part_acc = p->part_acc; v.part_cnt = p->part_cnt;
+  if (p->sigrec) {
+    const int64_t b0s = vg0 * p->vG;
+    const size_t rin = p->dtype == TFFT_C64 ? sizeof(SigIn<float>) : sizeof(SigIn<double>);
+    const size_t rout = p->dtype == TFFT_C64 ? sizeof(SigOut<float>) : sizeof(SigOut<double>);
+    v.sigrec = 1;
+    v.dtype = p->dtype == TFFT_C64 ? 0 : 1;
+    v.sig_in = static_cast<const unsigned char*>(p->sig_in) + (size_t)b0s * p->sslots_in * rin;
+    v.sig_out = static_cast<const unsigned char*>(p->sig_out) + (size_t)b0s * p->sslots_out * rout;
+    v.sig_slots_in = p->sslots_in; v.sig_slots_out = p->sslots_out;
+    v.sig_split = p->sig_split;
+    v.sig_blk_lanes = p->sig_blk_lanes; v.sig_gpb = p->sig_gpb;
+    v.sig_acc = p->sig_acc ? p->sig_acc + b0s * kSigAcc : nullptr;
+    v.part_cnt = p->part_cnt ? p->part_cnt + vg0 : nullptr;
+    // a threshold never below that of signals whose every value is the
+    // smallest normal number of the element type
+    const double tiny = p->dtype == TFFT_C64 ? 1.1754943508222875e-38 : 2.2250738585072014e-308;
+    v.tau_floor = v.kappa_u_log2n_sqrtn * std::sqrt((double)p->n) * tiny;
+    if (p->chk2) {
+      const size_t rc2 = p->dtype == TFFT_C64 ? sizeof(SigChk<float>) : sizeof(SigChk<double>);
+      v.chk2 = 1;
+      v.sig_chk = static_cast<const unsigned char*>(p->sig_chk) + (size_t)b0s * p->sslots_out * rc2;
+      // the last pass alone: its n_last-point transform's rounding
+      const int lgl = ilog2(p->pp[p->passes - 1].nsub) + 4;
+      v.kappa_u_chk2 = p->kappa * u * lgl * std::sqrt((double)p->n);
+    }
+  }
+  f.n = p->n; f.batch = nb; f.group = p->vG; f.dtype = p->dtype;
+  f.in = in; f.out = out; f.soff = p->soff; f.ws_c1 = p->ws_c1; f.ws_acc = p->ws_acc; f.lists = p->lists;
+  f.counters = p->counters; f.err_flag = p->err_flag;
+}
+
+// Which cached graph a whole-batch exec on a stream that is not being
+// captured takes: 2 the whole exec (passes, verification, the conditional
+// correction) when no test fault is armed and no per-kernel timing is on and
+// `allow_full`; 1 the verification and correction only (after the passes'
+// stream launches); 0 none (stream launches).  A graph is built when a pair
+// of buffers comes back (an exec that rotates over many buffers keeps the
+// stream launches), and again when the kind it needs changes.
+int pick_graph(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_t b0, int64_t nb,
+               const VerifyParams& v, const FixParams& f, bool allow_full) {
+  if (!p->abft || b0 != 0 || nb != p->batch || p->cg_off) return 0;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  bool capturing = true;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess) capturing = cs != cudaStreamCaptureStatusNone;
+  else cudaGetLastError();        // e.g. the legacy stream during another thread's global capture
+  if (capturing) return 0;
+  const bool armed = p->npending > 0 || p->pending.mode != 0;
+  const bool full = allow_full && !p->timing && !armed;
+  const bool cached = p->cgx && p->cg_in == in && p->cg_out == out && p->cg_full == full;
+  const bool again = p->last_in == in && p->last_out == out;
+  p->last_in = in;
+  p->last_out = out;
+  if (!cached && again && build_correction_graph(p, v, f, in, out, full)) {
+    p->cg_off = true;
+    return 0;
+  }
+  if (p->cgx && p->cg_in == in && p->cg_out == out && p->cg_full == full) return full ? 2 : 1;
+  return 0;
+}
+
+// Launches the cached graph with this exec's index in the verification's
+// fault-log entries (timed as one launch; the whole-exec graph counts its
+// pass launches too).
+int launch_graph(tfft_plan_s* p, cudaStream_t s) {
+  VerifyParams v2 = p->cg_v;
+  v2.exec_index = p->execs;
+  int lanes = p->cg_lanes;
+  void* args[2] = {&v2, &lanes};
+  cudaKernelNodeParams kp = p->cg_kp;
+  kp.kernelParams = args;
+  TFFT_CUDA(cudaGraphExecKernelNodeSetParams(p->cgx, p->cg_vnode, &kp));
+  if (p->cg_full) p->launches += p->passes;
+  return timed_launch(p, 4, s, [&] { return cudaGraphLaunch(p->cgx, s); });
+}
 
 // The exec over signals [b0, b0 + nb) (b0 a multiple of G, nb > 0): the
 // passes, the verification of their groups and the correction path, all on
@@ -1343,98 +1459,30 @@ int exec_range(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
   in = static_cast<const unsigned char*>(in) + off;
   out = static_cast<unsigned char*>(out) + off;
   const int64_t vg0 = b0 / p->vG;
+  VerifyParams v{};
+  FixParams f{};
+  if (p->abft) make_checks(p, in, out, b0, nb, v, f);
+  const int gk = pick_graph(p, in, out, s, b0, nb, v, f, true);
+  if (gk == 2) return launch_graph(p, s);
   int rc = run_passes(p, in, out, s, true, nullptr, 0, 0, 0, nb, -1, true, vg0);
   if (rc) return rc;
-  return exec_checks(p, in, out, s, b0, nb);
+  if (!p->abft) return 0;
+  if (gk == 1) return launch_graph(p, s);
+  if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
+  return enqueue_correction(p, f, in, out, nb, s);
 }
 
 // The verification and correction of an exec over signals [b0, b0 + nb)
 // whose passes have been enqueued on `s` (in and out point at signal b0).
 int exec_checks(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_t b0, int64_t nb) {
+  if (!p->abft) return 0;
+  VerifyParams v{};
+  FixParams f{};
+  make_checks(p, in, out, b0, nb, v, f);
+  if (pick_graph(p, in, out, s, b0, nb, v, f, false) == 1) return launch_graph(p, s);
   int rc;
-  const int64_t vg0 = b0 / p->vG;
-  if (p->abft) {
-    VerifyParams v{};
-    v.n = p->n; v.batch = nb; v.group = p->vG; v.ngroups = (nb + p->vG - 1) / p->vG;
-    v.group_base = vg0;
-    v.slots_in = p->slots_in; v.slots_out = p->slots_out;
-    v.rec_in = p->rec_in + vg0 * p->slots_in; v.rec_out = p->rec_out + vg0 * p->slots_out;
-    // unit roundoff of the butterfly arithmetic: FP32, FP64, or the tensor-core forms
-    const double u = p->dtype != TFFT_C64 ? std::ldexp(1.0, -53)
-                   : p->prec == TFFT_PREC_TF32X3 ? std::ldexp(1.0, -20)
-                   : p->prec == TFFT_PREC_TF32 ? std::ldexp(1.0, -10)
-                   : p->prec == TFFT_PREC_BF16X3 ? std::ldexp(1.0, -17) : std::ldexp(1.0, -24);
-    // tau = kappa u (log2 N + 4) sqrt(N) sqrt(E): the log2 N term follows the
-    // rounding of the stages, the constant the fixed share of the checksum
-    // arithmetic itself (table rounding, FP32 accumulation), which dominates
-    // for very short transforms
-    const int lg = ilog2(p->n) + 4;
-    v.kappa_u_log2n_sqrtn = p->kappa * u * lg * std::sqrt((double)p->n);
-    v.detect_only = p->detect_only;
-    v.lists = p->lists; v.counters = p->counters; v.log = p->log; v.exec_index = p->execs;
-    v.max_blocks = 8 * p->sms;
-    v.split = p->vsplit; v.part_acc = p->part_acc; v.part_cnt = p->part_cnt;
-    if (p->sigrec) {
-      const int64_t b0s = vg0 * p->vG;
-      const size_t rin = p->dtype == TFFT_C64 ? sizeof(SigIn<float>) : sizeof(SigIn<double>);
-      const size_t rout = p->dtype == TFFT_C64 ? sizeof(SigOut<float>) : sizeof(SigOut<double>);
-      v.sigrec = 1;
-      v.dtype = p->dtype == TFFT_C64 ? 0 : 1;
-      v.sig_in = static_cast<const unsigned char*>(p->sig_in) + (size_t)b0s * p->sslots_in * rin;
-      v.sig_out = static_cast<const unsigned char*>(p->sig_out) + (size_t)b0s * p->sslots_out * rout;
-      v.sig_slots_in = p->sslots_in; v.sig_slots_out = p->sslots_out;
-      v.sig_split = p->sig_split;
-      v.sig_blk_lanes = p->sig_blk_lanes; v.sig_gpb = p->sig_gpb;
-      v.sig_acc = p->sig_acc ? p->sig_acc + b0s * kSigAcc : nullptr;
-      v.part_cnt = p->part_cnt ? p->part_cnt + vg0 : nullptr;
-      // a threshold never below that of signals whose every value is the
-      // smallest normal number of the element type
-      const double tiny = p->dtype == TFFT_C64 ? 1.1754943508222875e-38 : 2.2250738585072014e-308;
-      v.tau_floor = v.kappa_u_log2n_sqrtn * std::sqrt((double)p->n) * tiny;
-      if (p->chk2) {
-        const size_t rc2 = p->dtype == TFFT_C64 ? sizeof(SigChk<float>) : sizeof(SigChk<double>);
-        v.chk2 = 1;
-        v.sig_chk = static_cast<const unsigned char*>(p->sig_chk) + (size_t)b0s * p->sslots_out * rc2;
-        // the last pass alone: its n_last-point transform's rounding
-        const int lgl = ilog2(p->pp[p->passes - 1].nsub) + 4;
-        v.kappa_u_chk2 = p->kappa * u * lgl * std::sqrt((double)p->n);
-      }
-    }
-    FixParams f{};
-    f.n = p->n; f.batch = nb; f.group = p->vG; f.dtype = p->dtype;
-    f.in = in; f.out = out; f.soff = p->soff; f.ws_c1 = p->ws_c1; f.ws_acc = p->ws_acc; f.lists = p->lists;
-    f.counters = p->counters; f.err_flag = p->err_flag;
-    // a whole-batch exec on a stream that is not being captured:
-    // verification and correction from the graph (timed as one launch)
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    bool capturing = true;
-    if (b0 == 0 && nb == p->batch && !p->cg_off) {
-      if (cudaStreamIsCapturing(s, &cs) == cudaSuccess) capturing = cs != cudaStreamCaptureStatusNone;
-      else cudaGetLastError();        // e.g. the legacy stream during another thread's global capture
-    }
-    if (b0 == 0 && nb == p->batch && !p->cg_off && !capturing) {
-      // the graph is built when a pair of buffers comes back (an exec that
-      // rotates over many buffers keeps the direct launches)
-      const bool cached = p->cgx && p->cg_in == in && p->cg_out == out;
-      const bool again = p->last_in == in && p->last_out == out;
-      p->last_in = in;
-      p->last_out = out;
-      if (!cached && again && build_correction_graph(p, v, f, in, out)) p->cg_off = true;
-      if (p->cgx && p->cg_in == in && p->cg_out == out) {
-        VerifyParams v2 = p->cg_v;
-        v2.exec_index = p->execs;
-        int lanes = p->cg_lanes;
-        void* args[2] = {&v2, &lanes};
-        cudaKernelNodeParams kp = p->cg_kp;
-        kp.kernelParams = args;
-        TFFT_CUDA(cudaGraphExecKernelNodeSetParams(p->cgx, p->cg_vnode, &kp));
-        return timed_launch(p, 4, s, [&] { return cudaGraphLaunch(p->cgx, s); });
-      }
-    }
-    if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
-    return enqueue_correction(p, f, in, out, nb, s);
-  }
-  return 0;
+  if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
+  return enqueue_correction(p, f, in, out, nb, s);
 }
 
 int exec_device(tfft_plan_s* p, const void* in, void* out, cudaStream_t s) {
