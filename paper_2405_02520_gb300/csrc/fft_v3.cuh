@@ -707,6 +707,7 @@ __device__ __forceinline__ bool v3_body(const PassParams& p, long long cfirst, l
   int k0 = 0;                   // (k of output q = 0) mod 3
   Partials<real> acc;
   bool setup_done = false;
+  long long setup_hi = -1, setup_lo0 = -1;   // the line block the setup was made for
   // the input side of the checksum runs in the first pass (single or
   // column role), the output side in the last (single or last role): the
   // other side is compiled out of each role
@@ -773,7 +774,13 @@ __device__ __forceinline__ bool v3_body(const PassParams& p, long long cfirst, l
       continue;
     }
     const long long hi = cur.hi(p), lo0 = cur.lo0(p);
-    if (ROLE != V3_SINGLE || !setup_done) {
+    // the checksum weights, signs and residues of a thread depend only on the
+    // line block (hi, lo0) of the chunk (the single pass: on nothing), so a
+    // block whose chunks keep their line block -- a grid that is a multiple
+    // of the line blocks -- sets them up once
+    if (!setup_done || (ROLE != V3_SINGLE && (hi != setup_hi || lo0 != setup_lo0))) {
+      setup_hi = hi;
+      setup_lo0 = lo0;
       setup_positions(hi, lo0);
       setup_done = true;
     }

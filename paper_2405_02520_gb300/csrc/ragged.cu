@@ -239,7 +239,10 @@ int enqueue(tfft_ragged_s* r, const void* in, void* out, cudaStream_t s) {
 
 // The pass families of the buckets whose every pass a persistent kernel
 // covers; their work items (ranges of chunks of about equal work, at least
-// four tiles each, about four per block of a full grid) sorted largest first.
+// four tiles each, about four per block of a full grid) sorted largest
+// first.  (About one item per block, each at least eight tiles, measured
+// slower: 1.90 against 1.87 ms on the 20,000-signal batch; the balance of
+// the last items outweighs the restart of the tile pipeline at each item.)
 int plan_families(tfft_ragged_s* r) {
   std::map<std::tuple<int, int, int>, int> index;
   for (size_t bi = 0; bi < r->buckets.size(); bi++) {
