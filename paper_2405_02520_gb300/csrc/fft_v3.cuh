@@ -30,6 +30,7 @@
 #pragma once
 
 #include "fft_tile.cuh"
+#include "sigverify.cuh"
 #include "tc.cuh"
 
 namespace tfft {
@@ -1116,6 +1117,9 @@ template <typename real, int NSUB, int E, int ROLE, int TC = 0, int NT = 256>
 __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() : 1)) fft_v3_kernel(const __grid_constant__ PassParams p) {
   __shared__ V3Smem<NT / 32> vs;
   v3_body<real, NSUB, E, ROLE, TC, NT>(p, blockIdx.x, gridDim.x, p.nchunks, blockIdx.x == 0, vs);
+  if constexpr (ROLE == V3_SINGLE) {
+    if (p.fverify) fused_verify<real>(&p);
+  }
 }
 
 }  // namespace tfft

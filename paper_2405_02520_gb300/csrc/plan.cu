@@ -198,6 +198,14 @@ struct tfft_plan_s {
   void* last_out = nullptr;
   bool cg_off = false;              // building failed once: stream launches only
   bool cg_full = false;             // the cached graph also holds the passes
+  // fused verification (single-pass plans of few groups, whole-batch execs):
+  // the pass kernel's last block verifies, with the parameters in fverify
+  int fuse = 0;
+  unsigned* fdone = nullptr;         // blocks done, reset by the last
+  VerifyParams* fverify = nullptr;   // without a conditional node
+  cudaGraphConditionalHandle fcond{};
+  bool fcond_on = false;             // the graph's handle goes into the pass parameters
+  PassParams cg_pp{};                // the captured pass node's parameters (fused plans)
   // tfft_exec_host pipeline: copy streams and per-chunk events, made on first use
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t ev_entry = nullptr, ev_end = nullptr;
@@ -243,7 +251,7 @@ void free_plan(tfft_plan_s* p) {
   void* bufs[] = {p->tw_sub, p->twN_lo, p->twN_hi, p->wt_lo, p->wt_hi, p->wtab, p->tmp, p->rec_in, p->rec_out,
                   p->lists_mem, p->counters, p->log, p->ws_c1, p->ws_acc, p->stage_in, p->stage_out,
                   p->err_flag, p->part_acc, p->part_cnt, p->sig_in, p->sig_out, p->sig_acc, p->ltab,
-                  p->sig_chk};
+                  p->sig_chk, p->fdone, p->fverify};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& q : p->pp)
@@ -915,6 +923,31 @@ int plan_wtable(tfft_plan_s* p) {
 // L + M k by an n_last-point DFT, so u2[L][n] = sum_k r2[L + M k] w_nl^(n k):
 // the classes gathered into rows and transformed by the library's own
 // complex128 path, then rounded to the plan's element type.
+void make_checks(tfft_plan_s* p, const void* in, void* out, int64_t b0, int64_t nb, VerifyParams& v,
+                 FixParams& f);
+
+// Fused verification: single-pass plans with per-signal records whose
+// groups one block verifies in a few rounds (at most kFuseGroups groups, few
+// records a signal) let the pass kernel's last block verify a whole-batch
+// exec -- one launch and one graph node less for small transforms.
+constexpr int64_t kFuseGroups = 64;
+int plan_fused(tfft_plan_s* p) {
+  const bool want = p->abft && p->sigrec && p->passes == 1 && p->pp[0].v3 && p->pp[0].role == 0 &&
+                    p->vgroups <= kFuseGroups && p->sig_split == 0 && p->sig_blk_lanes == 0;
+  if (!want) return 0;
+  VerifyParams v{};
+  FixParams f{};
+  make_checks(p, nullptr, nullptr, 0, p->batch, v, f);
+  v.cond_flag = nullptr;
+  TFFT_CUDA(cudaMalloc(&p->fdone, sizeof(unsigned)));
+  TFFT_CUDA(cudaMemset(p->fdone, 0, sizeof(unsigned)));
+  TFFT_CUDA(cudaMalloc(&p->fverify, sizeof(VerifyParams)));
+  TFFT_CUDA(cudaMemcpy(p->fverify, &v, sizeof(VerifyParams), cudaMemcpyHostToDevice));
+  p->workspace_bytes += (int64_t)(sizeof(unsigned) + sizeof(VerifyParams));
+  p->fuse = 1;
+  return 0;
+}
+
 int plan_ltab(tfft_plan_s* p) {
   if (!p->chk2) return 0;
   const int64_t n = p->n, nl = p->pp[p->passes - 1].nsub, M = n / nl;
@@ -1237,6 +1270,16 @@ PassParams main_params(tfft_plan_s* p, int i, const void* in, void* out, int64_t
     a.zero_on_entry[1] = p->lists.rec;
     a.zero_on_entry[2] = p->cond_flag;
   }
+  // a whole-batch exec of a fused plan verifies in the pass kernel's last block
+  if (p->fuse && vgroup0 == 0 && batch == p->batch) {
+    a.fverify = p->fverify;
+    a.fdone = p->fdone;
+    a.exec_index = p->execs;
+    if (p->fcond_on) {
+      a.fcond_flag = p->cond_flag;
+      a.fcond = p->fcond;
+    }
+  }
   return a;
 }
 
@@ -1292,12 +1335,15 @@ int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, c
         const int64_t launches = p->launches;
         const bool timing = p->timing;
         p->timing = false;
+        p->fcond = h;
+        p->fcond_on = true;               // a fused pass switches this graph's correction on
         launched = run_passes(p, in, out, p->gcap, true, nullptr, 0, 0, 0, p->batch, -1, true, 0) == 0;
+        p->fcond_on = false;
         p->timing = timing;
         p->launches = launches;
       }
-      launched = launched && launch_verify(v, p->gcap) == cudaSuccess;
-      // the node just captured is the verification kernel
+      if (!p->fuse) launched = launched && launch_verify(v, p->gcap) == cudaSuccess;
+      // the node just captured is the verification kernel (a fused plan's pass kernel)
       cudaStreamCaptureStatus st{};
       const cudaGraphNode_t* deps = nullptr;
       size_t ndeps = 0;
@@ -1346,7 +1392,16 @@ int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, c
   p->cg_full = full;
   p->cg_kp = kp;
   p->cg_v = v;
-  p->cg_lanes = *static_cast<int*>(kp.kernelParams[1]);
+  if (p->fuse) {
+    // the clean form: a test fault armed while the graph was captured lasts
+    // that one exec
+    p->cg_pp = *static_cast<PassParams*>(kp.kernelParams[0]);
+    p->cg_pp.fault = FaultSite{};
+    for (auto& q : p->cg_pp.fault_more) q = FaultSite{};
+    p->cg_pp.nfault = 0;
+  } else {
+    p->cg_lanes = *static_cast<int*>(kp.kernelParams[1]);
+  }
   p->cg_in = in;
   p->cg_out = out;
   return 0;
@@ -1423,7 +1478,11 @@ int pick_graph(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
   else cudaGetLastError();        // e.g. the legacy stream during another thread's global capture
   if (capturing) return 0;
   const bool armed = p->npending > 0 || p->pending.mode != 0;
-  const bool full = allow_full && !p->timing && !armed;
+  // a fused plan's graph refreshes its one pass node every exec (an armed
+  // test fault included); it has no verification kernel to switch a
+  // graph's correction on but its pass, so it takes only the whole-exec graph
+  const bool full = allow_full && !p->timing && (p->fuse || !armed);
+  if (p->fuse && !full) return 0;
   const bool cached = p->cgx && p->cg_in == in && p->cg_out == out && p->cg_full == full;
   const bool again = p->last_in == in && p->last_out == out;
   p->last_in = in;
@@ -1444,10 +1503,27 @@ int launch_graph(tfft_plan_s* p, cudaStream_t s) {
   v2.exec_index = p->execs;
   int lanes = p->cg_lanes;
   void* args[2] = {&v2, &lanes};
+  // fused: the pass node verifies; its captured parameters with this exec's
+  // index, rebuilt (with the graph's conditional handle) when a test fault is
+  // armed for this exec
+  PassParams pp2{};
+  if (p->fuse) {
+    if (p->npending > 0 || p->pending.mode != 0) {
+      p->fcond_on = true;
+      pp2 = main_params(p, 0, p->cg_in, p->cg_out, p->batch, true, 0);
+      p->fcond_on = false;
+      const int rc = prepare_tma(p, pp2, 0);
+      if (rc) return rc;
+    } else {
+      pp2 = p->cg_pp;
+      pp2.exec_index = p->execs;
+    }
+  }
+  void* pargs[1] = {&pp2};
   cudaKernelNodeParams kp = p->cg_kp;
-  kp.kernelParams = args;
+  kp.kernelParams = p->fuse ? pargs : args;
   TFFT_CUDA(cudaGraphExecKernelNodeSetParams(p->cgx, p->cg_vnode, &kp));
-  if (p->cg_full) p->launches += p->passes;
+  if (p->cg_full) p->launches += p->passes - (p->fuse ? 1 : 0);
   return timed_launch(p, 4, s, [&] { return cudaGraphLaunch(p->cgx, s); });
 }
 
@@ -1468,7 +1544,8 @@ int exec_range(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
   if (rc) return rc;
   if (!p->abft) return 0;
   if (gk == 1) return launch_graph(p, s);
-  if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
+  const bool fused = p->fuse && b0 == 0 && nb == p->batch;     // the pass kernel verified
+  if (!fused && (rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
   return enqueue_correction(p, f, in, out, nb, s);
 }
 
@@ -1617,6 +1694,7 @@ int plan_create(tfft_plan_t* out, const tfft_plan_opts* o, int tuned) {
   if (!rc) rc = plan_workspace(p);
   if (!rc) rc = plan_wtable(p);
   if (!rc) rc = plan_ltab(p);
+  if (!rc) rc = plan_fused(p);
   if (rc) { free_plan(p); return rc; }
   *out = p;
   return TFFT_SUCCESS;
