@@ -198,14 +198,12 @@ struct tfft_plan_s {
   void* last_out = nullptr;
   bool cg_off = false;              // building failed once: stream launches only
   bool cg_full = false;             // the cached graph also holds the passes
-  // fused verification (single-pass plans of few groups, whole-batch execs):
+  // fused verification (single-pass plans of few groups, stream-launched whole-batch execs):
   // the pass kernel's last block verifies, with the parameters in fverify
   int fuse = 0;
   unsigned* fdone = nullptr;         // blocks done, reset by the last
   VerifyParams* fverify = nullptr;   // without a conditional node
-  cudaGraphConditionalHandle fcond{};
-  bool fcond_on = false;             // the graph's handle goes into the pass parameters
-  PassParams cg_pp{};                // the captured pass node's parameters (fused plans)
+
   // tfft_exec_host pipeline: copy streams and per-chunk events, made on first use
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t ev_entry = nullptr, ev_end = nullptr;
@@ -1275,10 +1273,6 @@ PassParams main_params(tfft_plan_s* p, int i, const void* in, void* out, int64_t
     a.fverify = p->fverify;
     a.fdone = p->fdone;
     a.exec_index = p->execs;
-    if (p->fcond_on) {
-      a.fcond_flag = p->cond_flag;
-      a.fcond = p->fcond;
-    }
   }
   return a;
 }
@@ -1335,15 +1329,15 @@ int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, c
         const int64_t launches = p->launches;
         const bool timing = p->timing;
         p->timing = false;
-        p->fcond = h;
-        p->fcond_on = true;               // a fused pass switches this graph's correction on
+        const int fuse = p->fuse;
+        p->fuse = 0;                      // the graph holds the separate verification kernel
         launched = run_passes(p, in, out, p->gcap, true, nullptr, 0, 0, 0, p->batch, -1, true, 0) == 0;
-        p->fcond_on = false;
+        p->fuse = fuse;
         p->timing = timing;
         p->launches = launches;
       }
-      if (!p->fuse) launched = launched && launch_verify(v, p->gcap) == cudaSuccess;
-      // the node just captured is the verification kernel (a fused plan's pass kernel)
+      launched = launched && launch_verify(v, p->gcap) == cudaSuccess;
+      // the node just captured is the verification kernel
       cudaStreamCaptureStatus st{};
       const cudaGraphNode_t* deps = nullptr;
       size_t ndeps = 0;
@@ -1392,16 +1386,7 @@ int build_correction_graph(tfft_plan_s* p, VerifyParams v, const FixParams& f, c
   p->cg_full = full;
   p->cg_kp = kp;
   p->cg_v = v;
-  if (p->fuse) {
-    // the clean form: a test fault armed while the graph was captured lasts
-    // that one exec
-    p->cg_pp = *static_cast<PassParams*>(kp.kernelParams[0]);
-    p->cg_pp.fault = FaultSite{};
-    for (auto& q : p->cg_pp.fault_more) q = FaultSite{};
-    p->cg_pp.nfault = 0;
-  } else {
-    p->cg_lanes = *static_cast<int*>(kp.kernelParams[1]);
-  }
+  p->cg_lanes = *static_cast<int*>(kp.kernelParams[1]);
   p->cg_in = in;
   p->cg_out = out;
   return 0;
@@ -1478,10 +1463,11 @@ int pick_graph(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
   else cudaGetLastError();        // e.g. the legacy stream during another thread's global capture
   if (capturing) return 0;
   const bool armed = p->npending > 0 || p->pending.mode != 0;
-  // a fused plan's graph refreshes its one pass node every exec (an armed
-  // test fault included); it has no verification kernel to switch a
-  // graph's correction on but its pass, so it takes only the whole-exec graph
-  const bool full = allow_full && !p->timing && (p->fuse || !armed);
+  const bool full = allow_full && !p->timing && !armed;
+  // a fused plan's stream-launched pass verifies itself, so it takes no
+  // verification-only graph; its whole-exec graph holds the separate
+  // verification kernel (measured faster there: 22.9 against 24.6 us at
+  // 1024 x 256, where the fused form saves a launch only on streams)
   if (p->fuse && !full) return 0;
   const bool cached = p->cgx && p->cg_in == in && p->cg_out == out && p->cg_full == full;
   const bool again = p->last_in == in && p->last_out == out;
@@ -1503,27 +1489,10 @@ int launch_graph(tfft_plan_s* p, cudaStream_t s) {
   v2.exec_index = p->execs;
   int lanes = p->cg_lanes;
   void* args[2] = {&v2, &lanes};
-  // fused: the pass node verifies; its captured parameters with this exec's
-  // index, rebuilt (with the graph's conditional handle) when a test fault is
-  // armed for this exec
-  PassParams pp2{};
-  if (p->fuse) {
-    if (p->npending > 0 || p->pending.mode != 0) {
-      p->fcond_on = true;
-      pp2 = main_params(p, 0, p->cg_in, p->cg_out, p->batch, true, 0);
-      p->fcond_on = false;
-      const int rc = prepare_tma(p, pp2, 0);
-      if (rc) return rc;
-    } else {
-      pp2 = p->cg_pp;
-      pp2.exec_index = p->execs;
-    }
-  }
-  void* pargs[1] = {&pp2};
   cudaKernelNodeParams kp = p->cg_kp;
-  kp.kernelParams = p->fuse ? pargs : args;
+  kp.kernelParams = args;
   TFFT_CUDA(cudaGraphExecKernelNodeSetParams(p->cgx, p->cg_vnode, &kp));
-  if (p->cg_full) p->launches += p->passes - (p->fuse ? 1 : 0);
+  if (p->cg_full) p->launches += p->passes;
   return timed_launch(p, 4, s, [&] { return cudaGraphLaunch(p->cgx, s); });
 }
 

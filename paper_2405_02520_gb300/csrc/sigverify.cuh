@@ -10,6 +10,13 @@
 
 namespace tfft {
 
+// An exec's own fields, given apart from the plan's verification parameters.
+struct ExecFields {
+  long long exec_index;
+  long long* cond_flag;
+  cudaGraphConditionalHandle cond;
+};
+
 // A record, read through the L2 (the fused verification reads records that
 // other blocks of the same launch wrote).
 template <typename T>
@@ -90,19 +97,33 @@ __device__ __forceinline__ void sig_add_records(const VerifyParams& v, int64_t b
                                                 int64_t o0, int64_t o1, int64_t step, SigSums<real>& a) {
   const SigIn<real>* rin = reinterpret_cast<const SigIn<real>*>(v.sig_in) + b * v.sig_slots_in;
   const SigOut<real>* rout = reinterpret_cast<const SigOut<real>*>(v.sig_out) + b * v.sig_slots_out;
-  for (int64_t k = i0; k < i1; k += step) {
-    const SigIn<real> r = ld_rec(rin + k);
-    a.q[0].add(r.sr); a.q[1].add(r.si); a.q[2].add(r.en);
+  // two records are loaded before either is added (two loads in flight; the
+  // sums are in the same order)
+  for (int64_t k = i0; k < i1; k += 2 * step) {
+    const bool two = k + step < i1;
+    const SigIn<real> r0 = ld_rec(rin + k);
+    SigIn<real> r1{};
+    if (two) r1 = ld_rec(rin + k + step);
+    a.q[0].add(r0.sr); a.q[1].add(r0.si); a.q[2].add(r0.en);
+    if (two) { a.q[0].add(r1.sr); a.q[1].add(r1.si); a.q[2].add(r1.en); }
   }
-  for (int64_t k = o0; k < o1; k += step) {
-    const SigOut<real> r = ld_rec(rout + k);
-    a.q[3].add(r.tr); a.q[4].add(r.ti);
+  for (int64_t k = o0; k < o1; k += 2 * step) {
+    const bool two = k + step < o1;
+    const SigOut<real> r0 = ld_rec(rout + k);
+    SigOut<real> r1{};
+    if (two) r1 = ld_rec(rout + k + step);
+    a.q[3].add(r0.tr); a.q[4].add(r0.ti);
+    if (two) { a.q[3].add(r1.tr); a.q[4].add(r1.ti); }
   }
   if (v.chk2) {
-    const SigChk<real> * rc = reinterpret_cast<const SigChk<real>*>(v.sig_chk) + b * v.sig_slots_out;
-    for (int64_t k = o0; k < o1; k += step) {
-      const SigChk<real> r = ld_rec(rc + k);
-      a.q[5].add(r.tr); a.q[6].add(r.ti); a.q[7].add(r.sr); a.q[8].add(r.si);
+    const SigChk<real>* rc = reinterpret_cast<const SigChk<real>*>(v.sig_chk) + b * v.sig_slots_out;
+    for (int64_t k = o0; k < o1; k += 2 * step) {
+      const bool two = k + step < o1;
+      const SigChk<real> r0 = ld_rec(rc + k);
+      SigChk<real> r1{};
+      if (two) r1 = ld_rec(rc + k + step);
+      a.q[5].add(r0.tr); a.q[6].add(r0.ti); a.q[7].add(r0.sr); a.q[8].add(r0.si);
+      if (two) { a.q[5].add(r1.tr); a.q[6].add(r1.ti); a.q[7].add(r1.sr); a.q[8].add(r1.si); }
     }
   }
 }
@@ -188,7 +209,13 @@ __device__ __forceinline__ void sig_test(const VerifyParams& v, SigGroup<real>& 
 // counters and the fault log.
 template <typename real>
 __device__ void decide_sig_group(const VerifyParams& v, int64_t g, int64_t gsize, const SigGroup<real>& c,
-                                 unsigned long long& clean_max) {
+                                 unsigned long long& clean_max, const ExecFields* ex = nullptr);
+
+// (ex: this exec's index and graph conditional in place of v's -- the fused
+// verification reads the plan's parameters where they lie)
+template <typename real>
+__device__ void decide_sig_group(const VerifyParams& v, int64_t g, int64_t gsize, const SigGroup<real>& c,
+                                 unsigned long long& clean_max, const ExecFields* ex) {
   const real res = sqrt(c.d1r * c.d1r + c.d1i * c.d1i);
   real tau = (real)v.kappa_u_log2n_sqrtn * sqrt(c.en > (real)0 ? c.en : (real)0);
   if (tau < (real)v.tau_floor) tau = (real)v.tau_floor;
@@ -232,13 +259,14 @@ __device__ void decide_sig_group(const VerifyParams& v, int64_t g, int64_t gsize
       }
     }
   }
-  if ((action == 1 || action == 2) && v.cond_flag &&
-      atomicExch(reinterpret_cast<unsigned long long*>(v.cond_flag), 1ull) == 0ull)
-    cudaGraphSetConditional(v.cond, 1u);      // run the correction body of this exec's graph
+  long long* const cond_flag = ex ? ex->cond_flag : v.cond_flag;
+  if ((action == 1 || action == 2) && cond_flag &&
+      atomicExch(reinterpret_cast<unsigned long long*>(cond_flag), 1ull) == 0ull)
+    cudaGraphSetConditional(ex ? ex->cond : v.cond, 1u);      // run the correction body of this exec's graph
   if (action == 3) atomicAdd(&v.counters->uncorrectable, 1ull);
   const unsigned long long slot = atomicAdd(&v.counters->log_total, 1ull);
   LogEvent ev;
-  ev.exec_index = v.exec_index;
+  ev.exec_index = ex ? ex->exec_index : v.exec_index;
   ev.group = v.group_base + g;
   ev.signal = bstar >= 0 ? v.group_base * v.group + gb + bstar : -1;
   ev.action = action;
@@ -261,7 +289,7 @@ __device__ void decide_sig_group(const VerifyParams& v, int64_t g, int64_t gsize
 // a single-pass kernel: all of them in one block).
 template <typename real>
 __device__ void verify_sig_serial(const VerifyParams& v, int lanes, unsigned long long& clean_max,
-                                  int64_t first_unit, int64_t unit_step) {
+                                  int64_t first_unit, int64_t unit_step, const ExecFields* ex = nullptr) {
   const int lane = threadIdx.x % lanes;
   const int64_t per_block = blockDim.x / lanes;
   for (int64_t g0 = first_unit * per_block; g0 < v.ngroups; g0 += unit_step * per_block) {
@@ -282,7 +310,7 @@ __device__ void verify_sig_serial(const VerifyParams& v, int lanes, unsigned lon
       }
     }
     for (int off = lanes >> 1; off > 0; off >>= 1) c.merge(c.shfl(off));
-    if (g < v.ngroups && lane == 0) decide_sig_group(v, g, gsize, c, clean_max);
+    if (g < v.ngroups && lane == 0) decide_sig_group(v, g, gsize, c, clean_max, ex);
   }
 }
 
@@ -300,14 +328,12 @@ __device__ __noinline__ void fused_verify(const PassParams* pp) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();                       // every block's records before they are read
-  VerifyParams v = *pp->fverify;
-  v.exec_index = pp->exec_index;
-  v.cond_flag = pp->fcond_flag;
-  v.cond = pp->fcond;
+  const VerifyParams& v = *pp->fverify;
+  const ExecFields ex{pp->exec_index, nullptr, cudaGraphConditionalHandle{}};
   int lanes = 1;
   while (lanes < v.group && lanes < 32) lanes <<= 1;
   unsigned long long clean_max = 0;
-  verify_sig_serial<real>(v, lanes, clean_max, 0, 1);
+  verify_sig_serial<real>(v, lanes, clean_max, 0, 1, &ex);
   for (int off = 16; off > 0; off >>= 1) clean_max = max(clean_max, __shfl_xor_sync(0xffffffffu, clean_max, off));
   if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = clean_max;
   __syncthreads();

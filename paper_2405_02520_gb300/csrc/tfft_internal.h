@@ -223,15 +223,14 @@ struct PassParams {
   unsigned buf_bytes;     // bytes per buffer (tile rounded up to 1 KiB)
   int* err_flag;          // set when a bounded wait gives up
   long long wait_limit;   // polls of a tile-arrival wait before it gives up
-  // fused verification (single-pass plans of few groups): every block counts
-  // itself in *fdone once its tiles are done, and the last one verifies every
-  // group with *fverify (this exec's index in its log entries), then resets
-  // the count; nullptr: a separate verification launch
+  // fused verification (single-pass plans of few groups, stream-launched
+  // whole-batch execs): every block counts itself in *fdone once its tiles
+  // are done, and the last one verifies every group with *fverify (this
+  // exec's index in its log entries), then resets the count; nullptr: a
+  // separate verification launch
   const VerifyParams* fverify;
   unsigned* fdone;
   long long exec_index;
-  long long* fcond_flag;                 // inside the exec's graph: its conditional correction
-  cudaGraphConditionalHandle fcond;
   TileMap map_in, map_out;
   CUtensorMap tmap_in;     // 64-byte aligned by its own type
   CUtensorMap tmap_out;
