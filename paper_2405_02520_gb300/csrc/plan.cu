@@ -198,6 +198,7 @@ struct tfft_plan_s {
   void* last_out = nullptr;
   bool cg_off = false;              // building failed once: stream launches only
   bool cg_full = false;             // the cached graph also holds the passes
+  bool cg_armed = false;            // ... with an armed test fault in them (built for one exec)
   // fused verification (single-pass plans of few groups, stream-launched whole-batch execs):
   // the pass kernel's last block verifies, with the parameters in fverify
   int fuse = 0;
@@ -1449,11 +1450,13 @@ void make_checks(tfft_plan_s* p, const void* in, void* out, int64_t b0, int64_t 
 
 // Which cached graph a whole-batch exec on a stream that is not being
 // captured takes: 2 the whole exec (passes, verification, the conditional
-// correction) when no test fault is armed and no per-kernel timing is on and
-// `allow_full`; 1 the verification and correction only (after the passes'
-// stream launches); 0 none (stream launches).  A graph is built when a pair
-// of buffers comes back (an exec that rotates over many buffers keeps the
-// stream launches), and again when the kind it needs changes.
+// correction) when no per-kernel timing is on and `allow_full`; 1 the
+// verification and correction only (after the passes' stream launches); 0
+// none (stream launches).  A graph is built when a pair of buffers comes back
+// (an exec that rotates over many buffers keeps the stream launches), and
+// again when the kind it needs changes.  An exec with a test fault armed
+// builds a whole-exec graph of its own (the fault sits in its pass nodes),
+// and the next exec rebuilds the clean one.
 int pick_graph(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_t b0, int64_t nb,
                const VerifyParams& v, const FixParams& f, bool allow_full) {
   if (!p->abft || b0 != 0 || nb != p->batch || p->cg_off) return 0;
@@ -1463,22 +1466,24 @@ int pick_graph(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
   else cudaGetLastError();        // e.g. the legacy stream during another thread's global capture
   if (capturing) return 0;
   const bool armed = p->npending > 0 || p->pending.mode != 0;
-  const bool full = allow_full && !p->timing && !armed;
+  const bool full = allow_full && !p->timing;
   // a fused plan's stream-launched pass verifies itself, so it takes no
   // verification-only graph; its whole-exec graph holds the separate
-  // verification kernel (measured faster there: 22.9 against 24.6 us at
-  // 1024 x 256, where the fused form saves a launch only on streams)
+  // verification kernel (no slower there than the fused pass node)
   if (p->fuse && !full) return 0;
-  const bool cached = p->cgx && p->cg_in == in && p->cg_out == out && p->cg_full == full;
+  const bool cached = p->cgx && p->cg_in == in && p->cg_out == out && p->cg_full == full &&
+                      !(full && (armed || p->cg_armed));
   const bool again = p->last_in == in && p->last_out == out;
   p->last_in = in;
   p->last_out = out;
-  if (!cached && again && build_correction_graph(p, v, f, in, out, full)) {
+  if (cached) return full ? 2 : 1;
+  if (!again) return 0;
+  if (build_correction_graph(p, v, f, in, out, full)) {
     p->cg_off = true;
     return 0;
   }
-  if (p->cgx && p->cg_in == in && p->cg_out == out && p->cg_full == full) return full ? 2 : 1;
-  return 0;
+  p->cg_armed = full && armed;
+  return full ? 2 : 1;
 }
 
 // Launches the cached graph with this exec's index in the verification's
