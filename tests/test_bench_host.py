@@ -52,3 +52,11 @@ def test_recorded_traffic_follows_the_source_hash(tmp_path, monkeypatch):
 def test_host_cores_positive():
     assert bench.host_cores() >= 1
     assert bench.host_cores() <= (os.cpu_count() or 1)
+
+
+def test_min_passes_follows_the_tile_and_two_pass_limits():
+    # one 4096-point tile, two passes of at most 8192-point sub-transforms
+    # (2^26 = 8192^2), three beyond
+    assert [bench.min_passes(1 << m) for m in (1, 8, 12)] == [1, 1, 1]
+    assert [bench.min_passes(1 << m) for m in (13, 20, 24, 26)] == [2, 2, 2, 2]
+    assert [bench.min_passes(1 << m) for m in (27, 29)] == [3, 3]
