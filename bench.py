@@ -769,12 +769,15 @@ def config1_measure(t, torch, stream, peak):
     return out
 
 
-# Real flops per element that the complex128 tile kernels execute per radix-8
-# stage: the in-register DFT-8 (48 adds and 8 multiplies per 8 values, 7 per
-# value) and the seven stage twiddles of a butterfly (6 flops each per 8
-# values, 5.25 per value); plus 6 per element at every inter-pass twiddle.
-C128_FLOPS_PER_ELEM_STAGE8 = 12.25
-C128_FLOPS_PER_ELEM_TWIDDLE = 6.0
+# Real flops that the complex128 tile kernels execute per value, from their
+# in-register DFTs (recursive radix 2 with the trivial roots free: DFT-2 4,
+# DFT-4 16, DFT-8 56 and DFT-16 176 flops), their stage twiddles (one complex
+# multiply, 6 flops, for E - 1 of every E values at each stage after the
+# first) and the column passes' inter-pass twiddles (a complex multiply a
+# value plus the recurrence that steps the twiddle along a thread's values).
+# The checksum arithmetic is not counted.
+C128_DFT_FLOPS = {1: 0, 2: 4, 4: 16, 8: 56, 16: 176}
+C128_CMUL_FLOPS = 6.0
 
 
 def sweep_campaign(t, torch, x, y, stream, sweep, total, launches=100):
@@ -846,9 +849,22 @@ def sweep_campaign(t, torch, x, y, stream, sweep, total, launches=100):
     return out
 
 
-def c128_executed_flops(n, b, passes):
+def c128_executed_flops(n, b, info):
+    """Flops the complex128 passes of a plan execute on their FFT arithmetic:
+    a pass of S stages over nsub values is a radix-R0 stage then S - 1 of
+    radix E (16 where S is log2(nsub) / 4 rounded up and differs from the
+    radix-8 count, else 8), R0 = nsub / E^(S-1)."""
     import math
-    return b * n * (C128_FLOPS_PER_ELEM_STAGE8 * math.log2(n) / 3.0 + C128_FLOPS_PER_ELEM_TWIDDLE * (passes - 1))
+    per = 0.0
+    for i in range(info["passes"]):
+        nsub, st = info["nsub"][i], info["stages"][i]
+        lg = int(round(math.log2(nsub)))
+        e = 16 if st == -(-lg // 4) and st != -(-lg // 3) else 8
+        r0 = nsub // e ** (st - 1)
+        per += C128_DFT_FLOPS[r0] / r0 + (st - 1) * (C128_DFT_FLOPS[e] / e + C128_CMUL_FLOPS * (e - 1) / e)
+        if i < info["passes"] - 1:          # inter-pass twiddle of this column pass
+            per += C128_CMUL_FLOPS * (1 + (e - 1) / e)
+    return b * n * per
 
 
 def c128_measure(t, torch, stream, peak):
@@ -859,8 +875,9 @@ def c128_measure(t, torch, stream, peak):
     multiply-add peak measured here (tfft_measure_fma_peak)."""
     fp64 = t.tfft_measure_fma_peak(True, 4000)
     out = {"fp64_peak_measured_tflops": round(fp64, 3), "fp64_nominal_tflops": 1.25,
-           "executed_flops_per_elem": f"{C128_FLOPS_PER_ELEM_STAGE8} per radix-8 stage (log2 N / 3 stages) "
-                                      f"+ {C128_FLOPS_PER_ELEM_TWIDDLE} per inter-pass twiddle"}
+           "executed_flops": "in-register DFTs (DFT-8 56, DFT-16 176 flops), stage twiddles "
+                             "(6 flops for (E-1)/E of the values at each later stage), inter-pass "
+                             "twiddles and their recurrence; checksums not counted"}
     for lg, b in ((20, 64), (12, 1 << 14)):
         n = 1 << lg
         xs = torch.empty((b, n), dtype=torch.complex128, device=stream.device)
@@ -871,7 +888,8 @@ def c128_measure(t, torch, stream, peak):
         res = {}
         for name, mode in (("on", t.TFFT_ABFT_TWO_SIDED), ("off", t.TFFT_ABFT_OFF)):
             pl = t.tfft_plan(n, b, t.TFFT_C128, mode)
-            passes = t.tfft_plan_info(pl)["passes"]
+            info = t.tfft_plan_info(pl)
+            passes = info["passes"]
             for _ in range(3):
                 t.tfft_exec(pl, xs, ys, stream)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -886,7 +904,7 @@ def c128_measure(t, torch, stream, peak):
                 res["passes"] = passes
                 res["gflops"] = round(flops(n, b) / (ms / 1e3) / 1e9, 1)
                 res["hbm_frac"] = round(32.0 * passes * n * b / (ms / 1e3) / 1e9 / peak, 4)
-                ex = c128_executed_flops(n, b, passes)
+                ex = c128_executed_flops(n, b, info)
                 res["executed_tflops"] = round(ex / (ms / 1e3) / 1e12, 4)
                 res["fp64_frac"] = round(ex / (ms / 1e3) / 1e12 / fp64, 4)
                 res["detected"] = t.tfft_report(pl)[0]

@@ -27,6 +27,7 @@ cudaError_t launch_pass_f64(const PassParams& p, int E, int grid, size_t smem, c
     case 2: return launch_E<2>(p, grid, smem, s);
     case 4: return launch_E<4>(p, grid, smem, s);
     case 8: return launch_E<8>(p, grid, smem, s);
+    case 16: return launch_E<16>(p, grid, smem, s);     // 4096-point single pass
     default: return cudaErrorInvalidValue;
   }
 }
@@ -37,6 +38,7 @@ cudaError_t pass_func_attrs_f64(int E, size_t smem, int block, int* blocks_per_s
     case 2: return attrs_E<2>(smem, block, blocks_per_sm);
     case 4: return attrs_E<4>(smem, block, blocks_per_sm);
     case 8: return attrs_E<8>(smem, block, blocks_per_sm);
+    case 16: return attrs_E<16>(smem, block, blocks_per_sm);
     default: return cudaErrorInvalidValue;
   }
 }

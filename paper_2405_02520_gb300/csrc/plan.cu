@@ -99,6 +99,7 @@ struct PassPlan {
   int vdt = 0;                     // v3 kernel family (launch_v3 dtype code)
   int vtc = 0;                     // v3 tensor-core variant (3 split TF32, 1 TF32), 0 none
   int vnt = 256;                   // v3 threads per block (256, or 512 for the wide tiles)
+  int no_tile = 0;                 // no TMA tile kernel for this pass's E (complex128, E = 16)
   int64_t vLB = 0;                 // v3 line blocks per signal
   unsigned buf_bytes = 0;
   size_t tsmem = 0;
@@ -367,9 +368,12 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
   // lose from 2^21 (2.58 against 2.56 ms, 2.76 against 2.49 ms at 2^22)
   const int64_t FMAX2 = c64 ? 2048 : NSUBMAX;
   const int64_t TWO_PASS_MAX = c64 ? (int64_t(1) << 20) : (int64_t)NSUBMAX * LASTMAX2;
+  // one pass up to 4096 points for both types: complex128 then takes 16
+  // values a thread (one 4096-point line a tile of 256 threads)
+  const int64_t ONE_PASS_MAX = 4096;
   int passes;
   if (o->force_passes) passes = o->force_passes;
-  else if (n <= TILE) passes = 1;
+  else if (n <= ONE_PASS_MAX) passes = 1;
   else if (n <= TWO_PASS_MAX) passes = 2;
   else passes = 3;
   const int m = ilog2(n);
@@ -406,7 +410,7 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
     mf[0] = o->first_pass_log2;
     mf[1] = m - mf[0];
   }
-  if (passes == 1 && n > TILE) return TFFT_ERR_INVALID_ARG;
+  if (passes == 1 && n > ONE_PASS_MAX) return TFFT_ERR_INVALID_ARG;
   for (int i = 1; i < passes; i++)
     if (mf[i] < 1) return TFFT_ERR_INVALID_ARG;
   if (passes == 2 && c64) {
@@ -424,6 +428,10 @@ int plan_build(tfft_plan_s* p, const tfft_plan_opts* o) {
     PassPlan& q = p->pp[0];
     q.nsub = (int)n;
     q.E = pick_E(q.nsub, E0);
+    if (n > TILE) {                     // complex128, 4096 points: radix 16
+      q.E = v3_radix(1, (int)n);
+      q.no_tile = 1;
+    }
     q.lines_are_signals = 1;
     int C = std::max(1, TILE / q.nsub);
     while (C > 1 && (G % C != 0 || C > G)) C >>= 1;   // tiles never straddle groups
@@ -508,8 +516,7 @@ void plan_slots(tfft_plan_s* p) {
   if (p->sigrec) {
     auto per_signal = [&](const PassPlan& q) -> int64_t {
       if (q.role != 0) return q.vLB * (q.vnt / 32);
-      const int E = p->dtype == TFFT_C64 ? 16 : 8;
-      const int64_t tpl = q.nsub / E;
+      const int64_t tpl = q.nsub / v3_radix(p->dtype == TFFT_C64 ? 0 : 1, q.nsub);
       return tpl > 32 ? tpl / 32 : 1;
     };
     p->sslots_in = per_signal(f);
@@ -577,6 +584,7 @@ int plan_tma(tfft_plan_s* p) {
   const int64_t B = p->batch, es = (int64_t)p->esize;
   for (int i = 0; i < p->passes; i++) {
     PassPlan& q = p->pp[i];
+    if (q.no_tile) continue;
     TileMap mi{}, mo{};
     MapGeom gi{}, go{};
     const int64_t nsub = q.nsub, C = q.C;
@@ -665,15 +673,15 @@ int plan_v3(tfft_plan_s* p) {
   const int vdt = c64 ? 0 : 1;
   const int vtc = p->prec == TFFT_PREC_TF32X3 ? 3
                 : p->prec == TFFT_PREC_BF16X3 ? 2 : (p->prec == TFFT_PREC_TF32 ? 1 : 0);
-  const int64_t E = c64 ? 16 : 8;
   const int64_t B = p->batch;
   // one pass on the v3 kernel of `nt` threads (tiles of nt E values); false
   // when that kernel has no instantiation for the pass or its tiles do not fit
   auto try_v3 = [&](int i, int nt) -> bool {
     PassPlan& q = p->pp[i];
+    const int64_t nsub = q.nsub;
+    const int64_t E = v3_radix(vdt, (int)nsub);
     const int64_t TILE = nt * E;
     const bool wide = nt == 512;
-    const int64_t nsub = q.nsub;
     const int role = q.lines_are_signals ? 0 : (i == p->passes - 1 ? 2 : 1);
     const int64_t C = TILE / nsub;
     if (C < 1 || TILE % nsub) return false;
@@ -788,6 +796,10 @@ int plan_v3(tfft_plan_s* p) {
   for (int i = 0; i < p->passes; i++) {
     const PassPlan& q = p->pp[i];
     const int role = q.lines_are_signals ? 0 : (i == p->passes - 1 ? 2 : 1);
+    if (q.no_tile) {                   // the 256-thread v3 tile, else the direct-load kernel
+      try_v3(i, 256);
+      continue;
+    }
     // complex64 column and last passes of 1024 and 2048 points: the
     // 512-thread tiles (twice the lines, twice the row bytes) first; 512-point
     // passes run faster on the 256-thread tiles (two blocks per SM): 0.89
@@ -819,7 +831,7 @@ int plan_tables(tfft_plan_s* p) {
   for (int i = 0; i < p->passes; i++) {
     PassPlan& q = p->pp[i];
     if (!q.v3) continue;
-    const int E = p->dtype == TFFT_C64 ? 16 : 8;
+    const int E = v3_radix(p->dtype == TFFT_C64 ? 0 : 1, q.nsub);
     int S = 0;
     for (int64_t v = 1; v < q.nsub; v *= E) S++;
     S = std::max(S, 1);

@@ -249,6 +249,7 @@ cudaError_t tile_func_attrs_f64(int E, size_t smem, int block, int* blocks_per_s
 // Return cudaErrorInvalidValue for an (nsub, role) without an instantiation.
 cudaError_t launch_v3(int dtype, int role, int nsub, const PassParams& p, int grid, size_t smem, cudaStream_t s);
 cudaError_t v3_attrs(int dtype, int role, int nsub, size_t smem, int* blocks_per_sm);
+int v3_radix(int dtype, int nsub);
 int v3_scratch_bytes(int dtype, int nsub);
 int v3_twiddle_smem_bytes(int dtype, int nsub);
 // 512-thread v3 kernels (v3_f32_wide.cu, complex64): column (role 1) and last

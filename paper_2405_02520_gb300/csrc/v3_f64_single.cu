@@ -10,6 +10,7 @@ cudaError_t v3_launch_f64_single(int nsub, const PassParams& p, int grid, size_t
     case 512: fft_v3_kernel<double, 512, 8, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
     case 1024: fft_v3_kernel<double, 1024, 8, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
     case 2048: fft_v3_kernel<double, 2048, 8, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
+    case 4096: fft_v3_kernel<double, 4096, 16, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
     default: return cudaErrorInvalidValue;
   }
 }
@@ -22,6 +23,7 @@ cudaError_t v3_attrs_f64_single(int nsub, size_t smem, int* bps) {
     case 512: f = (const void*)fft_v3_kernel<double, 512, 8, 0>; break;
     case 1024: f = (const void*)fft_v3_kernel<double, 1024, 8, 0>; break;
     case 2048: f = (const void*)fft_v3_kernel<double, 2048, 8, 0>; break;
+    case 4096: f = (const void*)fft_v3_kernel<double, 4096, 16, 0>; break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);

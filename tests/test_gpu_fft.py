@@ -109,3 +109,36 @@ def test_full_size_sampled_parity(log2n):
     t.tfft_destroy(plan)
     del xt, yt
     torch.cuda.empty_cache()
+
+
+def test_c128_4096_one_pass_radix16():
+    """complex128 N = 4096 runs as one pass of three radix-16 stages (one line
+    a 256-thread tile): parity with the oracle over a batch with a ragged last
+    group, the same output as the forced two-pass plan within tolerance, and
+    a scaled value at every stage (input read, each radix stage) detected,
+    named and corrected -- the correction recomputes through the direct-load
+    pass kernel of the same radix."""
+    n, batch = 4096, 37
+    x = normal_batch(n, batch, seed=41)
+    ref = oracle_fft(x)
+    plan = t.tfft_plan(n, batch, t.TFFT_C128, t.TFFT_ABFT_TWO_SIDED)
+    info = t.tfft_plan_info(plan)
+    assert info["passes"] == 1 and info["stages"][0] == 3 and info["tile_threads"][0] == 256
+    y, _ = run_gpu(x, t.TFFT_C128, plan=plan)
+    assert rel_err_rows(y, ref).max() <= tol(n, t.TFFT_C128)
+    assert t.tfft_report(plan) == (0, 0)
+    y2, p2 = run_gpu(x, t.TFFT_C128, force_passes=2)
+    assert t.tfft_plan_info(p2)["passes"] == 2
+    assert rel_err_rows(y2, ref).max() <= tol(n, t.TFFT_C128)
+    t.tfft_destroy(p2)
+    rng = np.random.default_rng(43)
+    for k, stage in enumerate((-1, 0, 1, 2)):
+        sig, idx = int(rng.integers(batch)), int(rng.integers(n))
+        fault = dict(mode=t.TFFT_FAULT_SCALE, pass_=0, stage=stage, signal=sig, line=0, index=idx,
+                     factor=1.0 + 1e-3)
+        yf, _ = run_gpu(x, t.TFFT_C128, plan=plan, fault=fault)
+        assert rel_err_rows(yf, ref).max() <= tol(n, t.TFFT_C128), stage
+        assert t.tfft_report(plan) == (k + 1, k + 1), stage
+        ev, _ = t.tfft_fault_log(plan)
+        assert ev[-1]["signal"] == sig, stage
+    t.tfft_destroy(plan)
