@@ -190,7 +190,11 @@ int tfft_plan_ex(tfft_plan_t *out, const tfft_plan_opts *opts);
  * (in, out) pair comes back on a stream that is not being captured, the plan
  * builds (once for that pair) a CUDA graph of the verification and the
  * correction launches, the latter under a conditional node that runs only
- * when a group was flagged; other execs launch them directly.
+ * when a group was flagged; other execs launch them directly.  A
+ * single-pass plan of at most 64 checksum groups (tfft_info's
+ * launches_per_exec is 1) runs a whole-batch exec as its pass kernel alone:
+ * the kernel's last block verifies every group and corrects the flagged
+ * ones itself (Section III-B, the one-pass case).
  * Returns TFFT_ERR_CUDA if a launch fails.
  */
 int tfft_exec(tfft_plan_t p, const void *in, void *out, tfft_stream_t stream);

@@ -31,6 +31,7 @@
 
 #include "fft_tile.cuh"
 #include "sigverify.cuh"
+#include "fusedfix.cuh"
 #include "tc.cuh"
 
 namespace tfft {
@@ -1118,7 +1119,13 @@ __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() 
   __shared__ V3Smem<NT / 32> vs;
   v3_body<real, NSUB, E, ROLE, TC, NT>(p, blockIdx.x, gridDim.x, p.nchunks, blockIdx.x == 0, vs);
   if constexpr (ROLE == V3_SINGLE) {
-    if (p.fverify) fused_verify<real>(&p);
+    // the last block verifies the exec and corrects what it queued, in the
+    // tile ring (free once every tile is done)
+    if (p.fverify && fused_verify<real>(&p)) {
+      extern __shared__ __align__(16) unsigned char smem_raw[];
+      unsigned char* ring = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+      fused_correct<real>(p, *p.fverify, ring, (size_t)p.nbuf * p.buf_bytes);
+    }
   }
 }
 

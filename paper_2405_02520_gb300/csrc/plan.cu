@@ -937,14 +937,19 @@ int plan_wtable(tfft_plan_s* p) {
 void make_checks(tfft_plan_s* p, const void* in, void* out, int64_t b0, int64_t nb, VerifyParams& v,
                  FixParams& f);
 
-// Fused verification: single-pass plans with per-signal records whose
-// groups one block verifies in a few rounds (at most kFuseGroups groups, few
-// records a signal) let the pass kernel's last block verify a whole-batch
-// exec -- one launch and one graph node less for small transforms.
+// Fused verification and correction: single-pass plans with per-signal
+// records whose groups one block verifies in a few rounds (at most
+// kFuseGroups groups, few records a signal) let the pass kernel's last block
+// verify a whole-batch exec and correct the groups it queued (one N-point
+// transform in the block's tile ring per group) -- a clean exec is one
+// kernel launch.
 constexpr int64_t kFuseGroups = 64;
 int plan_fused(tfft_plan_s* p) {
-  const bool want = p->abft && p->sigrec && p->passes == 1 && p->pp[0].v3 && p->pp[0].role == 0 &&
-                    p->vgroups <= kFuseGroups && p->sig_split == 0 && p->sig_blk_lanes == 0;
+  const PassPlan& q = p->pp[0];
+  const bool want = p->abft && p->sigrec && p->passes == 1 && q.v3 && q.role == 0 &&
+                    p->vgroups <= kFuseGroups && p->sig_split == 0 && p->sig_blk_lanes == 0 &&
+                    (int64_t)q.nbuf * q.buf_bytes >= p->n * (int64_t)p->esize && p->n <= 4096 &&
+                    p->tw_sub_n == p->n;
   if (!want) return 0;
   VerifyParams v{};
   FixParams f{};
@@ -1479,10 +1484,9 @@ int pick_graph(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
   if (capturing) return 0;
   const bool armed = p->npending > 0 || p->pending.mode != 0;
   const bool full = allow_full && !p->timing;
-  // a fused plan's stream-launched pass verifies itself, so it takes no
-  // verification-only graph; its whole-exec graph holds the separate
-  // verification kernel (no slower there than the fused pass node)
-  if (p->fuse && !full) return 0;
+  // a fused plan's exec is its pass kernel alone (it verifies and corrects
+  // in its last block): nothing to put in a graph
+  if (p->fuse) return 0;
   const bool cached = p->cgx && p->cg_in == in && p->cg_out == out && p->cg_full == full &&
                       !(full && (armed || p->cg_armed));
   const bool again = p->last_in == in && p->last_out == out;
@@ -1530,8 +1534,9 @@ int exec_range(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
   if (rc) return rc;
   if (!p->abft) return 0;
   if (gk == 1) return launch_graph(p, s);
-  const bool fused = p->fuse && b0 == 0 && nb == p->batch;     // the pass kernel verified
-  if (!fused && (rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
+  // the pass kernel of a fused plan verified and corrected the whole batch
+  if (p->fuse && b0 == 0 && nb == p->batch) return 0;
+  if ((rc = timed_launch(p, 4, s, [&] { return launch_verify(v, s); }))) return rc;
   return enqueue_correction(p, f, in, out, nb, s);
 }
 
@@ -1919,7 +1924,7 @@ int tfft_plan_info(tfft_plan_t p, tfft_info* info) {
   info->max_faults = p->cap_fix;
   info->kappa = p->kappa;
   info->workspace_bytes = p->workspace_bytes;
-  info->launches_per_exec = p->passes + (p->abft ? 3 + 2 * p->passes : 0);
+  info->launches_per_exec = p->fuse ? 1 : p->passes + (p->abft ? 3 + 2 * p->passes : 0);
   info->checksum_vector = p->rvec == RVEC_WANG ? TFFT_R_WANG : TFFT_R_SIGNED_WANG;
   info->checksum_seed = p->rseed;
   info->direction = p->inverse ? TFFT_INVERSE : TFFT_FORWARD;

@@ -315,18 +315,20 @@ __device__ void verify_sig_serial(const VerifyParams& v, int lanes, unsigned lon
 }
 
 // The fused verification, at the end of a single-pass tile kernel: each
-// block's threads fence their record stores and the block counts itself; the
-// last block (no block waits for another) fences again, verifies every
-// group, adds its largest clean ratio and resets the count.
+// block's threads fence their record stores (and the tile stores their
+// block's bulk copies completed) and the block counts itself; the last block
+// (no block waits for another) fences again, verifies every group, adds its
+// largest clean ratio and resets the count.  Returns true in that block.
 template <typename real>
-__device__ __noinline__ void fused_verify(const PassParams* pp) {
+__device__ __noinline__ bool fused_verify(const PassParams* pp) {
   __shared__ int s_last;
   __shared__ unsigned long long s_max[32];
-  __threadfence();                       // this thread's records before the count
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  __threadfence();                       // this thread's records and stores before the count
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(pp->fdone, 1u) == gridDim.x - 1u;
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last) return false;
   __threadfence();                       // every block's records before they are read
   const VerifyParams& v = *pp->fverify;
   const ExecFields ex{pp->exec_index, nullptr, cudaGraphConditionalHandle{}};
@@ -343,6 +345,8 @@ __device__ __noinline__ void fused_verify(const PassParams* pp) {
     if (m) atomicMax(&v.counters->max_clean_ratio_bits, m);
     *pp->fdone = 0u;
   }
+  __syncthreads();                       // the groups this block queued are in the lists
+  return true;
 }
 
 }  // namespace tfft

@@ -146,9 +146,10 @@ def test_no_false_positives_on_clean_launches(log2n, batch, launches):
 @pytest.mark.parametrize("log2n,batch", [(10, 64), (16, 20)])
 def test_correction_graph_replayed_with_faults(log2n, batch):
     """The same buffers exec'd again and again (verification and correction
-    replayed from the plan's graph): clean execs stay clean, a located fault
-    is corrected through the graph's conditional body, two faults in one
-    group are recomputed through it, and later clean execs are clean."""
+    replayed from the plan's graph; N = 1024 x 64 is a fused plan, whose
+    kernel corrects in its last block instead): clean execs stay clean, a
+    located fault is corrected, two faults in one group are recomputed, and
+    later clean execs are clean."""
     import torch
     n = 1 << log2n
     x = uniform_batch(n, batch, seed=5100 + log2n)
@@ -220,4 +221,38 @@ def test_plain_wang_vector_parity_and_fault(log2n, batch):
         res = oabft.run(x, yf, group=info["group"], u=2.0 ** -24, kappa=info["kappa"], kind="wang",
                         per_signal=True)
         assert res.located == {fault["signal"] // info["group"]: fault["signal"]}
+    t.tfft_destroy(plan)
+
+
+@pytest.mark.parametrize("dtype", [t.TFFT_C64, t.TFFT_C128])
+def test_fused_exec_is_one_launch_and_corrects_in_its_kernel(dtype):
+    """A single-pass plan of few checksum groups (N = 1024, batch 256: 16
+    groups) runs an exec as one kernel whose last block verifies and corrects:
+    a huge input-side flip (located: W c1 minus the other signals' outputs),
+    two faults in one group (not locatable: the group recomputed in the
+    block), each exec one launch, every output within the tolerance."""
+    n, batch = 1024, 256
+    x = uniform_batch(n, batch, seed=77)
+    if dtype == t.TFFT_C128:
+        x = x.astype(np.complex128)
+    ref = oracle_fft(x)
+    plan = t.tfft_plan(n, batch, dtype, t.TFFT_ABFT_TWO_SIDED)
+    info = t.tfft_plan_info(plan)
+    assert info["passes"] == 1 and info["launches_per_exec"] == 1
+    y, _ = run_gpu(x, dtype, plan=plan)
+    assert rel_err_rows(y, ref).max() <= tol(n, dtype)
+    assert t.tfft_report(plan) == (0, 0)
+    bit = 30 if dtype == t.TFFT_C64 else 62
+    faults = [dict(mode=t.TFFT_FAULT_BITFLIP, pass_=0, stage=-1, signal=200, line=0, index=9, bit=bit),
+              dict(mode=t.TFFT_FAULT_ADD_PAIR, pass_=0, stage=info["stages"][0] - 1, signal=35, line=0, index=5,
+                   factor=3.0)]
+    for k, fault in enumerate(faults):
+        before = t.tfft_report_ex(plan)["launches"]
+        y, _ = run_gpu(x, dtype, plan=plan, fault=fault)
+        assert t.tfft_report_ex(plan)["launches"] == before + 1
+        assert rel_err_rows(y, ref).max() <= tol(n, dtype), fault
+    st = t.tfft_report_ex(plan)
+    assert st["detected"] == 2 and st["corrected"] == 1 and st["recomputed"] == 1, st
+    ev, total = t.tfft_fault_log(plan)
+    assert total == 2 and ev[0]["signal"] == 200 and ev[0]["action"] == 1 and ev[1]["action"] == 2
     t.tfft_destroy(plan)
