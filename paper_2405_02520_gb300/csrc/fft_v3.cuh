@@ -461,6 +461,14 @@ __device__ __forceinline__ bool v3_body(const PassParams& p, long long cfirst, l
   cT* scr = reinterpret_cast<cT*>(base + (size_t)nbuf * p.buf_bytes + 1024);
   volatile int* abort_flag = &s_abort;
 
+  // stage twiddles: from the plan's table, staged next to the scratch when small
+  const cT* twt = reinterpret_cast<const cT*>(p.tw_stage);
+  auto stage_twiddles = [&] {
+    if constexpr (G::TWS) {
+      cT* tsm = scr + G::SCR;
+      for (int i = t; i < G::TWN; i += G::T) tsm[i] = twt[i];
+    }
+  };
   if (t == 0) {
     for (int s = 0; s < nbuf; s++) {
       mbar_init(&full[s], 1);
@@ -470,11 +478,17 @@ __device__ __forceinline__ bool v3_body(const PassParams& p, long long cfirst, l
     }
     fence_mbar_init();
     s_abort = 0;
-    if (zero_entry) {
-      if (p.zero_on_entry[0]) *p.zero_on_entry[0] = 0;
-      if (p.zero_on_entry[1]) *p.zero_on_entry[1] = 0;
-      if (p.zero_on_entry[2]) *p.zero_on_entry[2] = 0;
-    }
+  }
+  if (p.pdl) {
+    // a programmatic dependent: the table (a plan constant) while the kernel
+    // before it finishes, then wait for it before any global write or load
+    stage_twiddles();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+  }
+  if (t == 0 && zero_entry) {
+    if (p.zero_on_entry[0]) *p.zero_on_entry[0] = 0;
+    if (p.zero_on_entry[1]) *p.zero_on_entry[1] = 0;
+    if (p.zero_on_entry[2]) *p.zero_on_entry[2] = 0;
   }
   __syncthreads();
   if (t == 0) {
@@ -488,13 +502,8 @@ __device__ __forceinline__ bool v3_body(const PassParams& p, long long cfirst, l
     }
     for (int w = 0; w < G::NW; w++) ldc[w] = ld;
   }
-  // stage twiddles: from the plan's table, staged next to the scratch when small
-  const cT* twt = reinterpret_cast<const cT*>(p.tw_stage);
-  if constexpr (G::TWS) {
-    cT* tsm = scr + G::SCR;
-    for (int i = t; i < G::TWN; i += G::T) tsm[i] = twt[i];
-    twt = tsm;
-  }
+  if (!p.pdl) stage_twiddles();
+  if constexpr (G::TWS) twt = scr + G::SCR;
   // tensor-core operands and accumulator (TC != 0)
   uint64_t* tcbar = vs.tcbar;
   uint32_t& tc_tmem = vs.tc_tmem;
@@ -1114,14 +1123,40 @@ __device__ __forceinline__ bool v3_body(const PassParams& p, long long cfirst, l
   return gave_up;
 }
 
+// Launches `kernel` on `s`; as a programmatic dependent of the kernel before
+// it on the stream when p.pdl is set (its blocks may start while that kernel
+// finishes and wait for it in griddepcontrol.wait).
+template <typename K>
+cudaError_t launch_v3_kernel(K kernel, int grid, int threads, size_t smem, cudaStream_t s, const PassParams& p) {
+  if (!p.pdl) {
+    kernel<<<grid, threads, smem, s>>>(p);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, p);
+}
+
 template <typename real, int NSUB, int E, int ROLE, int TC = 0, int NT = 256>
 __global__ void __launch_bounds__(NT, (NT == 256 ? v3_min_blocks_tc<real, TC>() : 1)) fft_v3_kernel(const __grid_constant__ PassParams p) {
   __shared__ V3Smem<NT / 32> vs;
   v3_body<real, NSUB, E, ROLE, TC, NT>(p, blockIdx.x, gridDim.x, p.nchunks, blockIdx.x == 0, vs);
+  // this block's tiles are done: a kernel launched as a programmatic
+  // dependent of this one may start its set-up (it waits for this grid to
+  // complete before it touches global memory)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if constexpr (ROLE == V3_SINGLE) {
     // the last block verifies the exec and corrects what it queued, in the
     // tile ring (free once every tile is done)
-    if (p.fverify && fused_verify<real>(&p)) {
+    if (p.fverify && fused_verify<real>(&p) == 2) {
       extern __shared__ __align__(16) unsigned char smem_raw[];
       unsigned char* ring = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
       fused_correct<real>(p, *p.fverify, ring, (size_t)p.nbuf * p.buf_bytes);

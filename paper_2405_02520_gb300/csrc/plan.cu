@@ -203,6 +203,7 @@ struct tfft_plan_s {
   // fused verification (single-pass plans of few groups, stream-launched whole-batch execs):
   // the pass kernel's last block verifies, with the parameters in fverify
   int fuse = 0;
+  int pdl_now = 0;                   // this exec's fused pass is a programmatic dependent launch
   unsigned* fdone = nullptr;         // blocks done, reset by the last
   VerifyParams* fverify = nullptr;   // without a conditional node
 
@@ -1291,6 +1292,7 @@ PassParams main_params(tfft_plan_s* p, int i, const void* in, void* out, int64_t
     a.fverify = p->fverify;
     a.fdone = p->fdone;
     a.exec_index = p->execs;
+    a.pdl = p->pdl_now;
   }
   return a;
 }
@@ -1530,7 +1532,15 @@ int exec_range(tfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_
   if (p->abft) make_checks(p, in, out, b0, nb, v, f);
   const int gk = pick_graph(p, in, out, s, b0, nb, v, f, true);
   if (gk == 2) return launch_graph(p, s);
+  // a fused exec (one kernel) on a stream that is not being captured starts
+  // its blocks' set-up while the kernel before it finishes
+  if (p->fuse && b0 == 0 && nb == p->batch && !p->timing) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cudaGetLastError();
+    p->pdl_now = cs == cudaStreamCaptureStatusNone;
+  }
   int rc = run_passes(p, in, out, s, true, nullptr, 0, 0, 0, nb, -1, true, vg0);
+  p->pdl_now = 0;
   if (rc) return rc;
   if (!p->abft) return 0;
   if (gk == 1) return launch_graph(p, s);

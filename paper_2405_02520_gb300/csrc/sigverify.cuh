@@ -15,6 +15,7 @@ struct ExecFields {
   long long exec_index;
   long long* cond_flag;
   cudaGraphConditionalHandle cond;
+  int* queued = nullptr;        // set (shared memory) when a group is queued for correction
 };
 
 // A record, read through the L2 (the fused verification reads records that
@@ -97,23 +98,20 @@ __device__ __forceinline__ void sig_add_records(const VerifyParams& v, int64_t b
                                                 int64_t o0, int64_t o1, int64_t step, SigSums<real>& a) {
   const SigIn<real>* rin = reinterpret_cast<const SigIn<real>*>(v.sig_in) + b * v.sig_slots_in;
   const SigOut<real>* rout = reinterpret_cast<const SigOut<real>*>(v.sig_out) + b * v.sig_slots_out;
-  // two records are loaded before either is added (two loads in flight; the
-  // sums are in the same order)
-  for (int64_t k = i0; k < i1; k += 2 * step) {
-    const bool two = k + step < i1;
-    const SigIn<real> r0 = ld_rec(rin + k);
-    SigIn<real> r1{};
-    if (two) r1 = ld_rec(rin + k + step);
-    a.q[0].add(r0.sr); a.q[1].add(r0.si); a.q[2].add(r0.en);
-    if (two) { a.q[0].add(r1.sr); a.q[1].add(r1.si); a.q[2].add(r1.en); }
-  }
-  for (int64_t k = o0; k < o1; k += 2 * step) {
-    const bool two = k + step < o1;
-    const SigOut<real> r0 = ld_rec(rout + k);
-    SigOut<real> r1{};
-    if (two) r1 = ld_rec(rout + k + step);
-    a.q[3].add(r0.tr); a.q[4].add(r0.ti);
-    if (two) { a.q[3].add(r1.tr); a.q[4].add(r1.ti); }
+  // two input and two output records are loaded before any is added (four
+  // loads in flight; each sum still adds its records in slot order)
+  for (int64_t ki = i0, ko = o0; ki < i1 || ko < o1; ki += 2 * step, ko += 2 * step) {
+    const bool ia = ki < i1, ib = ki + step < i1, oa = ko < o1, ob = ko + step < o1;
+    SigIn<real> r0{}, r1{};
+    SigOut<real> u0{}, u1{};
+    if (ia) r0 = ld_rec(rin + ki);
+    if (ib) r1 = ld_rec(rin + ki + step);
+    if (oa) u0 = ld_rec(rout + ko);
+    if (ob) u1 = ld_rec(rout + ko + step);
+    if (ia) { a.q[0].add(r0.sr); a.q[1].add(r0.si); a.q[2].add(r0.en); }
+    if (ib) { a.q[0].add(r1.sr); a.q[1].add(r1.si); a.q[2].add(r1.en); }
+    if (oa) { a.q[3].add(u0.tr); a.q[4].add(u0.ti); }
+    if (ob) { a.q[3].add(u1.tr); a.q[4].add(u1.ti); }
   }
   if (v.chk2) {
     const SigChk<real>* rc = reinterpret_cast<const SigChk<real>*>(v.sig_chk) + b * v.sig_slots_out;
@@ -259,6 +257,7 @@ __device__ void decide_sig_group(const VerifyParams& v, int64_t g, int64_t gsize
       }
     }
   }
+  if ((action == 1 || action == 2) && ex && ex->queued) *ex->queued = 1;
   long long* const cond_flag = ex ? ex->cond_flag : v.cond_flag;
   if ((action == 1 || action == 2) && cond_flag &&
       atomicExch(reinterpret_cast<unsigned long long*>(cond_flag), 1ull) == 0ull)
@@ -318,20 +317,23 @@ __device__ void verify_sig_serial(const VerifyParams& v, int lanes, unsigned lon
 // block's threads fence their record stores (and the tile stores their
 // block's bulk copies completed) and the block counts itself; the last block
 // (no block waits for another) fences again, verifies every group, adds its
-// largest clean ratio and resets the count.  Returns true in that block.
+// largest clean ratio and resets the count.  Returns 0 in the other blocks,
+// 1 in that block when the exec is clean, 2 when it queued a group.
 template <typename real>
-__device__ __noinline__ bool fused_verify(const PassParams* pp) {
-  __shared__ int s_last;
+__device__ __noinline__ int fused_verify(const PassParams* pp) {
+  __shared__ int s_last, s_queued;
   __shared__ unsigned long long s_max[32];
   asm volatile("fence.proxy.async.global;" ::: "memory");
   __threadfence();                       // this thread's records and stores before the count
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(pp->fdone, 1u) == gridDim.x - 1u;
   __syncthreads();
-  if (!s_last) return false;
+  if (!s_last) return 0;
   __threadfence();                       // every block's records before they are read
   const VerifyParams& v = *pp->fverify;
-  const ExecFields ex{pp->exec_index, nullptr, cudaGraphConditionalHandle{}};
+  if (threadIdx.x == 0) s_queued = 0;
+  __syncthreads();
+  const ExecFields ex{pp->exec_index, nullptr, cudaGraphConditionalHandle{}, &s_queued};
   int lanes = 1;
   while (lanes < v.group && lanes < 32) lanes <<= 1;
   unsigned long long clean_max = 0;
@@ -346,7 +348,7 @@ __device__ __noinline__ bool fused_verify(const PassParams* pp) {
     *pp->fdone = 0u;
   }
   __syncthreads();                       // the groups this block queued are in the lists
-  return true;
+  return s_queued ? 2 : 1;
 }
 
 }  // namespace tfft

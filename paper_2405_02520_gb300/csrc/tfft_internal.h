@@ -231,6 +231,11 @@ struct PassParams {
   const VerifyParams* fverify;
   unsigned* fdone;
   long long exec_index;
+  // launched as a programmatic dependent of the kernel before it on the
+  // stream: the block sets up what reads only plan constants, then waits for
+  // that kernel (griddepcontrol.wait) before its first global write or tile
+  // load
+  int pdl;
   TileMap map_in, map_out;
   CUtensorMap tmap_in;     // 64-byte aligned by its own type
   CUtensorMap tmap_out;

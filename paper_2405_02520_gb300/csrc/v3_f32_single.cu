@@ -5,11 +5,11 @@ namespace tfft {
 
 cudaError_t v3_launch_f32_single(int nsub, const PassParams& p, int grid, size_t smem, cudaStream_t s) {
   switch (nsub) {
-    case 256: fft_v3_kernel<float, 256, 16, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
-    case 512: fft_v3_kernel<float, 512, 16, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
-    case 1024: fft_v3_kernel<float, 1024, 16, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
-    case 2048: fft_v3_kernel<float, 2048, 16, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
-    case 4096: fft_v3_kernel<float, 4096, 16, 0><<<grid, 256, smem, s>>>(p); return cudaGetLastError();
+    case 256: return launch_v3_kernel(fft_v3_kernel<float, 256, 16, 0>, grid, 256, smem, s, p);
+    case 512: return launch_v3_kernel(fft_v3_kernel<float, 512, 16, 0>, grid, 256, smem, s, p);
+    case 1024: return launch_v3_kernel(fft_v3_kernel<float, 1024, 16, 0>, grid, 256, smem, s, p);
+    case 2048: return launch_v3_kernel(fft_v3_kernel<float, 2048, 16, 0>, grid, 256, smem, s, p);
+    case 4096: return launch_v3_kernel(fft_v3_kernel<float, 4096, 16, 0>, grid, 256, smem, s, p);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -256,3 +256,32 @@ def test_fused_exec_is_one_launch_and_corrects_in_its_kernel(dtype):
     ev, total = t.tfft_fault_log(plan)
     assert total == 2 and ev[0]["signal"] == 200 and ev[0]["action"] == 1 and ev[1]["action"] == 2
     t.tfft_destroy(plan)
+
+
+def test_back_to_back_fused_execs_overlap_safely():
+    """Eight fused execs (N = 1024, batch 128) issued back to back on one
+    stream with no synchronisation between them, each on its own buffers
+    (each kernel may start its set-up while the one before it verifies and
+    corrects): a fault in the fifth is corrected there, and every output
+    matches the oracle."""
+    import torch
+    n, batch = 1024, 128
+    xs = [uniform_batch(n, batch, seed=880 + i) for i in range(8)]
+    plan = t.tfft_plan(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED)
+    assert t.tfft_plan_info(plan)["launches_per_exec"] == 1
+    xt = [torch.from_numpy(x).cuda() for x in xs]
+    yt = [torch.empty_like(x) for x in xt]
+    s = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    for i in range(8):
+        if i == 4:
+            t.tfft_set_fault(plan, mode=t.TFFT_FAULT_SCALE, pass_=0, stage=0, signal=77, line=0, index=300,
+                             factor=1.25)
+        t.tfft_exec(plan, xt[i], yt[i], s)
+    torch.cuda.synchronize()
+    for i in range(8):
+        assert rel_err_rows(yt[i].cpu().numpy(), oracle_fft(xs[i])).max() <= tol(n, t.TFFT_C64), i
+    assert t.tfft_report(plan) == (1, 1)
+    ev, _ = t.tfft_fault_log(plan)
+    assert ev[-1]["signal"] == 77 and ev[-1]["exec_index"] == 4
+    t.tfft_destroy(plan)
