@@ -285,3 +285,28 @@ def test_back_to_back_fused_execs_overlap_safely():
     ev, _ = t.tfft_fault_log(plan)
     assert ev[-1]["signal"] == 77 and ev[-1]["exec_index"] == 4
     t.tfft_destroy(plan)
+
+
+def test_fused_exec_after_a_kernel_that_writes_its_input():
+    """A fused exec launched right after another kernel on the stream that
+    rewrites its input buffer (an elementwise kernel) transforms the new input:
+    the exec's kernel waits for the kernel before it before it loads a tile,
+    whatever that kernel is."""
+    import torch
+    n, batch = 1024, 64
+    xs = [uniform_batch(n, batch, seed=990 + i) for i in range(6)]
+    src = [torch.from_numpy(x).cuda() for x in xs]
+    xt = torch.empty_like(src[0])
+    yt = [torch.empty_like(xt) for _ in xs]
+    plan = t.tfft_plan(n, batch, t.TFFT_C64, t.TFFT_ABFT_TWO_SIDED)
+    assert t.tfft_plan_info(plan)["launches_per_exec"] == 1
+    s = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    for i in range(6):
+        torch.mul(src[i], 1.0, out=xt)
+        t.tfft_exec(plan, xt, yt[i], s)
+    torch.cuda.synchronize()
+    for i in range(6):
+        assert rel_err_rows(yt[i].cpu().numpy(), oracle_fft(xs[i])).max() <= tol(n, t.TFFT_C64), i
+    assert t.tfft_report(plan) == (0, 0)
+    t.tfft_destroy(plan)
