@@ -987,13 +987,28 @@ __device__ __forceinline__ bool v3_body(const PassParams& p, long long cfirst, l
         // T += r^T y over this thread's outputs: sum_q s_q w3^(k0 + q dl) y_q,
         // the outputs grouped by q mod 3
         real a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
+        if constexpr (sizeof(real) == 4) {
+          // s_q y_q as one paired multiply-add by (s_q, s_q), s_q = +-1 built
+          // from bit q of the mask (exact: the same sums as signed adds)
+          float2 A0 = {0.f, 0.f}, A1 = {0.f, 0.f}, A2 = {0.f, 0.f};
 #pragma unroll
-        for (int q = 0; q < E; q++) {
-          const bool neg = (smask >> q) & 1u;
-          const real yr = neg ? -v[q].x : v[q].x, yi = neg ? -v[q].y : v[q].y;
-          if (q % 3 == 0) { a0r += yr; a0i += yi; }
-          else if (q % 3 == 1) { a1r += yr; a1i += yi; }
-          else { a2r += yr; a2i += yi; }
+          for (int q = 0; q < E; q++) {
+            const float sq = __uint_as_float(0x3f800000u | ((smask << (31 - q)) & 0x80000000u));
+            const float2 s2 = {sq, sq};
+            if (q % 3 == 0) A0 = __ffma2_rn(s2, v[q], A0);
+            else if (q % 3 == 1) A1 = __ffma2_rn(s2, v[q], A1);
+            else A2 = __ffma2_rn(s2, v[q], A2);
+          }
+          a0r = A0.x; a0i = A0.y; a1r = A1.x; a1i = A1.y; a2r = A2.x; a2i = A2.y;
+        } else {
+#pragma unroll
+          for (int q = 0; q < E; q++) {
+            const bool neg = (smask >> q) & 1u;
+            const real yr = neg ? -v[q].x : v[q].x, yi = neg ? -v[q].y : v[q].y;
+            if (q % 3 == 0) { a0r += yr; a0i += yi; }
+            else if (q % 3 == 1) { a1r += yr; a1i += yi; }
+            else { a2r += yr; a2i += yi; }
+          }
         }
         const real hr = (real)-0.5, hs = (real)0.86602540378443864676;
         // rotate (x, y) by w3^k0
