@@ -60,3 +60,28 @@ def test_min_passes_follows_the_tile_and_two_pass_limits():
     assert [bench.min_passes(1 << m) for m in (1, 8, 12)] == [1, 1, 1]
     assert [bench.min_passes(1 << m) for m in (13, 20, 24, 26)] == [2, 2, 2, 2]
     assert [bench.min_passes(1 << m) for m in (27, 29)] == [3, 3]
+
+
+def test_c128_dft_flop_table_follows_the_radix2_recursion():
+    # Dft<R> is two Dft<R/2> and R/2 butterflies: a complex add and subtract
+    # (4 flops) after a multiply by omega_R^k, free for k = 0 and R/4, 4 flops
+    # for the eighth roots (an add, a subtract, two multiplies by sqrt(1/2)),
+    # 6 for the others (two multiplies and two multiply-adds)
+    def root_flops(r, k):
+        m = (k * (16 // r)) % 16
+        if m % 4 == 0:
+            return 0
+        return 4 if m % 2 == 0 else 6
+
+    def dft(r):
+        if r == 1:
+            return 0
+        return 2 * dft(r // 2) + sum(4 + root_flops(r, k) for k in range(r // 2))
+
+    assert {r: dft(r) for r in (1, 2, 4, 8, 16)} == bench.C128_DFT_FLOPS
+    # a 4096-point single pass: radix-16 stages 16 x 16 x 16; two 64-point
+    # passes: 8 x 8 each, plus the inter-pass twiddle and its recurrence
+    one = bench.c128_executed_flops(4096, 1, {"passes": 1, "nsub": [4096], "stages": [3]})
+    two = bench.c128_executed_flops(4096, 1, {"passes": 2, "nsub": [64, 64], "stages": [2, 2]})
+    assert one == 4096 * (176 / 16 + 2 * (176 / 16 + 6 * 15 / 16))
+    assert two == 4096 * (2 * (56 / 8 + 56 / 8 + 6 * 7 / 8) + 6 * (1 + 7 / 8))
