@@ -119,16 +119,20 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kind: str):
+def recorded_traffic(kind: str, elements: int):
     """DRAM bytes per launch of `kind` from the committed ncu summary, only if
-    it was taken on the current kernel sources."""
+    it was taken on the current kernel sources, for launches of `elements`
+    values (the summary's bytes scale with the elements of a launch)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         if d.get("kernel_source_hash") != kernel_source_hash():
             return None
-        return d.get("bytes_per_launch", {}).get(kind)
+        b = d.get("bytes_per_launch", {}).get(kind)
+        if b is None:
+            return None
+        return int(round(b * elements / d.get("bench_elements_per_launch", elements)))
     except Exception:
         return None
 
@@ -494,7 +498,7 @@ def run_ours(args):
     if rank != 0:
         return 0
     clocks = sampler.summary()
-    tr = recorded_traffic(dom)
+    tr = recorded_traffic(dom, total)
     per_n_out = {}
     for lg in sweep:
         n = 1 << lg

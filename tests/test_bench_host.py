@@ -39,14 +39,17 @@ def test_oracle_pool_runs_one_sample_per_process():
 
 
 def test_recorded_traffic_follows_the_source_hash(tmp_path, monkeypatch):
-    rec = {"kernel_source_hash": bench.kernel_source_hash(), "bytes_per_launch": {"first_pass": 123}}
+    rec = {"kernel_source_hash": bench.kernel_source_hash(), "bytes_per_launch": {"first_pass": 1230},
+           "bench_elements_per_launch": 1 << 28}
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: rec["kernel_source_hash"])
-    assert bench.recorded_traffic("first_pass") == 123
+    assert bench.recorded_traffic("first_pass", 1 << 28) == 1230
+    assert bench.recorded_traffic("first_pass", 1 << 27) == 615     # bytes scale with the launch
+    assert bench.recorded_traffic("single_pass", 1 << 28) is None
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "changed")
-    assert bench.recorded_traffic("first_pass") is None
+    assert bench.recorded_traffic("first_pass", 1 << 28) is None
 
 
 def test_host_cores_positive():
