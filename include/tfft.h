@@ -97,7 +97,10 @@ enum tfft_status {
  * Section IV-A into two or three launches), builds the FP64-accurate twiddle
  * and checksum tables on the host, uploads them, and allocates the workspace
  * (the inter-pass buffer, checksum records, fault lists, counters) on the
- * current CUDA device.  Launches no kernel.  *out receives the plan.
+ * current CUDA device.  A multi-pass plan with checksums builds its second
+ * check's table on the device (a few kernels and a complex128 transform on
+ * the legacy default stream, waited for before the call returns); no other
+ * plan launches a kernel.  *out receives the plan.
  */
 int tfft_plan(tfft_plan_t *out, int64_t n, int64_t batch, int dtype, int abft_mode);
 
