@@ -197,7 +197,11 @@ int tfft_plan_ex(tfft_plan_t *out, const tfft_plan_opts *opts);
  * single-pass plan of at most 64 checksum groups (tfft_info's
  * launches_per_exec is 1) runs a whole-batch exec as its pass kernel alone:
  * the kernel's last block verifies every group and corrects the flagged
- * ones itself (Section III-B, the one-pass case).
+ * ones itself (Section III-B, the one-pass case).  On a stream that is not
+ * being captured that kernel is a programmatic dependent launch: its blocks
+ * may initialise shared memory while the kernel before it on the stream
+ * finishes, and wait for that kernel to complete before they read or write
+ * global memory, so stream order holds as for any launch.
  * Returns TFFT_ERR_CUDA if a launch fails.
  */
 int tfft_exec(tfft_plan_t p, const void *in, void *out, tfft_stream_t stream);
